@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the batched rigid-body hot path on one GB300.
+
+One step = one pass of the whole path over one resident batch of the 7-DoF
+serial chain (2^20 instances, FP32 SoA): FK + end-effector Jacobian, RNEA,
+CRBA + L^T D L, ABA, RNEA VJP and ABA VJP. The metric counts one evaluation
+per op per instance (6 x 2^20 per step). Per-kernel CUDA-event times feed the
+roofline of the dominant kernel; a short served stream gives p50/p99; the FP64
+oracle is timed on the host cores on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl frax|reference]
+
+Under torchrun (N > 1) every rank runs its own replica of the batch (the
+instances are independent: weak scaling, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ABA/RNEA evals/sec at 1 GB300 vs roofline; served p50/p99 latency at 1e-4 rel err"
+UNIT = "evals/s"
+OPS = ["fk_jac", "rnea", "crba_ltdl", "aba", "rnea_vjp", "aba_vjp"]
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+# ------------------------------------------------------------- flop accounting
+# FP32 operations per body of each formulation (fma = 2, add/mul = 1), counted
+# from the kernels' formulas; sincos/sqrt/div are kept out. See the design doc.
+PER_BODY = {
+    # op: (revolute with parent, revolute at world, free-flyer root)
+    "fk_jac": (128, 99, 126),
+    "rnea": (298, 184, 228),
+    "crba_ltdl": (171, 0, 0),     # composite transform; the ancestor walk is added per pair
+    "aba": (852, 250, 320),
+    "rnea_vjp": (780, 500, 560),
+    "aba_vjp": (1550, 800, 900),
+}
+WALK = 54  # one force transform in the CRBA ancestor walk
+
+
+def flops_per_instance(op: str, parent, free_root: bool, nv: int) -> int:
+    n = len(parent)
+    a, r, f = PER_BODY[op]
+    tot = 0
+    for i in range(n):
+        if i == 0 and free_root:
+            tot += f
+        elif parent[i] < 0:
+            tot += r
+        else:
+            tot += a
+    if op == "crba_ltdl":
+        depth = [0] * n
+        for i in range(n):
+            depth[i] = depth[parent[i]] + 1 if parent[i] >= 0 else 0
+        tot += WALK * sum(depth)
+        tot += sum(k * k + 2 * k for k in range(nv))  # L^T D L on the dense chain bound
+    return tot
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workloads
+def make_inputs(robot, B, seed, device):
+    import numpy as np
+    import torch
+
+    import gen
+    s = gen.draw_states(robot, B, seed)
+    g = gen.draw_gbar(robot.nv, B, seed + 7)
+    host = {k: torch.from_numpy(gen.to_soa(v)) for k, v in
+            (("q", s.q), ("qd", s.qd), ("qdd", s.qdd), ("tau", s.tau), ("gbar", g))}
+    dev = {k: v.to(device) for k, v in host.items()}
+    return host, dev
+
+
+class Step:
+    """The whole hot path over one resident batch; output buffers are
+    allocated once (torch), the kernels write into them."""
+
+    def __init__(self, fx, model, robot, dev, device):
+        import torch
+        self.fx, self.m, self.d = fx, model, dev
+        B = dev["q"].shape[1]
+        nv, nb = model.nv, model.n_bodies
+        e = lambda k: torch.empty((k, B), dtype=torch.float32, device=device)
+        self.frames = list(robot.end_frames)
+        self.out = {
+            "pose": e(12 * nb), "J": e(len(self.frames) * 6 * nv), "tau": e(nv), "M": e(nv * nv),
+            "LD": e(nv * (nv + 1) // 2), "qdd": e(nv), "rq": e(model.nq), "rqd": e(nv), "rqdd": e(nv),
+            "aq": e(model.nq), "aqd": e(nv), "at": e(nv),
+        }
+        self.B = B
+
+    def run(self, events=None):
+        fx, m, d, o = self.fx, self.m, self.d, self.out
+        launches = [
+            ("fk_jac", lambda: fx.frax_jacobian(m, d["q"], self.frames, pose=o["pose"], J=o["J"])),
+            ("rnea", lambda: fx.frax_rnea(m, d["q"], d["qd"], d["qdd"], tau=o["tau"])),
+            ("crba_ltdl", lambda: fx.frax_crba(m, d["q"], M=o["M"], LD=o["LD"])),
+            ("aba", lambda: fx.frax_aba(m, d["q"], d["qd"], d["tau"], qdd=o["qdd"])),
+            ("rnea_vjp", lambda: fx.frax_rnea_vjp(m, d["q"], d["qd"], d["qdd"], d["gbar"], qbar=o["rq"],
+                                                  qdbar=o["rqd"], qddbar=o["rqdd"])),
+            ("aba_vjp", lambda: fx.frax_aba_vjp(m, d["q"], d["qd"], d["tau"], o["qdd"], d["gbar"], qbar=o["aq"],
+                                                qdbar=o["aqd"], taubar=o["at"])),
+        ]
+        for k, (name, fn) in enumerate(launches):
+            if events is not None:
+                events[name][0].record()
+            fn()
+            if events is not None:
+                events[name][1].record()
+        return len(launches)
+
+
+def cpu_baseline_child(args):
+    """Times the FP64 oracle (as it stands) on a bounded sample of the chain
+    workload, single-threaded. Prints one JSON object."""
+    import numpy as np
+
+    import gen
+    from oracle import derivatives as dv
+    from oracle import rbd
+    robot = gen.chain7(0)
+    t_budget = args.cpu_seconds
+    S = 256
+    done_inst = 0
+    t0 = time.perf_counter()
+    while True:
+        s = gen.draw_states(robot, S, 99 + done_inst)
+        g = gen.draw_gbar(robot.nv, S, 5 + done_inst)
+        rbd.fk_flat(robot, s.q)
+        rbd.jacobian(robot, s.q, list(robot.end_frames))
+        rbd.rnea(robot, s.q, s.qd, s.qdd)
+        M = rbd.crba(robot, s.q)
+        rbd.ltdl(M)
+        qdd = rbd.aba(robot, s.q, s.qd, s.tau)
+        dv.rnea_vjp(robot, s.q, s.qd, s.qdd, g)
+        dv.aba_vjp(robot, s.q, s.qd, s.tau, g)
+        done_inst += S
+        if time.perf_counter() - t0 > t_budget:
+            break
+    el = time.perf_counter() - t0
+    print(json.dumps({"value": len(OPS) * done_inst / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                      "sample": f"{done_inst} instances of the 7-DoF chain, all 6 ops, FP64 numpy oracle, "
+                                f"{el:.1f} s, 1 thread"}))
+
+
+def run_cpu_baseline(seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--cpu-seconds",
+                        str(seconds)], capture_output=True, text=True, env=env, cwd=ROOT)
+    for line in r.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+
+
+def serve_probe(fx, device, seconds):
+    """A short served stream (if the server is built): p50/p99 latency."""
+    if not hasattr(fx, "Server"):
+        return None
+    from paper_2604_04310_gb300 import serving
+    return serving.bench_stream(device, seconds=seconds)
+
+
+# ---------------------------------------------------------------- main arms
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    base = run_cpu_baseline(min(30.0, per_step * args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "7-DoF revolute chain (seed 0), 2^20 instances, FK+J/RNEA/CRBA+LTDL/ABA/"
+                                   "RNEA-VJP/ABA-VJP", "global_batch": 1 << 20, "parallelism": "replicas"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def frax_arm(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import gen
+    import paper_2604_04310_gb300 as fx
+
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    robot = gen.chain7(0)
+    B = args.batch
+    model = fx.Model.from_robot(robot)
+    host, dev = make_inputs(robot, B, 1001 + rank, device)
+    step = Step(fx, model, robot, dev, device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2 (129 MB)
+
+    for _ in range(args.warmup):
+        step.run()
+    torch.cuda.synchronize()
+    events = [{n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in OPS}
+              for _ in range(args.steps)]
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else
+                          int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    launches = 0
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between steps, outside the step's events
+        step_ev[k][0].record()
+        launches += step.run(events[k])
+        step_ev[k][1].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = sum(a.elapsed_time(b) for a, b in step_ev)
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms_max = float(t.item())
+    ms_per_step = step_ms_max / args.steps
+    evals_per_step = len(OPS) * B
+    value = world * evals_per_step / (ms_per_step / 1e3)
+
+    per_op_ms = {n: sum(ev[n][0].elapsed_time(ev[n][1]) for ev in events) / args.steps for n in OPS}
+    per_op = {n: {"ms": per_op_ms[n], "evals_per_s": B / (per_op_ms[n] / 1e3),
+                  "flops_per_instance": flops_per_instance(n, list(robot.parent), robot.has_free_root, robot.nv)}
+              for n in OPS}
+    dom = max(OPS, key=lambda n: per_op_ms[n])
+    f_inst = per_op[dom]["flops_per_instance"]
+    achieved = f_inst * B / (per_op_ms[dom] / 1e3) / 1e12
+    peak = fp32_peak_tflops(2070.0)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
+    for n in OPS:
+        fi = per_op[n]["flops_per_instance"]
+        per_op[n]["tflops"] = fi * B / (per_op_ms[n] / 1e3) / 1e12
+        per_op[n]["frac_fp32_peak"] = per_op[n]["tflops"] / peak
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = {k: v.pin_memory() for k, v in host.items()}
+        outs_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in step.out.items()}
+        h2d = sum(v.numel() * 4 for v in pin.values())
+        d2h = sum(v.numel() * 4 for v in outs_h.values())
+        n_e2e = max(3, min(args.steps, 20))
+        for it in range(n_e2e + 2):
+            if it == 2:
+                torch.cuda.synchronize()
+                te = time.perf_counter()
+            for k in dev:
+                dev[k].copy_(pin[k], non_blocking=True)
+            step.run()
+            for k in step.out:
+                outs_h[k].copy_(step.out[k], non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - te) / n_e2e
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=device)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * evals_per_step / float(tt.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": float(tt.item()) * 1e3}
+
+    serve = None
+    if rank == 0 and not args.no_serve:
+        serve = serve_probe(fx, device, args.serve_seconds)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = run_cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "7-DoF revolute chain (seed 0), 2^20 instances per GPU, one step = "
+                                       "FK+EE Jacobian, RNEA, CRBA+LTDL, ABA, RNEA-VJP, ABA-VJP",
+                           "global_batch": B * world, "parallelism": f"replicas x{world}",
+                           "l2": "256 MB buffer written between steps (L2 flush)"},
+                "clocks": clk, "gpu_launches": launches, "wall_s": wall, "per_op": per_op, "roofline": roofline,
+                "e2e": e2e, "cpu_baseline": cpu, "serving": serve}
+        print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="frax", choices=["frax", "reference"])
+    ap.add_argument("--batch", type=int, default=1 << 20)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--cpu-baseline-child", action="store_true")
+    args = ap.parse_args()
+    if args.cpu_baseline_child:
+        cpu_baseline_child(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    frax_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * frax.h — C ABI of the GB300 batched rigid-body kinematics/dynamics library.
+ *
+ * The operations are those the paper states its problem with (Sec. II):
+ * forward kinematics FK(q) -> ^0T_i, frame Jacobians, inverse dynamics
+ * (Eq. 1, tau = M qdd + c + g, no external force), the joint-space mass
+ * matrix M (Algorithm 2's result) with its tree-sparse factorisation
+ * M = L^T D L (the Cholesky-style solve of the Sec. VI footnote), and forward
+ * dynamics (Eq. 2, qdd = M^-1 (tau - c - g)) by the articulated-body
+ * algorithm, plus vector-Jacobian products of Eq. 1 and Eq. 2 (the analytic
+ * derivatives Sec. VI lists as future work).
+ *
+ * Conventions
+ *  - Spatial vectors are [angular; linear]. Body frames sit after their joint:
+ *    ^parent T_i = placement_i * joint_i(q_i).
+ *  - Gravity g (world) enters as the base acceleration a_0 = [0; -g], so tau
+ *    includes the gravity term g(q) of Eq. 1.
+ *  - A free-flyer joint (body 0 only) has 7 q entries [p (3), quat (x,y,z,w)]
+ *    and 6 velocity entries, the body-frame twist [w_b; v_b]; qdd is its time
+ *    derivative. Revolute joints have one entry each.
+ *  - Batched arrays are FP32, structure-of-arrays, entry-major: element
+ *    (entry k, instance b) lives at ptr[k * ld + b], ld >= B. All batched
+ *    pointers are DEVICE pointers, caller-owned, 4-byte aligned.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*,
+ *    NULL = legacy default stream) and never synchronise. Argument errors are
+ *    reported before anything is launched. B == 0 is a no-op returning
+ *    FRAX_OK. Outputs are undefined after an error.
+ *  - The library never allocates device memory in these calls; the model
+ *    travels to the GPU inside each launch's parameter block.
+ *  - Thread safety: a model handle may be used from several threads at once;
+ *    frax_last_error() is thread-local.
+ */
+#ifndef FRAX_H
+#define FRAX_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FRAX_API __attribute__((visibility("default")))
+#else
+#define FRAX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct frax_model_s* frax_model_t;
+
+typedef enum {
+  FRAX_OK = 0,
+  FRAX_EINVAL = 1,    /* bad argument; frax_last_error() says which        */
+  FRAX_ECUDA = 2,     /* a CUDA runtime call failed                         */
+  FRAX_ENOMEM = 3,    /* host or device allocation failed / budget exceeded */
+  FRAX_ETIMEOUT = 4,  /* a bounded device or host wait ran out              */
+  FRAX_EBUSY = 5,     /* resource still has work in flight                  */
+  FRAX_EINTERNAL = 6
+} frax_status;
+
+enum { FRAX_JOINT_REVOLUTE = 0, FRAX_JOINT_FREE = 1 };
+enum { FRAX_MAX_BODIES = 64, FRAX_MAX_FRAMES = 8 };
+
+/*
+ * frax_model_create — build a model from a parent array (topological:
+ * parent[i] < i, -1 = world; the ancestor structure U of Sec. III), joint
+ * types, joint axes, joint placements and body inertias (Table III's S and I).
+ * Host-only: validates, derives the tree structure, and packs an FP32 image
+ * from the FP64 inputs. No CUDA call is made.
+ *   n_bodies    1..FRAX_MAX_BODIES
+ *   parent      [n] int32, parent[i] in [-1, i-1]
+ *   joint_type  [n] int32, FRAX_JOINT_REVOLUTE, or FRAX_JOINT_FREE for body 0
+ *               (whose parent must be -1)
+ *   axis        [n*3] unit joint axis in the joint frame (ignored for FREE)
+ *   placement   [n*12] joint frame in the parent body frame: R (row-major,
+ *               joint->parent, orthonormal) then p
+ *   inertia     [n*10] mass m > 0, COM c (3, body frame), rotational inertia
+ *               about the COM (xx, yy, zz, xy, xz, yz), positive definite
+ *   gravity     [3] world gravity, e.g. {0, 0, -9.81}
+ *   out         receives the handle (owned by the caller; frax_model_destroy)
+ * Errors: FRAX_EINVAL with a message naming the offending body.
+ */
+FRAX_API frax_status frax_model_create(int n_bodies, const int32_t* parent, const int32_t* joint_type,
+                              const double* axis, const double* placement, const double* inertia,
+                              const double* gravity, frax_model_t* out);
+FRAX_API frax_status frax_model_destroy(frax_model_t model);
+/* nq, nv, n_bodies of the model (any pointer may be NULL). */
+FRAX_API frax_status frax_model_dims(frax_model_t model, int* nq, int* nv, int* n_bodies);
+/* Kernel family the model dispatches to: 0 = serial chain (thread per
+ * instance, topology compiled in), 1 = general tree (thread per instance),
+ * 2 = the 30-body floating-base humanoid shape (branch-parallel warp). */
+FRAX_API frax_status frax_model_kind(frax_model_t model, int* kind);
+
+/*
+ * frax_fk — forward kinematics (Sec. II): ^0T_i(q) of every body.
+ *   q     [nq][ld] in
+ *   pose  [n_bodies*12][ld] out: per body R (row-major 9) then p (3), world
+ */
+FRAX_API frax_status frax_fk(frax_model_t model, int64_t B, int64_t ld, const float* q, float* pose,
+                    void* stream);
+
+/*
+ * frax_jacobian — geometric Jacobians of body frames (Sec. IV, "Jacobians"),
+ * fused with forward kinematics. J maps qd to [omega (world); d/dt p_k
+ * (world)] of frame body k's origin; columns of non-ancestor joints are 0.
+ *   n_frames    1..FRAX_MAX_FRAMES; frame_body [n_frames] HOST int32 bodies
+ *   pose        [n_bodies*12][ld] out, or NULL
+ *   J           [n_frames*6*nv][ld] out, entry (f, r, c) at (f*6 + r)*nv + c
+ */
+FRAX_API frax_status frax_jacobian(frax_model_t model, int64_t B, int64_t ld, const float* q, int n_frames,
+                          const int32_t* frame_body, float* pose, float* J, void* stream);
+
+/*
+ * frax_rnea — inverse dynamics, Eq. 1 with f = 0 (Algorithm 1's result):
+ * tau = M(q) qdd + c(q, qd) + g(q), by the recursive Newton-Euler algorithm.
+ *   q [nq][ld], qd [nv][ld], qdd [nv][ld] in (qdd == NULL gives the bias
+ *   forces c + g); tau [nv][ld] out.
+ */
+FRAX_API frax_status frax_rnea(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                      const float* qdd, float* tau, void* stream);
+
+/*
+ * frax_crba — the mass matrix M(q) (Algorithm 2's result) by the
+ * composite-rigid-body algorithm, and optionally its factorisation
+ * M = L^T D L (L unit lower triangular, zero fill-in in the ancestor
+ * pattern), the Cholesky-style factor of the Sec. VI footnote.
+ *   q  [nq][ld] in
+ *   M  [nv*nv][ld] out, row-major, full (symmetric); may be NULL if LD given
+ *   LD [nv*(nv+1)/2][ld] out or NULL: packed lower triangle row-major,
+ *      entry (i, j<=i) at i*(i+1)/2 + j; D_i on the diagonal, L_ij below.
+ */
+FRAX_API frax_status frax_crba(frax_model_t model, int64_t B, int64_t ld, const float* q, float* M,
+                      float* LD, void* stream);
+
+/*
+ * frax_aba — forward dynamics, Eq. 2 with f = 0: qdd = M^-1 (tau - c - g),
+ * by the articulated-body algorithm (O(n); named future work in Sec. VI).
+ *   q [nq][ld], qd [nv][ld], tau [nv][ld] in; qdd [nv][ld] out.
+ */
+FRAX_API frax_status frax_aba(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                     const float* tau, float* qdd, void* stream);
+
+/*
+ * frax_rnea_vjp — reverse-mode derivative of Eq. 1 (analytic RNEA
+ * derivatives, Sec. VI future work). Given gbar (adjoint of tau):
+ *   qbar   = (dtau/dq)^T gbar     [nq][ld] (ambient layout: a free-flyer
+ *            root gets R v_bar in its position slots and 2 Q(quat) w_bar in
+ *            its quaternion slots, tangent to the unit sphere)
+ *   qdbar  = (dtau/dqd)^T gbar    [nv][ld]
+ *   qddbar = M gbar               [nv][ld]  (may be NULL)
+ * Spatial velocities are recomputed inside the call, never stored.
+ */
+FRAX_API frax_status frax_rnea_vjp(frax_model_t model, int64_t B, int64_t ld, const float* q,
+                          const float* qd, const float* qdd, const float* gbar, float* qbar,
+                          float* qdbar, float* qddbar, void* stream);
+
+/*
+ * frax_aba_vjp — reverse-mode derivative of Eq. 2 at qdd = ABA(q, qd, tau)
+ * (qdd is passed in, as saved by the forward call). With w = M^-1 gbar:
+ *   taubar = w, qbar = -(dtau/dq)^T w (ambient layout), qdbar = -(dtau/dqd)^T w.
+ */
+FRAX_API frax_status frax_aba_vjp(frax_model_t model, int64_t B, int64_t ld, const float* q,
+                         const float* qd, const float* tau, const float* qdd, const float* gbar,
+                         float* qbar, float* qdbar, float* taubar, void* stream);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+FRAX_API const char* frax_last_error(void);
+
+/* Library version string. */
+FRAX_API const char* frax_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRAX_H */

@@ -1,0 +1,16 @@
+"""GB300-native batched rigid-body kinematics and dynamics (sm_103a CUDA).
+
+The public entry points mirror the C ABI in include/frax.h:
+frax_model_create, frax_fk, frax_jacobian, frax_rnea, frax_crba, frax_aba,
+frax_rnea_vjp, frax_aba_vjp, plus the autograd wrappers RneaFn / AbaFn.
+"""
+
+from .frax import (AbaFn, FraxError, Model, RneaFn, aba, frax_aba, frax_aba_vjp, frax_crba, frax_fk,
+                   frax_jacobian, frax_last_error, frax_model_create, frax_rnea, frax_rnea_vjp, frax_version,
+                   lib, rnea)
+
+__all__ = [
+    "AbaFn", "FraxError", "Model", "RneaFn", "aba", "frax_aba", "frax_aba_vjp", "frax_crba", "frax_fk",
+    "frax_jacobian", "frax_last_error", "frax_model_create", "frax_rnea", "frax_rnea_vjp", "frax_version",
+    "lib", "rnea",
+]

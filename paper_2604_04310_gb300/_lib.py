@@ -1,0 +1,55 @@
+"""ctypes declarations of libfrax.so (the C ABI in include/frax.h).
+
+Loading fails loudly when the library has not been built: there is no
+fallback implementation.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfrax.so")
+
+c_f = ctypes.POINTER(ctypes.c_float)
+c_i32 = ctypes.POINTER(ctypes.c_int32)
+c_d = ctypes.POINTER(ctypes.c_double)
+c_int = ctypes.c_int
+c_i64 = ctypes.c_int64
+c_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "frax_model_create": (c_int, [c_int, c_i32, c_i32, c_d, c_d, c_d, c_d, ctypes.POINTER(c_vp)]),
+    "frax_model_destroy": (c_int, [c_vp]),
+    "frax_model_dims": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "frax_model_kind": (c_int, [c_vp, ctypes.POINTER(c_int)]),
+    "frax_fk": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
+    "frax_jacobian": (c_int, [c_vp, c_i64, c_i64, c_vp, c_int, c_i32, c_vp, c_vp, c_vp]),
+    "frax_rnea": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_crba": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
+    "frax_aba": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_rnea_vjp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_aba_vjp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_last_error": (ctypes.c_char_p, []),
+    "frax_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libfrax.so once and declares every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build it first (python -m paper_2604_04310_gb300.build). "
+            "This package has no CPU or Python fallback.")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,205 @@
+// C ABI: argument validation, model handles, kernel dispatch.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <new>
+#include <string>
+
+#include "../../include/frax.h"
+#include "launch.h"
+#include "model.h"
+
+struct frax_model_s {
+  frax::HostModel m;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+frax_status fail(frax_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+frax_status ok() {
+  g_last_error.clear();
+  return FRAX_OK;
+}
+
+frax_status check_batch(frax_model_t model, int64_t B, int64_t ld, const char* fn) {
+  if (!model) return fail(FRAX_EINVAL, std::string(fn) + ": model is NULL");
+  if (B < 0) return fail(FRAX_EINVAL, std::string(fn) + ": B must be >= 0");
+  if (B > 0 && ld < B) return fail(FRAX_EINVAL, std::string(fn) + ": ld must be >= B");
+  if (B > (int64_t(1) << 40)) return fail(FRAX_EINVAL, std::string(fn) + ": B too large");
+  return FRAX_OK;
+}
+
+frax_status need(const void* p, const char* fn, const char* name) {
+  if (!p) return fail(FRAX_EINVAL, std::string(fn) + ": " + name + " is NULL");
+  return FRAX_OK;
+}
+
+frax_status dispatch(frax_model_t model, frax::Op op, const frax::OpArgs& a, const char* fn) {
+  const frax::HostModel& m = model->m;
+  cudaError_t e;
+  if (m.kind == frax::kKindChain)
+    e = frax::launch_chain7(m, op, a);
+  else if (m.nb <= 32)
+    e = frax::launch_tree32(m, op, a);
+  else
+    e = frax::launch_tree64(m, op, a);
+  if (e != cudaSuccess)
+    return fail(FRAX_ECUDA, std::string(fn) + ": kernel launch failed: " + cudaGetErrorString(e));
+  return ok();
+}
+
+#define FRAX_TRY(expr)                    \
+  do {                                    \
+    frax_status s_ = (expr);              \
+    if (s_ != FRAX_OK) return s_;         \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+const char* frax_last_error(void) { return g_last_error.c_str(); }
+const char* frax_version(void) { return "frax-gb300 0.1 (sm_103a)"; }
+
+frax_status frax_model_create(int n_bodies, const int32_t* parent, const int32_t* joint_type,
+                              const double* axis, const double* placement, const double* inertia,
+                              const double* gravity, frax_model_t* out) {
+  if (!out) return fail(FRAX_EINVAL, "frax_model_create: out is NULL");
+  *out = nullptr;
+  frax_model_s* h = new (std::nothrow) frax_model_s;
+  if (!h) return fail(FRAX_ENOMEM, "frax_model_create: out of host memory");
+  std::string err =
+      frax::build_model(n_bodies, parent, joint_type, axis, placement, inertia, gravity, &h->m);
+  if (!err.empty()) {
+    delete h;
+    return fail(FRAX_EINVAL, "frax_model_create: " + err);
+  }
+  *out = h;
+  return ok();
+}
+
+frax_status frax_model_destroy(frax_model_t model) {
+  delete model;
+  return ok();
+}
+
+frax_status frax_model_dims(frax_model_t model, int* nq, int* nv, int* n_bodies) {
+  if (!model) return fail(FRAX_EINVAL, "frax_model_dims: model is NULL");
+  if (nq) *nq = model->m.nq;
+  if (nv) *nv = model->m.nv;
+  if (n_bodies) *n_bodies = model->m.nb;
+  return ok();
+}
+
+frax_status frax_model_kind(frax_model_t model, int* kind) {
+  if (!model || !kind) return fail(FRAX_EINVAL, "frax_model_kind: NULL argument");
+  *kind = model->m.kind;
+  return ok();
+}
+
+frax_status frax_fk(frax_model_t model, int64_t B, int64_t ld, const float* q, float* pose, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_fk"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_fk", "q"));
+  FRAX_TRY(need(pose, "frax_fk", "pose"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.out0 = pose; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpFk, a, "frax_fk");
+}
+
+frax_status frax_jacobian(frax_model_t model, int64_t B, int64_t ld, const float* q, int n_frames,
+                          const int32_t* frame_body, float* pose, float* J, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_jacobian"));
+  if (n_frames < 1 || n_frames > FRAX_MAX_FRAMES)
+    return fail(FRAX_EINVAL, "frax_jacobian: n_frames must be in [1, 8]");
+  FRAX_TRY(need(frame_body, "frax_jacobian", "frame_body"));
+  frax::OpArgs a;
+  a.frames.n = n_frames;
+  for (int f = 0; f < n_frames; ++f) {
+    if (frame_body[f] < 0 || frame_body[f] >= model->m.nb)
+      return fail(FRAX_EINVAL, "frax_jacobian: frame body index out of range");
+    a.frames.body[f] = frame_body[f];
+  }
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_jacobian", "q"));
+  FRAX_TRY(need(J, "frax_jacobian", "J"));
+  a.B = B; a.ld = ld; a.q = q; a.out0 = pose; a.out1 = J; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpJac, a, "frax_jacobian");
+}
+
+frax_status frax_rnea(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                      const float* qdd, float* tau, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_rnea"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_rnea", "q"));
+  FRAX_TRY(need(qd, "frax_rnea", "qd"));
+  FRAX_TRY(need(tau, "frax_rnea", "tau"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.qdd = qdd; a.out0 = tau;
+  a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpRnea, a, "frax_rnea");
+}
+
+frax_status frax_crba(frax_model_t model, int64_t B, int64_t ld, const float* q, float* M, float* LD,
+                      void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_crba"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_crba", "q"));
+  if (!M && !LD) return fail(FRAX_EINVAL, "frax_crba: M and LD are both NULL");
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.out0 = M; a.out1 = LD; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpCrba, a, "frax_crba");
+}
+
+frax_status frax_aba(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                     const float* tau, float* qdd, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_aba"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_aba", "q"));
+  FRAX_TRY(need(qd, "frax_aba", "qd"));
+  FRAX_TRY(need(tau, "frax_aba", "tau"));
+  FRAX_TRY(need(qdd, "frax_aba", "qdd"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.tau = tau; a.out0 = qdd;
+  a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpAba, a, "frax_aba");
+}
+
+frax_status frax_rnea_vjp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                          const float* qdd, const float* gbar, float* qbar, float* qdbar, float* qddbar,
+                          void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_rnea_vjp"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_rnea_vjp", "q"));
+  FRAX_TRY(need(qd, "frax_rnea_vjp", "qd"));
+  FRAX_TRY(need(qdd, "frax_rnea_vjp", "qdd"));
+  FRAX_TRY(need(gbar, "frax_rnea_vjp", "gbar"));
+  if (!qbar && !qdbar && !qddbar) return fail(FRAX_EINVAL, "frax_rnea_vjp: all outputs are NULL");
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.qdd = qdd; a.gbar = gbar;
+  a.out0 = qbar; a.out1 = qdbar; a.out2 = qddbar; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpRneaVjp, a, "frax_rnea_vjp");
+}
+
+frax_status frax_aba_vjp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                         const float* tau, const float* qdd, const float* gbar, float* qbar, float* qdbar,
+                         float* taubar, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_aba_vjp"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_aba_vjp", "q"));
+  FRAX_TRY(need(qd, "frax_aba_vjp", "qd"));
+  FRAX_TRY(need(qdd, "frax_aba_vjp", "qdd"));
+  FRAX_TRY(need(gbar, "frax_aba_vjp", "gbar"));
+  if (!qbar && !qdbar && !taubar) return fail(FRAX_EINVAL, "frax_aba_vjp: all outputs are NULL");
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.tau = tau; a.qdd = qdd; a.gbar = gbar;
+  a.out0 = qbar; a.out1 = qdbar; a.out2 = taubar; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpAbaVjp, a, "frax_aba_vjp");
+}
+
+}  // extern "C"

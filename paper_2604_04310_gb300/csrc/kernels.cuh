@@ -1,0 +1,96 @@
+// __global__ wrappers: one thread per instance, 128-thread blocks, the model
+// image as a __grid_constant__ parameter (read through the constant bank).
+#pragma once
+#include "dyn.cuh"
+#include "launch.h"
+
+namespace frax {
+
+#define FRAX_TID()                                                     \
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; \
+  if (b >= B) return;                                                \
+  const Col col{ld, b};
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_fk(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                int64_t ld, const float* q, float* pose,
+                                                const __grid_constant__ Frames fr, float* J) {
+  FRAX_TID();
+  fk_one<T>(M, q, pose, fr, J, col);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_rnea(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                  int64_t ld, const float* q, const float* qd,
+                                                  const float* qdd, float* tau) {
+  FRAX_TID();
+  rnea_one<T>(M, q, qd, qdd, tau, col);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_crba(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                  int64_t ld, const float* q, float* Mout, float* LD) {
+  FRAX_TID();
+  crba_one<T>(M, q, Mout, LD, col);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_aba(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                 int64_t ld, const float* q, const float* qd,
+                                                 const float* tau, float* qdd) {
+  FRAX_TID();
+  aba_one<T>(M, q, qd, tau, qdd, col);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_rnea_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                      int64_t ld, const float* q, const float* qd,
+                                                      const float* qdd, const float* gbar, float* qbar,
+                                                      float* qdbar, float* qddbar) {
+  FRAX_TID();
+  rnea_vjp_one<T>(M, q, qd, qdd, gbar, qbar, qdbar, qddbar, col);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_aba_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                     int64_t ld, const float* q, const float* qd,
+                                                     const float* tau, const float* qdd, const float* gbar,
+                                                     float* qbar, float* qdbar, float* taubar) {
+  FRAX_TID();
+  aba_vjp_one<T>(M, q, qd, tau, qdd, gbar, qbar, qdbar, taubar, col);
+}
+
+template <class T>
+cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a) {
+  const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock)), block(kBlock);
+  Frames fr{a.frames.n, {0}};
+  for (int k = 0; k < 8; ++k) fr.body[k] = a.frames.body[k];
+  switch (op) {
+    case kOpFk:
+    case kOpJac:
+      k_fk<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, fr, a.out1);
+      break;
+    case kOpRnea:
+      k_rnea<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.out0);
+      break;
+    case kOpCrba:
+      k_crba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
+      break;
+    case kOpAba:
+      k_aba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.out0);
+      break;
+    case kOpRneaVjp:
+      k_rnea_vjp<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1,
+                                                  a.out2);
+      break;
+    case kOpAbaVjp:
+      k_aba_vjp<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.qdd, a.gbar, a.out0,
+                                                 a.out1, a.out2);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace frax

@@ -1,0 +1,39 @@
+// Internal launcher interface between the C ABI (api.cu) and the kernel
+// translation units (one per topology family, compiled in parallel).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "model.h"
+
+namespace frax {
+
+enum Op { kOpFk = 0, kOpJac, kOpRnea, kOpCrba, kOpAba, kOpRneaVjp, kOpAbaVjp, kOpCount };
+
+struct FramesArg {
+  int n;
+  int body[8];
+};
+
+struct OpArgs {
+  int64_t B = 0, ld = 0;
+  const float* q = nullptr;
+  const float* qd = nullptr;
+  const float* qdd = nullptr;
+  const float* tau = nullptr;
+  const float* gbar = nullptr;
+  float* out0 = nullptr;  // pose / tau / M / qdd / qbar
+  float* out1 = nullptr;  // J / LD / qdbar
+  float* out2 = nullptr;  // qddbar / taubar
+  FramesArg frames{0, {0}};
+  cudaStream_t stream = nullptr;
+};
+
+// Each returns the launch status (cudaGetLastError after the launch).
+cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a);
+cudaError_t launch_tree32(const HostModel& m, Op op, const OpArgs& a);
+cudaError_t launch_tree64(const HostModel& m, Op op, const OpArgs& a);
+
+constexpr int kBlock = 128;
+
+}  // namespace frax

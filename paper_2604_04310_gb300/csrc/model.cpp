@@ -1,0 +1,198 @@
+// Model validation, derived tree structure and FP32 image packing (host only).
+#include "model.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+namespace frax {
+namespace {
+
+struct M3 {
+  double a[9];
+  double operator()(int r, int c) const { return a[3 * r + c]; }
+  double& operator()(int r, int c) { return a[3 * r + c]; }
+};
+
+M3 mul(const M3& A, const M3& B) {
+  M3 C{};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += A(r, k) * B(k, c);
+      C(r, c) = s;
+    }
+  return C;
+}
+
+M3 transpose(const M3& A) {
+  M3 T{};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) T(r, c) = A(c, r);
+  return T;
+}
+
+M3 identity() {
+  M3 I{};
+  I(0, 0) = I(1, 1) = I(2, 2) = 1;
+  return I;
+}
+
+// A rotation Q with Q e_z = a (a unit): the internal frame of a revolute body.
+M3 frame_with_z(const double a[3]) {
+  double h[3] = {1, 0, 0};
+  if (std::fabs(a[0]) > 0.9) { h[0] = 0; h[1] = 1; }
+  double d = h[0] * a[0] + h[1] * a[1] + h[2] * a[2];
+  double x[3] = {h[0] - d * a[0], h[1] - d * a[1], h[2] - d * a[2]};
+  double nx = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  for (double& v : x) v /= nx;
+  double y[3] = {a[1] * x[2] - a[2] * x[1], a[2] * x[0] - a[0] * x[2], a[0] * x[1] - a[1] * x[0]};
+  M3 Q{};
+  for (int r = 0; r < 3; ++r) {
+    Q(r, 0) = x[r];
+    Q(r, 1) = y[r];
+    Q(r, 2) = a[r];
+  }
+  return Q;
+}
+
+bool finite_all(const double* p, int n) {
+  for (int k = 0; k < n; ++k)
+    if (!std::isfinite(p[k])) return false;
+  return true;
+}
+
+std::string fmt(const char* f, int i) {
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), f, i);
+  return buf;
+}
+
+}  // namespace
+
+std::string build_model(int n, const int32_t* parent, const int32_t* joint_type, const double* axis,
+                        const double* placement, const double* inertia, const double* gravity,
+                        HostModel* out) {
+  if (n < 1 || n > kMaxBodies) return fmt("n_bodies must be in [1, 64], got %d", n);
+  if (!parent || !joint_type || !axis || !placement || !inertia || !gravity || !out)
+    return "null argument to frax_model_create";
+  if (!finite_all(gravity, 3)) return "gravity is not finite";
+  HostModel m;
+  m.nb = n;
+  m.parent.assign(parent, parent + n);
+  for (int i = 0; i < n; ++i) {
+    if (parent[i] < -1 || parent[i] >= i)
+      return fmt("body %d: parent must be in [-1, i-1] (topological order)", i);
+    if (joint_type[i] != 0 && joint_type[i] != 1) return fmt("body %d: unknown joint type", i);
+    if (joint_type[i] == 1 && (i != 0 || parent[i] != -1))
+      return fmt("body %d: a free-flyer joint is only allowed at body 0 with parent -1", i);
+    if (!finite_all(axis + 3 * i, 3) || !finite_all(placement + 12 * i, 12) ||
+        !finite_all(inertia + 10 * i, 10))
+      return fmt("body %d: non-finite parameter", i);
+  }
+  m.free_root = joint_type[0] == 1;
+  int nq = 0, nv = 0;
+  for (int i = 0; i < n; ++i) {
+    m.iq.push_back(nq);
+    m.iv.push_back(nv);
+    bool fr = joint_type[i] == 1;
+    nq += fr ? 7 : 1;
+    nv += fr ? 6 : 1;
+  }
+  m.nq = nq;
+  m.nv = nv;
+  m.dof_parent.assign(nv, -1);
+  m.anc.assign(n, 0);
+  m.depth.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    int k = parent[i];
+    m.anc[i] = (k >= 0 ? m.anc[k] : 0) | (uint64_t(1) << i);
+    m.depth[i] = k >= 0 ? m.depth[k] + 1 : 0;
+    if (joint_type[i] == 1) {
+      for (int d = 0; d < 6; ++d) m.dof_parent[m.iv[i] + d] = d - 1;
+    } else {
+      int last_parent_dof = k < 0 ? -1 : m.iv[k] + (joint_type[k] == 1 ? 5 : 0);
+      m.dof_parent[m.iv[i]] = last_parent_dof;
+    }
+  }
+  for (int k = 0; k < 3; ++k) m.gravity[k] = gravity[k];
+
+  std::vector<M3> Q(n);
+  for (int i = 0; i < n; ++i) {
+    if (joint_type[i] == 1) {
+      Q[i] = identity();
+      continue;
+    }
+    const double* a = axis + 3 * i;
+    double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    if (std::fabs(na - 1.0) > 1e-6) return fmt("body %d: joint axis is not a unit vector", i);
+    double au[3] = {a[0] / na, a[1] / na, a[2] / na};
+    Q[i] = frame_with_z(au);
+  }
+  m.bodies.resize(n);
+  for (int i = 0; i < n; ++i) {
+    M3 RT{};
+    for (int k = 0; k < 9; ++k) RT.a[k] = placement[12 * i + k];
+    M3 RtR = mul(transpose(RT), RT);
+    double err = 0, det = 0;
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) err = std::fmax(err, std::fabs(RtR(r, c) - (r == c ? 1.0 : 0.0)));
+    det = RT(0, 0) * (RT(1, 1) * RT(2, 2) - RT(1, 2) * RT(2, 1)) -
+          RT(0, 1) * (RT(1, 0) * RT(2, 2) - RT(1, 2) * RT(2, 0)) +
+          RT(0, 2) * (RT(1, 0) * RT(2, 1) - RT(1, 1) * RT(2, 0));
+    if (err > 1e-6 || det < 0) return fmt("body %d: placement rotation is not a proper rotation", i);
+    const double* pT = placement + 12 * i + 9;
+    const double* in = inertia + 10 * i;
+    double mass = in[0];
+    if (!(mass > 0)) return fmt("body %d: mass must be positive", i);
+    M3 Ic{};
+    Ic(0, 0) = in[4]; Ic(1, 1) = in[5]; Ic(2, 2) = in[6];
+    Ic(0, 1) = Ic(1, 0) = in[7];
+    Ic(0, 2) = Ic(2, 0) = in[8];
+    Ic(1, 2) = Ic(2, 1) = in[9];
+    // positive definiteness by leading principal minors
+    double d1 = Ic(0, 0), d2 = Ic(0, 0) * Ic(1, 1) - Ic(0, 1) * Ic(1, 0);
+    double d3 = Ic(0, 0) * (Ic(1, 1) * Ic(2, 2) - Ic(1, 2) * Ic(2, 1)) -
+                Ic(0, 1) * (Ic(1, 0) * Ic(2, 2) - Ic(1, 2) * Ic(2, 0)) +
+                Ic(0, 2) * (Ic(1, 0) * Ic(2, 1) - Ic(1, 1) * Ic(2, 0));
+    if (!(d1 > 0 && d2 > 0 && d3 > 0))
+      return fmt("body %d: rotational inertia is not positive definite", i);
+
+    BodyImage& b = m.bodies[i];
+    int k = parent[i];
+    M3 Qp = k >= 0 ? Q[k] : identity();
+    M3 Rint = joint_type[i] == 1 ? RT : mul(mul(transpose(Qp), RT), Q[i]);
+    double pint[3];
+    for (int r = 0; r < 3; ++r) {
+      pint[r] = joint_type[i] == 1 ? pT[r]
+                                   : Qp(0, r) * pT[0] + Qp(1, r) * pT[1] + Qp(2, r) * pT[2];
+    }
+    for (int t = 0; t < 9; ++t) b.R[t] = static_cast<float>(Rint.a[t]);
+    for (int t = 0; t < 3; ++t) b.p[t] = static_cast<float>(pint[t]);
+    for (int t = 0; t < 9; ++t) b.Q[t] = static_cast<float>(Q[i].a[t]);
+    // inertia in internal coordinates, about the body origin
+    const double* c = in + 1;
+    double ci[3];
+    for (int r = 0; r < 3; ++r) ci[r] = Q[i](0, r) * c[0] + Q[i](1, r) * c[1] + Q[i](2, r) * c[2];
+    M3 Ici = mul(mul(transpose(Q[i]), Ic), Q[i]);
+    double c2 = ci[0] * ci[0] + ci[1] * ci[1] + ci[2] * ci[2];
+    M3 Io{};
+    for (int r = 0; r < 3; ++r)
+      for (int s = 0; s < 3; ++s) Io(r, s) = Ici(r, s) + mass * ((r == s ? c2 : 0.0) - ci[r] * ci[s]);
+    b.m = static_cast<float>(mass);
+    for (int t = 0; t < 3; ++t) b.h[t] = static_cast<float>(mass * ci[t]);
+    b.I[0] = static_cast<float>(Io(0, 0));
+    b.I[1] = static_cast<float>(Io(1, 1));
+    b.I[2] = static_cast<float>(Io(2, 2));
+    b.I[3] = static_cast<float>(Io(0, 1));
+    b.I[4] = static_cast<float>(Io(0, 2));
+    b.I[5] = static_cast<float>(Io(1, 2));
+  }
+  bool chain = !m.free_root;
+  for (int i = 0; i < n; ++i) chain = chain && parent[i] == i - 1;
+  m.kind = (chain && n == 7) ? kKindChain : kKindTree;
+  *out = std::move(m);
+  return "";
+}
+
+}  // namespace frax

@@ -1,0 +1,261 @@
+// Device spatial algebra, FP32, one instance per thread: 3-vectors, 6-D
+// spatial vectors [angular; linear], compact rigid-body inertias and
+// articulated (general symmetric 6x6) inertias, and the joint transforms in
+// the internal frames of model_image.h (joint axis = local z).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "model_image.h"
+
+namespace frax {
+
+#define FD __host__ __device__ __forceinline__
+
+struct V3 {
+  float x, y, z;
+};
+struct SV {
+  V3 w, v;  // motion: [omega; v]   force: [n; f]
+};
+
+FD V3 mk(float x, float y, float z) { return V3{x, y, z}; }
+FD V3 operator+(V3 a, V3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+FD V3 operator-(V3 a, V3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+FD V3 operator-(V3 a) { return mk(-a.x, -a.y, -a.z); }
+FD V3 operator*(float s, V3 a) { return mk(s * a.x, s * a.y, s * a.z); }
+FD float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+FD V3 cross(V3 a, V3 b) {
+  return mk(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
+}
+FD SV operator+(const SV& a, const SV& b) { return SV{a.w + b.w, a.v + b.v}; }
+FD SV operator-(const SV& a, const SV& b) { return SV{a.w - b.w, a.v - b.v}; }
+FD SV operator*(float s, const SV& a) { return SV{s * a.w, s * a.v}; }
+FD float dot(const SV& a, const SV& b) { return dot(a.w, b.w) + dot(a.v, b.v); }
+FD SV szero() { return SV{mk(0, 0, 0), mk(0, 0, 0)}; }
+
+// motion x motion (Table III's x)
+FD SV crm(const SV& a, const SV& b) { return SV{cross(a.w, b.w), cross(a.w, b.v) + cross(a.v, b.w)}; }
+// motion x* force (Table III's x*)
+FD SV crf(const SV& a, const SV& f) { return SV{cross(a.w, f.w) + cross(a.v, f.v), cross(a.w, f.v)}; }
+
+// --- rotations --------------------------------------------------------------
+FD V3 rot(const float* R, V3 a) {  // R a, R row-major
+  return mk(fmaf(R[0], a.x, fmaf(R[1], a.y, R[2] * a.z)), fmaf(R[3], a.x, fmaf(R[4], a.y, R[5] * a.z)),
+            fmaf(R[6], a.x, fmaf(R[7], a.y, R[8] * a.z)));
+}
+FD V3 rotT(const float* R, V3 a) {  // R^T a
+  return mk(fmaf(R[0], a.x, fmaf(R[3], a.y, R[6] * a.z)), fmaf(R[1], a.x, fmaf(R[4], a.y, R[7] * a.z)),
+            fmaf(R[2], a.x, fmaf(R[5], a.y, R[8] * a.z)));
+}
+// Rot_z(q) a and Rot_z(q)^T a with (c, s) = (cos q, sin q)
+FD V3 rotz(float c, float s, V3 a) { return mk(fmaf(c, a.x, -s * a.y), fmaf(s, a.x, c * a.y), a.z); }
+FD V3 rotzT(float c, float s, V3 a) { return mk(fmaf(c, a.x, s * a.y), fmaf(-s, a.x, c * a.y), a.z); }
+
+// rotation matrix of a unit quaternion (x, y, z, w), row-major
+FD void quat_to_R(float x, float y, float z, float w, float* R) {
+  float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z, wx = w * x,
+        wy = w * y, wz = w * z;
+  R[0] = 1.f - 2.f * (yy + zz); R[1] = 2.f * (xy - wz);       R[2] = 2.f * (xz + wy);
+  R[3] = 2.f * (xy + wz);       R[4] = 1.f - 2.f * (xx + zz); R[5] = 2.f * (yz - wx);
+  R[6] = 2.f * (xz - wy);       R[7] = 2.f * (yz + wx);       R[8] = 1.f - 2.f * (xx + yy);
+}
+// C = A B (3x3 row-major)
+FD void mat_mul(const float* A, const float* B, float* C) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      C[3 * r + c] = fmaf(A[3 * r], B[c], fmaf(A[3 * r + 1], B[3 + c], A[3 * r + 2] * B[6 + c]));
+}
+
+// --- joint transforms (internal frames) -------------------------------------
+// A revolute body i sits at ^parent'T_i' = (R Rot_z(q), p) with R, p constant.
+// Motion vectors: parent' -> child' coordinates.
+FD SV mot_in(const BodyImage& b, float c, float s, const SV& m) {
+  V3 p = mk(b.p[0], b.p[1], b.p[2]);
+  return SV{rotzT(c, s, rotT(b.R, m.w)), rotzT(c, s, rotT(b.R, m.v - cross(p, m.w)))};
+}
+// Force vectors: child' -> parent' coordinates (the transpose of mot_in).
+FD SV frc_out(const BodyImage& b, float c, float s, const SV& f) {
+  V3 p = mk(b.p[0], b.p[1], b.p[2]);
+  V3 fl = rot(b.R, rotz(c, s, f.v));
+  return SV{rot(b.R, rotz(c, s, f.w)) + cross(p, fl), fl};
+}
+// Motion vectors child' -> parent' (inverse of mot_in); used by adjoints.
+FD SV mot_out(const BodyImage& b, float c, float s, const SV& m) {
+  V3 p = mk(b.p[0], b.p[1], b.p[2]);
+  V3 w = rot(b.R, rotz(c, s, m.w));
+  return SV{w, rot(b.R, rotz(c, s, m.v)) + cross(p, w)};
+}
+
+// e x m and e x* f for e = [z; 0] (the revolute motion subspace)
+FD SV ez_crm(const SV& m) { return SV{mk(-m.w.y, m.w.x, 0.f), mk(-m.v.y, m.v.x, 0.f)}; }
+FD SV ez_crf(const SV& f) { return SV{mk(-f.w.y, f.w.x, 0.f), mk(-f.v.y, f.v.x, 0.f)}; }
+
+// --- compact rigid-body inertia (m, h = m c, I about the origin) -------------
+struct RBI {
+  float m;
+  V3 h;
+  float xx, yy, zz, xy, xz, yz;
+};
+FD RBI rbi_of(const BodyImage& b) {
+  return RBI{b.m, mk(b.h[0], b.h[1], b.h[2]), b.I[0], b.I[1], b.I[2], b.I[3], b.I[4], b.I[5]};
+}
+FD V3 symv(float xx, float yy, float zz, float xy, float xz, float yz, V3 a) {
+  return mk(fmaf(xx, a.x, fmaf(xy, a.y, xz * a.z)), fmaf(xy, a.x, fmaf(yy, a.y, yz * a.z)),
+            fmaf(xz, a.x, fmaf(yz, a.y, zz * a.z)));
+}
+FD SV rbi_mul(const RBI& I, const SV& v) {
+  return SV{symv(I.xx, I.yy, I.zz, I.xy, I.xz, I.yz, v.w) + cross(I.h, v.v),
+            I.m * v.v - cross(I.h, v.w)};
+}
+FD RBI rbi_add(const RBI& a, const RBI& b) {
+  return RBI{a.m + b.m, a.h + b.h, a.xx + b.xx, a.yy + b.yy, a.zz + b.zz,
+             a.xy + b.xy, a.xz + b.xz, a.yz + b.yz};
+}
+
+// symmetric S (6 entries) -> Rot_z S Rot_z^T
+FD void sym_rotz(float c, float s, float* S) {
+  float xx = S[0], yy = S[1], xy = S[3], xz = S[4], yz = S[5];
+  float cc = c * c, ss = s * s, cs = c * s;
+  S[0] = fmaf(cc, xx, fmaf(-2.f * cs, xy, ss * yy));
+  S[1] = fmaf(ss, xx, fmaf(2.f * cs, xy, cc * yy));
+  S[3] = fmaf(cs, xx - yy, (cc - ss) * xy);
+  S[4] = fmaf(c, xz, -s * yz);
+  S[5] = fmaf(s, xz, c * yz);
+}
+// symmetric S (xx yy zz xy xz yz) -> R S R^T, R row-major
+FD void sym_rot(const float* R, float* S) {
+  float T[9];  // T = S R^T
+  float Sf[9] = {S[0], S[3], S[4], S[3], S[1], S[5], S[4], S[5], S[2]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      T[3 * i + j] = fmaf(Sf[3 * i], R[3 * j], fmaf(Sf[3 * i + 1], R[3 * j + 1], Sf[3 * i + 2] * R[3 * j + 2]));
+  auto o = [&](int i, int j) {
+    return fmaf(R[3 * i], T[j], fmaf(R[3 * i + 1], T[3 + j], R[3 * i + 2] * T[6 + j]));
+  };
+  S[0] = o(0, 0); S[1] = o(1, 1); S[2] = o(2, 2); S[3] = o(0, 1); S[4] = o(0, 2); S[5] = o(1, 2);
+}
+// general M (row-major 9) -> R M R^T
+FD void gen_rot(const float* R, float* M) {
+  float T[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      T[3 * i + j] = fmaf(M[3 * i], R[3 * j], fmaf(M[3 * i + 1], R[3 * j + 1], M[3 * i + 2] * R[3 * j + 2]));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      M[3 * i + j] = fmaf(R[3 * i], T[j], fmaf(R[3 * i + 1], T[3 + j], R[3 * i + 2] * T[6 + j]));
+}
+// general M -> Rot_z M Rot_z^T
+FD void gen_rotz(float c, float s, float* M) {
+  // rows: A = Rot_z M
+  float a0 = fmaf(c, M[0], -s * M[3]), a1 = fmaf(c, M[1], -s * M[4]), a2 = fmaf(c, M[2], -s * M[5]);
+  float b0 = fmaf(s, M[0], c * M[3]), b1 = fmaf(s, M[1], c * M[4]), b2 = fmaf(s, M[2], c * M[5]);
+  float d0 = M[6], d1 = M[7], d2 = M[8];
+  // columns: A Rot_z^T
+  M[0] = fmaf(c, a0, -s * a1); M[1] = fmaf(s, a0, c * a1); M[2] = a2;
+  M[3] = fmaf(c, b0, -s * b1); M[4] = fmaf(s, b0, c * b1); M[5] = b2;
+  M[6] = fmaf(c, d0, -s * d1); M[7] = fmaf(s, d0, c * d1); M[8] = d2;
+}
+
+// Composite inertia of body i (child' coords) carried to parent' coords:
+// X^T I X for ^child X_parent = the revolute joint transform.
+FD RBI rbi_out(const BodyImage& b, float c, float s, const RBI& I) {
+  float S[6] = {I.xx, I.yy, I.zz, I.xy, I.xz, I.yz};
+  sym_rotz(c, s, S);
+  sym_rot(b.R, S);
+  V3 hr = rot(b.R, rotz(c, s, I.h));
+  V3 p = mk(b.p[0], b.p[1], b.p[2]);
+  V3 hn = hr + I.m * p;
+  float sh = dot(p, hn + hr);
+  // I' = I_r + (p.(h'+h_r)) 1 - (p h'^T + h_r p^T)
+  RBI o;
+  o.m = I.m;
+  o.h = hn;
+  o.xx = S[0] + sh - (p.x * hn.x + hr.x * p.x);
+  o.yy = S[1] + sh - (p.y * hn.y + hr.y * p.y);
+  o.zz = S[2] + sh - (p.z * hn.z + hr.z * p.z);
+  o.xy = S[3] - (p.x * hn.y + hr.x * p.y);
+  o.xz = S[4] - (p.x * hn.z + hr.x * p.z);
+  o.yz = S[5] - (p.y * hn.z + hr.y * p.z);
+  return o;
+}
+
+// --- articulated inertia: symmetric 6x6 [[A, B], [B^T, C]] -------------------
+struct AI {
+  float A[6];  // xx yy zz xy xz yz
+  float B[9];  // row-major
+  float C[6];  // xx yy zz xy xz yz
+};
+FD AI ai_of(const RBI& I) {
+  AI o;
+  o.A[0] = I.xx; o.A[1] = I.yy; o.A[2] = I.zz; o.A[3] = I.xy; o.A[4] = I.xz; o.A[5] = I.yz;
+  // B = [h]x
+  o.B[0] = 0.f;    o.B[1] = -I.h.z; o.B[2] = I.h.y;
+  o.B[3] = I.h.z;  o.B[4] = 0.f;    o.B[5] = -I.h.x;
+  o.B[6] = -I.h.y; o.B[7] = I.h.x;  o.B[8] = 0.f;
+  o.C[0] = I.m; o.C[1] = I.m; o.C[2] = I.m; o.C[3] = 0.f; o.C[4] = 0.f; o.C[5] = 0.f;
+  return o;
+}
+FD SV ai_mul(const AI& I, const SV& v) {
+  V3 n = symv(I.A[0], I.A[1], I.A[2], I.A[3], I.A[4], I.A[5], v.w) + rot(I.B, v.v);
+  V3 f = rotT(I.B, v.w) + symv(I.C[0], I.C[1], I.C[2], I.C[3], I.C[4], I.C[5], v.v);
+  return SV{n, f};
+}
+FD void ai_add(AI& a, const AI& b) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) { a.A[k] += b.A[k]; a.C[k] += b.C[k]; }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) a.B[k] += b.B[k];
+}
+// column z of the angular part: I e_z = [A[:,2]; B[2,:]^T]
+FD SV ai_col_z(const AI& I) { return SV{mk(I.A[4], I.A[5], I.A[2]), mk(I.B[6], I.B[7], I.B[8])}; }
+// I -= u u^T * k
+FD void ai_rank1_sub(AI& I, const SV& u, float k) {
+  float a[6] = {u.w.x, u.w.y, u.w.z, u.v.x, u.v.y, u.v.z};
+  const int si[6] = {0, 1, 2, 0, 0, 1}, sj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    I.A[t] = fmaf(-k * a[si[t]], a[sj[t]], I.A[t]);
+    I.C[t] = fmaf(-k * a[3 + si[t]], a[3 + sj[t]], I.C[t]);
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) I.B[3 * r + c] = fmaf(-k * a[r], a[3 + c], I.B[3 * r + c]);
+}
+// X^T I X for the revolute joint transform: rotate all blocks by
+// E = R Rot_z(q), then shift by p: C' = C, B' = B + P C, A' = A - (Y P + (Y P)^T)
+// with P = [p]x and Y = B + P C / 2.
+FD void ai_out(const BodyImage& b, float c, float s, AI& I) {
+  sym_rotz(c, s, I.A); sym_rot(b.R, I.A);
+  sym_rotz(c, s, I.C); sym_rot(b.R, I.C);
+  gen_rotz(c, s, I.B); gen_rot(b.R, I.B);
+  V3 p = mk(b.p[0], b.p[1], b.p[2]);
+  float Cf[9] = {I.C[0], I.C[3], I.C[4], I.C[3], I.C[1], I.C[5], I.C[4], I.C[5], I.C[2]};
+  float W[9];  // P C: column j = p x C[:, j]
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    V3 col = cross(p, mk(Cf[j], Cf[3 + j], Cf[6 + j]));
+    W[j] = col.x; W[3 + j] = col.y; W[6 + j] = col.z;
+  }
+  float Y[9], Z[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) { Y[k] = fmaf(0.5f, W[k], I.B[k]); I.B[k] += W[k]; }
+  // Z = Y P: row i = Y[i,:] x p
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    V3 r = cross(mk(Y[3 * i], Y[3 * i + 1], Y[3 * i + 2]), p);
+    Z[3 * i] = r.x; Z[3 * i + 1] = r.y; Z[3 * i + 2] = r.z;
+  }
+  I.A[0] -= 2.f * Z[0]; I.A[1] -= 2.f * Z[4]; I.A[2] -= 2.f * Z[8];
+  I.A[3] -= Z[1] + Z[3]; I.A[4] -= Z[2] + Z[6]; I.A[5] -= Z[5] + Z[7];
+}
+
+}  // namespace frax

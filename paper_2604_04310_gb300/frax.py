@@ -1,0 +1,262 @@
+"""Python binding of the C ABI: the same names as include/frax.h, argument
+marshalling only. Every computation runs in libfrax's CUDA kernels; torch
+supplies device memory and the current stream.
+
+Batched tensors are FP32 CUDA tensors in the ABI's structure-of-arrays
+layout: shape (entries, B) with stride (ld, 1), ld >= B, the same ld for
+every tensor of one call. Outputs are allocated with torch on the inputs'
+device unless passed in.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+OK = 0
+STATUS = {0: "FRAX_OK", 1: "FRAX_EINVAL", 2: "FRAX_ECUDA", 3: "FRAX_ENOMEM", 4: "FRAX_ETIMEOUT",
+          5: "FRAX_EBUSY", 6: "FRAX_EINTERNAL"}
+JOINT_REVOLUTE, JOINT_FREE = 0, 1
+MAX_FRAMES = 8
+
+
+class FraxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    return _lib.load()
+
+
+def _check(status):
+    if status != OK:
+        raise FraxError(status, lib().frax_last_error().decode())
+
+
+def frax_version() -> str:
+    return lib().frax_version().decode()
+
+
+def frax_last_error() -> str:
+    return lib().frax_last_error().decode()
+
+
+class Model:
+    """Owns a frax_model_t built by frax_model_create (host-only; the model
+    reaches the GPU inside every launch)."""
+
+    def __init__(self, parent, joint_type, axis, placement, inertia, gravity=(0.0, 0.0, -9.81), name="model"):
+        self.name = name
+        self.parent = np.ascontiguousarray(parent, dtype=np.int32)
+        self.joint_type = np.ascontiguousarray(joint_type, dtype=np.int32)
+        self.axis = np.ascontiguousarray(axis, dtype=np.float64).reshape(-1)
+        self.placement = np.ascontiguousarray(placement, dtype=np.float64).reshape(-1)
+        self.inertia = np.ascontiguousarray(inertia, dtype=np.float64).reshape(-1)
+        self.gravity = np.ascontiguousarray(gravity, dtype=np.float64).reshape(-1)
+        n = int(self.parent.shape[0])
+        if (self.joint_type.shape[0] != n or self.axis.shape[0] != 3 * n or self.placement.shape[0] != 12 * n
+                or self.inertia.shape[0] != 10 * n or self.gravity.shape[0] != 3):
+            raise FraxError(1, "frax_model_create: array sizes do not match n_bodies")
+        h = ctypes.c_void_p()
+        L = lib()
+        _check(L.frax_model_create(
+            n, self.parent.ctypes.data_as(_lib.c_i32), self.joint_type.ctypes.data_as(_lib.c_i32),
+            self.axis.ctypes.data_as(_lib.c_d), self.placement.ctypes.data_as(_lib.c_d),
+            self.inertia.ctypes.data_as(_lib.c_d), self.gravity.ctypes.data_as(_lib.c_d), ctypes.byref(h)))
+        self.handle = h
+        nq, nv, nb, kind = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(L.frax_model_dims(h, ctypes.byref(nq), ctypes.byref(nv), ctypes.byref(nb)))
+        _check(L.frax_model_kind(h, ctypes.byref(kind)))
+        self.nq, self.nv, self.n_bodies, self.kind = nq.value, nv.value, nb.value, kind.value
+
+    @classmethod
+    def from_robot(cls, robot):
+        """From any object with parent, joint_type, axis, placement, inertia,
+        gravity arrays (e.g. the seeded generators' RobotModel)."""
+        return cls(robot.parent, robot.joint_type, robot.axis, robot.placement, robot.inertia, robot.gravity,
+                   name=getattr(robot, "name", "model"))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().frax_model_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def frax_model_create(parent, joint_type, axis, placement, inertia, gravity=(0.0, 0.0, -9.81)) -> Model:
+    return Model(parent, joint_type, axis, placement, inertia, gravity)
+
+
+# ----------------------------------------------------------------- marshalling
+
+def _stream(t):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _soa(t, rows, name, ld=None, B=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
+        raise FraxError(1, f"{name} must be a float32 CUDA tensor")
+    if t.dim() != 2 or t.shape[0] != rows or (t.shape[0] > 1 and t.stride(1) != 1) or (
+            t.shape[0] > 0 and t.shape[1] > 1 and t.stride(1) != 1):
+        raise FraxError(1, f"{name} must have shape ({rows}, B) with unit stride along B")
+    if ld is not None and rows > 1 and t.stride(0) != ld:
+        raise FraxError(1, f"{name}: every tensor of one call must share the same leading dimension")
+    if B is not None and t.shape[1] != B:
+        raise FraxError(1, f"{name}: batch size {t.shape[1]} != {B}")
+    return t
+
+
+def _ld(t):
+    return t.stride(0) if t.shape[0] > 1 else t.shape[1]
+
+
+def _out(rows, like, ld, B):
+    if ld == B:
+        return torch.empty((rows, B), dtype=torch.float32, device=like.device)
+    return torch.empty((rows, ld), dtype=torch.float32, device=like.device)[:, :B]
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _prep(model, q, **others):
+    _soa(q, model.nq, "q")
+    B, ld = q.shape[1], _ld(q)
+    for name, (t, rows) in others.items():
+        _soa(t, rows, name, ld, B)
+    return B, ld
+
+
+# -------------------------------------------------------------------- the ABI
+
+def frax_fk(model: Model, q, pose=None):
+    """World pose of every body, (n_bodies*12, B): R row-major then p."""
+    B, ld = _prep(model, q, pose=(pose, 12 * model.n_bodies))
+    pose = _out(12 * model.n_bodies, q, ld, B) if pose is None else pose
+    _check(lib().frax_fk(model.handle, B, ld, _p(q), _p(pose), _stream(q)))
+    return pose
+
+
+def frax_jacobian(model: Model, q, frames, pose=None, J=None, want_pose=False):
+    """Frame Jacobians (n_frames*6*nv, B); returns (pose or None, J)."""
+    frames = np.ascontiguousarray(frames, dtype=np.int32).reshape(-1)
+    nf = int(frames.shape[0])
+    B, ld = _prep(model, q, pose=(pose, 12 * model.n_bodies), J=(J, nf * 6 * model.nv))
+    J = _out(nf * 6 * model.nv, q, ld, B) if J is None else J
+    if pose is None and want_pose:
+        pose = _out(12 * model.n_bodies, q, ld, B)
+    _check(lib().frax_jacobian(model.handle, B, ld, _p(q), nf, frames.ctypes.data_as(_lib.c_i32), _p(pose),
+                               _p(J), _stream(q)))
+    return pose, J
+
+
+def frax_rnea(model: Model, q, qd, qdd=None, tau=None):
+    """tau = M qdd + c + g (Eq. 1); qdd=None gives the bias forces c + g."""
+    B, ld = _prep(model, q, qd=(qd, model.nv), qdd=(qdd, model.nv), tau=(tau, model.nv))
+    tau = _out(model.nv, q, ld, B) if tau is None else tau
+    _check(lib().frax_rnea(model.handle, B, ld, _p(q), _p(qd), _p(qdd), _p(tau), _stream(q)))
+    return tau
+
+
+def frax_crba(model: Model, q, M=None, LD=None, want_M=True, want_LD=False):
+    """Mass matrix (nv*nv, B) and/or packed L^T D L factor (nv(nv+1)/2, B)."""
+    nv = model.nv
+    B, ld = _prep(model, q, M=(M, nv * nv), LD=(LD, nv * (nv + 1) // 2))
+    if M is None and want_M:
+        M = _out(nv * nv, q, ld, B)
+    if LD is None and want_LD:
+        LD = _out(nv * (nv + 1) // 2, q, ld, B)
+    _check(lib().frax_crba(model.handle, B, ld, _p(q), _p(M), _p(LD), _stream(q)))
+    return M, LD
+
+
+def frax_aba(model: Model, q, qd, tau, qdd=None):
+    """qdd = M^-1 (tau - c - g) (Eq. 2) by the articulated-body algorithm."""
+    B, ld = _prep(model, q, qd=(qd, model.nv), tau=(tau, model.nv), qdd=(qdd, model.nv))
+    qdd = _out(model.nv, q, ld, B) if qdd is None else qdd
+    _check(lib().frax_aba(model.handle, B, ld, _p(q), _p(qd), _p(tau), _p(qdd), _stream(q)))
+    return qdd
+
+
+def frax_rnea_vjp(model: Model, q, qd, qdd, gbar, qbar=None, qdbar=None, qddbar=None, want_qddbar=True):
+    """(dtau/dq)^T gbar [ambient, nq], (dtau/dqd)^T gbar, M gbar."""
+    nv = model.nv
+    B, ld = _prep(model, q, qd=(qd, nv), qdd=(qdd, nv), gbar=(gbar, nv), qbar=(qbar, model.nq),
+                  qdbar=(qdbar, nv), qddbar=(qddbar, nv))
+    qbar = _out(model.nq, q, ld, B) if qbar is None else qbar
+    qdbar = _out(nv, q, ld, B) if qdbar is None else qdbar
+    if qddbar is None and want_qddbar:
+        qddbar = _out(nv, q, ld, B)
+    _check(lib().frax_rnea_vjp(model.handle, B, ld, _p(q), _p(qd), _p(qdd), _p(gbar), _p(qbar), _p(qdbar),
+                               _p(qddbar), _stream(q)))
+    return qbar, qdbar, qddbar
+
+
+def frax_aba_vjp(model: Model, q, qd, tau, qdd, gbar, qbar=None, qdbar=None, taubar=None):
+    """VJP of Eq. 2 at qdd = ABA(q, qd, tau): (qbar [nq], qdbar, taubar = M^-1 gbar)."""
+    nv = model.nv
+    B, ld = _prep(model, q, qd=(qd, nv), tau=(tau, nv), qdd=(qdd, nv), gbar=(gbar, nv),
+                  qbar=(qbar, model.nq), qdbar=(qdbar, nv), taubar=(taubar, nv))
+    qbar = _out(model.nq, q, ld, B) if qbar is None else qbar
+    qdbar = _out(nv, q, ld, B) if qdbar is None else qdbar
+    taubar = _out(nv, q, ld, B) if taubar is None else taubar
+    _check(lib().frax_aba_vjp(model.handle, B, ld, _p(q), _p(qd), _p(tau), _p(qdd), _p(gbar), _p(qbar),
+                              _p(qdbar), _p(taubar), _stream(q)))
+    return qbar, qdbar, taubar
+
+
+# ------------------------------------------------------------- autograd wrappers
+
+class RneaFn(torch.autograd.Function):
+    """tau = RNEA(q, qd, qdd) with the hand-written adjoint as backward.
+    Saves only q, qd, qdd; the backward recomputes the sweeps."""
+
+    @staticmethod
+    def forward(ctx, model, q, qd, qdd):
+        ctx.model = model
+        ctx.save_for_backward(q, qd, qdd)
+        return frax_rnea(model, q, qd, qdd)
+
+    @staticmethod
+    def backward(ctx, gtau):
+        q, qd, qdd = ctx.saved_tensors
+        qbar, qdbar, qddbar = frax_rnea_vjp(ctx.model, q, qd, qdd, gtau.contiguous())
+        return None, qbar, qdbar, qddbar
+
+
+class AbaFn(torch.autograd.Function):
+    """qdd = ABA(q, qd, tau) with the hand-written adjoint as backward.
+    Saves q, qd, tau and qdd only (no per-body state)."""
+
+    @staticmethod
+    def forward(ctx, model, q, qd, tau):
+        qdd = frax_aba(model, q, qd, tau)
+        ctx.model = model
+        ctx.save_for_backward(q, qd, tau, qdd)
+        return qdd
+
+    @staticmethod
+    def backward(ctx, g):
+        q, qd, tau, qdd = ctx.saved_tensors
+        qbar, qdbar, taubar = frax_aba_vjp(ctx.model, q, qd, tau, qdd, g.contiguous())
+        return None, qbar, qdbar, taubar
+
+
+def rnea(model, q, qd, qdd):
+    return RneaFn.apply(model, q, qd, qdd)
+
+
+def aba(model, q, qd, tau):
+    return AbaFn.apply(model, q, qd, tau)

@@ -22,3 +22,19 @@ def models():
         "tree_a": gen.random_tree(101),
         "tree_b": gen.random_tree(117),
     }
+
+
+def pytest_collection_modifyitems(config, items):
+    """GPU tests need a CUDA device; without one (this CPU container) they are
+    skipped, never silently routed elsewhere."""
+    try:
+        import torch
+        has_cuda = torch.cuda.is_available()
+    except Exception:
+        has_cuda = False
+    if has_cuda:
+        return
+    skip = pytest.mark.skip(reason="no CUDA device")
+    for it in items:
+        if "gpu" in it.keywords:
+            it.add_marker(skip)

@@ -1,0 +1,234 @@
+"""GPU FP32 kernels vs the FP64 oracle, element by element, through the C ABI.
+
+Error metric (per instance, per output array): ||x_gpu - x_ref||_inf /
+max(||x_ref||_inf, 1e-12), max over instances. Tolerances: 1e-4 on poses,
+Jacobians, tau, M and its factor; 1e-3 on forward dynamics of the humanoid and
+on every gradient. Batch sizes span several 128-thread blocks with a ragged
+tail; full-size batches are checked on sampled instances."""
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import paper_2604_04310_gb300 as fx
+from oracle import derivatives as dv
+from oracle import rbd
+from tests.gpu_util import dev, host, states
+from tests.pins import normwise
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+TOL_ABA_TREE = 1e-3
+TOL_GRAD = 1e-3
+
+MODELS = {
+    "chain7": gen.chain7(0),
+    "humanoid": gen.humanoid(0),
+    "tree101": gen.random_tree(101),
+    "tree117": gen.random_tree(117),
+    "tree_big": gen.random_tree(7, 64),
+}
+
+
+@pytest.fixture(scope="module")
+def fxm():
+    return {k: fx.Model.from_robot(m) for k, m in MODELS.items()}
+
+
+def _aba_tol(name):
+    return TOL if name == "chain7" else TOL_ABA_TREE
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+@pytest.mark.parametrize("B", [300])
+def test_fk_jacobian(fxm, name, B):
+    m, h = MODELS[name], fxm[name]
+    s, d = states(m, B, 21)
+    frames = list(m.end_frames)[:8]
+    pose, J = fx.frax_jacobian(h, d["q"], frames, want_pose=True)
+    assert normwise(host(pose), rbd.fk_flat(m, s.q)) < TOL
+    assert normwise(host(J), rbd.jacobian(m, s.q, frames).reshape(B, -1)) < TOL
+    pose2 = fx.frax_fk(h, d["q"])
+    assert torch.equal(pose, pose2)
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_rnea(fxm, name):
+    m, h = MODELS[name], fxm[name]
+    B = 300
+    s, d = states(m, B, 22)
+    tau = fx.frax_rnea(h, d["q"], d["qd"], d["qdd"])
+    assert normwise(host(tau), rbd.rnea(m, s.q, s.qd, s.qdd)) < TOL
+    bias = fx.frax_rnea(h, d["q"], d["qd"], None)
+    assert normwise(host(bias), rbd.rnea(m, s.q, s.qd, np.zeros_like(s.qd))) < TOL
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_crba_ltdl(fxm, name):
+    m, h = MODELS[name], fxm[name]
+    B = 300
+    s, d = states(m, B, 23)
+    M, LD = fx.frax_crba(h, d["q"], want_M=True, want_LD=True)
+    Mref = rbd.crba(m, s.q)
+    assert normwise(host(M), Mref.reshape(B, -1)) < TOL
+    L, D = rbd.ltdl(Mref)
+    assert normwise(host(LD), rbd.pack_ltdl(L, D)) < TOL
+    M_only, none = fx.frax_crba(h, d["q"], want_M=True, want_LD=False)
+    assert none is None and torch.equal(M_only, M)
+    _, LD_only = fx.frax_crba(h, d["q"], want_M=False, want_LD=True)
+    assert torch.equal(LD_only, LD)
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_aba(fxm, name):
+    m, h = MODELS[name], fxm[name]
+    B = 300
+    s, d = states(m, B, 24)
+    qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+    assert normwise(host(qdd), rbd.aba(m, s.q, s.qd, s.tau)) < _aba_tol(name)
+
+
+@pytest.mark.parametrize("name", ["chain7", "humanoid", "tree101", "tree_big"])
+def test_rnea_vjp(fxm, name):
+    m, h = MODELS[name], fxm[name]
+    B = 160
+    s, d = states(m, B, 25)
+    g = gen.draw_gbar(m.nv, B, 26).astype(np.float32).astype(np.float64)
+    qb, qdb, qddb = fx.frax_rnea_vjp(h, d["q"], d["qd"], d["qdd"], dev(g))
+    rq, rqd, rqdd = dv.rnea_vjp(m, s.q, s.qd, s.qdd, g)
+    assert normwise(host(qb), rq) < TOL_GRAD
+    assert normwise(host(qdb), rqd) < TOL_GRAD
+    assert normwise(host(qddb), rqdd) < TOL_GRAD
+
+
+@pytest.mark.parametrize("name", ["chain7", "humanoid", "tree101", "tree_big"])
+def test_aba_vjp(fxm, name):
+    m, h = MODELS[name], fxm[name]
+    B = 160
+    s, d = states(m, B, 27)
+    g = gen.draw_gbar(m.nv, B, 28).astype(np.float32).astype(np.float64)
+    qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+    qb, qdb, tb = fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], qdd, dev(g))
+    rq, rqd, rt = dv.aba_vjp(m, s.q, s.qd, s.tau, g)
+    assert normwise(host(qb), rq) < TOL_GRAD
+    assert normwise(host(qdb), rqd) < TOL_GRAD
+    assert normwise(host(tb), rt) < TOL_GRAD
+
+
+@pytest.mark.parametrize("name", ["chain7", "humanoid"])
+def test_vjp_vs_central_differences(fxm, name):
+    """GPU VJPs against FP64 central differences (step 1e-6) of the oracle's
+    RNEA and forward dynamics, contracted with the same seed."""
+    m, h = MODELS[name], fxm[name]
+    B = 8
+    s, d = states(m, B, 29)
+    g = gen.draw_gbar(m.nv, B, 30).astype(np.float32).astype(np.float64)
+    hstep = 1e-6
+
+    def central(fun, n):
+        cols = []
+        for k in range(n):
+            e = np.zeros((B, n))
+            e[:, k] = hstep
+            cols.append((fun(e) - fun(-e)) / (2 * hstep))
+        return np.stack(cols, -1)
+
+    Jq = central(lambda e: rbd.rnea(m, dv.retract(m, s.q, e), s.qd, s.qdd), m.nv)
+    Jqd = central(lambda e: rbd.rnea(m, s.q, s.qd + e, s.qdd), m.nv)
+    qb, qdb, _ = fx.frax_rnea_vjp(h, d["q"], d["qd"], d["qdd"], dev(g))
+    assert normwise(host(qb), dv.to_ambient(m, s.q, np.einsum("bi,bij->bj", g, Jq))) < TOL_GRAD
+    assert normwise(host(qdb), np.einsum("bi,bij->bj", g, Jqd)) < TOL_GRAD
+    Aq = central(lambda e: rbd.aba(m, dv.retract(m, s.q, e), s.qd, s.tau), m.nv)
+    Aqd = central(lambda e: rbd.aba(m, s.q, s.qd + e, s.tau), m.nv)
+    At = central(lambda e: rbd.aba(m, s.q, s.qd, s.tau + e), m.nv)
+    qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+    qb, qdb, tb = fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], qdd, dev(g))
+    assert normwise(host(qb), dv.to_ambient(m, s.q, np.einsum("bi,bij->bj", g, Aq))) < TOL_GRAD
+    assert normwise(host(qdb), np.einsum("bi,bij->bj", g, Aqd)) < TOL_GRAD
+    assert normwise(host(tb), np.einsum("bi,bij->bj", g, At)) < TOL_GRAD
+
+
+@pytest.mark.parametrize("B", [1, 31, 32, 33, 127, 128, 129, 257])
+def test_edge_batch_sizes_and_padding(fxm, B):
+    """Ragged batches, and ld > B: the padding columns are never written."""
+    m, h = MODELS["chain7"], fxm["chain7"]
+    ld = B + 13
+    s = gen.draw_states(m, B, 31).as_f32()
+    q, qd, qdd, tau = (dev(x, ld) for x in (s.q, s.qd, s.qdd, s.tau))
+    out = torch.full((m.nv, ld), 7.0, device="cuda")
+    fx.frax_rnea(h, q, qd, qdd, tau=out[:, :B])
+    assert normwise(host(out[:, :B]), rbd.rnea(m, s.q, s.qd, s.qdd)) < TOL
+    assert torch.all(out[:, B:] == 7.0)
+    qddo = fx.frax_aba(h, q, qd, tau)
+    assert normwise(host(qddo), rbd.aba(m, s.q, s.qd, s.tau)) < TOL
+
+
+def test_empty_batch_is_noop(fxm):
+    h = fxm["chain7"]
+    z = torch.empty((7, 0), device="cuda")
+    assert fx.frax_rnea(h, torch.empty((7, 0), device="cuda"), z, z).shape == (7, 0)
+
+
+def test_argument_errors(fxm):
+    h = fxm["chain7"]
+    q = torch.zeros((7, 16), device="cuda")
+    with pytest.raises(fx.FraxError):
+        fx.frax_rnea(h, q, torch.zeros((6, 16), device="cuda"))
+    with pytest.raises(fx.FraxError):
+        fx.frax_rnea(h, q.double(), q)
+    with pytest.raises(fx.FraxError):
+        fx.frax_jacobian(h, q, [9])
+
+
+@pytest.mark.parametrize("name,B", [("chain7", 1 << 20), ("humanoid", 1 << 18)])
+def test_full_size_sampled(fxm, name, B):
+    """The configurations the bench times, in its launch configuration: every
+    op on the full batch, a random sample of instances checked against the
+    oracle."""
+    m, h = MODELS[name], fxm[name]
+    s, d = states(m, B, 1000 + (1 if name == "chain7" else 2))
+    idx = np.sort(np.random.default_rng(5).choice(B, 96, replace=False))
+    idx[-1] = B - 1
+    ss = s.take(idx)
+    frames = list(m.end_frames)
+    pose, J = fx.frax_jacobian(h, d["q"], frames, want_pose=True)
+    tau = fx.frax_rnea(h, d["q"], d["qd"], d["qdd"])
+    M, LD = fx.frax_crba(h, d["q"], want_LD=True)
+    qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+    sel = torch.from_numpy(idx).cuda()
+    pick = lambda t: host(t.index_select(1, sel))
+    assert normwise(pick(pose), rbd.fk_flat(m, ss.q)) < TOL
+    assert normwise(pick(J), rbd.jacobian(m, ss.q, frames).reshape(len(idx), -1)) < TOL
+    assert normwise(pick(tau), rbd.rnea(m, ss.q, ss.qd, ss.qdd)) < TOL
+    Mref = rbd.crba(m, ss.q)
+    assert normwise(pick(M), Mref.reshape(len(idx), -1)) < TOL
+    assert normwise(pick(LD), rbd.pack_ltdl(*rbd.ltdl(Mref))) < TOL
+    assert normwise(pick(qdd), rbd.aba(m, ss.q, ss.qd, ss.tau)) < _aba_tol(name)
+    g = gen.draw_gbar(m.nv, B, 77).astype(np.float32).astype(np.float64)
+    gd = dev(g)
+    qb, qdb, qddb = fx.frax_rnea_vjp(h, d["q"], d["qd"], d["qdd"], gd)
+    rq, rqd, rqdd = dv.rnea_vjp(m, ss.q, ss.qd, ss.qdd, g[idx])
+    assert normwise(pick(qb), rq) < TOL_GRAD and normwise(pick(qdb), rqd) < TOL_GRAD
+    assert normwise(pick(qddb), rqdd) < TOL_GRAD
+    aq, aqd, at = fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], qdd, gd)
+    rq, rqd, rt = dv.aba_vjp(m, ss.q, ss.qd, ss.tau, g[idx])
+    assert normwise(pick(aq), rq) < TOL_GRAD and normwise(pick(aqd), rqd) < TOL_GRAD
+    assert normwise(pick(at), rt) < TOL_GRAD
+
+
+def test_autograd_functions(fxm):
+    m, h = MODELS["humanoid"], fxm["humanoid"]
+    B = 64
+    s, d = states(m, B, 33)
+    q, qd, qdd, tau = (d[k].clone().requires_grad_(True) for k in ("q", "qd", "qdd", "tau"))
+    g = torch.randn((m.nv, B), device="cuda")
+    out = fx.rnea(h, q, qd, qdd)
+    gq, gqd, gqdd = torch.autograd.grad(out, (q, qd, qdd), g)
+    rq, rqd, rqdd = fx.frax_rnea_vjp(h, d["q"], d["qd"], d["qdd"], g)
+    assert torch.equal(gq, rq) and torch.equal(gqd, rqd) and torch.equal(gqdd, rqdd)
+    a = fx.aba(h, q, qd, tau)
+    gq, gqd, gt = torch.autograd.grad(a, (q, qd, tau), g)
+    aq, aqd, at = fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], a.detach(), g)
+    assert torch.equal(gq, aq) and torch.equal(gqd, aqd) and torch.equal(gt, at)
