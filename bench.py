@@ -36,38 +36,36 @@ FP32_LANES_PER_SM = 128
 
 
 # ------------------------------------------------------------- flop accounting
-# FP32 operations per body of each formulation (fma = 2, add/mul = 1), counted
-# from the kernels' formulas; sincos/sqrt/div are kept out. See the design doc.
-PER_BODY = {
-    # op: (revolute with parent, revolute at world, free-flyer root)
-    "fk_jac": (128, 99, 126),
-    "rnea": (298, 184, 228),
-    "crba_ltdl": (171, 0, 0),     # composite transform; the ancestor walk is added per pair
-    "aba": (852, 250, 320),
-    "rnea_vjp": (780, 500, 560),
-    "aba_vjp": (1550, 800, 900),
+# FP32 operations per instance of each kernel's formulation (fma = 2 flops,
+# add/sub/mul = 1; sincos, sqrt and divisions are not in the FMA-pipe count).
+# Counted exactly by running the device code on the host with a counting
+# float type: `python bench.py --count-flops` rebuilds flopcount.cu and
+# reprints this table.
+FLOPS = {
+    "chain7": {"fk_jac": 903, "fk": 819, "rnea": 2000, "bias": 2000, "crba_ltdl": 2305, "crba": 2172,
+               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 9331},
+    "humanoid": {"fk_jac": 5304, "fk": 3792, "rnea": 8992, "bias": 8986, "crba_ltdl": 16691, "crba": 12901,
+                 "aba": 25231, "rnea_vjp": 22034, "aba_vjp": 43301},
 }
-WALK = 54  # one force transform in the CRBA ancestor walk
 
 
-def flops_per_instance(op: str, parent, free_root: bool, nv: int) -> int:
-    n = len(parent)
-    a, r, f = PER_BODY[op]
-    tot = 0
-    for i in range(n):
-        if i == 0 and free_root:
-            tot += f
-        elif parent[i] < 0:
-            tot += r
-        else:
-            tot += a
-    if op == "crba_ltdl":
-        depth = [0] * n
-        for i in range(n):
-            depth[i] = depth[parent[i]] + 1 if parent[i] >= 0 else 0
-        tot += WALK * sum(depth)
-        tot += sum(k * k + 2 * k for k in range(nv))  # L^T D L on the dense chain bound
-    return tot
+def count_flops():
+    """Builds flopcount.cu (host-only) and prints the per-op table."""
+    import gen
+    exe = os.path.join(ROOT, "_build", "flopcount")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run(["g++", "-std=c++17", "-O1", "-x", "c++", "-I/usr/local/cuda/include", "-w",
+                    "-o", exe, os.path.join(ROOT, "flopcount.cu"),
+                    os.path.join(ROOT, "paper_2604_04310_gb300", "csrc", "model.cpp")], check=True)
+    for m in (gen.chain7(0), gen.humanoid(0)):
+        fr = list(m.end_frames)
+        ints = lambda xs: " ".join(str(int(x)) for x in xs)
+        flts = lambda xs: " ".join(repr(float(x)) for x in xs)
+        text = " ".join([ints([m.n_bodies, *m.parent, *m.joint_type]),
+                         flts([*m.axis.ravel(), *m.placement.ravel(), *m.inertia.ravel(), *m.gravity]),
+                         ints([len(fr), *fr])])
+        r = subprocess.run([exe], input=text, capture_output=True, text=True, check=True)
+        print(m.name, r.stdout)
 
 
 def fp32_peak_tflops(sm_mhz: float) -> float:
@@ -127,7 +125,6 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- workloads
 def make_inputs(robot, B, seed, device):
-    import numpy as np
     import torch
 
     import gen
@@ -143,9 +140,9 @@ class Step:
     """The whole hot path over one resident batch; output buffers are
     allocated once (torch), the kernels write into them."""
 
-    def __init__(self, fx, model, robot, dev, device):
+    def __init__(self, fx, model, robot, dev, device, ops):
         import torch
-        self.fx, self.m, self.d = fx, model, dev
+        self.fx, self.m, self.d, self.ops = fx, model, dev, ops
         B = dev["q"].shape[1]
         nv, nb = model.nv, model.n_bodies
         e = lambda k: torch.empty((k, B), dtype=torch.float32, device=device)
@@ -155,27 +152,72 @@ class Step:
             "LD": e(nv * (nv + 1) // 2), "qdd": e(nv), "rq": e(model.nq), "rqd": e(nv), "rqdd": e(nv),
             "aq": e(model.nq), "aqd": e(nv), "at": e(nv),
         }
+        fx_, m, d, o = fx, model, dev, self.out
+        table = {
+            "fk_jac": lambda: fx_.frax_jacobian(m, d["q"], self.frames, pose=o["pose"], J=o["J"]),
+            "rnea": lambda: fx_.frax_rnea(m, d["q"], d["qd"], d["qdd"], tau=o["tau"]),
+            "bias": lambda: fx_.frax_rnea(m, d["q"], d["qd"], None, tau=o["tau"]),
+            "crba_ltdl": lambda: fx_.frax_crba(m, d["q"], M=o["M"], LD=o["LD"]),
+            "aba": lambda: fx_.frax_aba(m, d["q"], d["qd"], d["tau"], qdd=o["qdd"]),
+            "rnea_vjp": lambda: fx_.frax_rnea_vjp(m, d["q"], d["qd"], d["qdd"], d["gbar"], qbar=o["rq"],
+                                                  qdbar=o["rqd"], qddbar=o["rqdd"]),
+            "aba_vjp": lambda: fx_.frax_aba_vjp(m, d["q"], d["qd"], d["tau"], o["qdd"], d["gbar"], qbar=o["aq"],
+                                                qdbar=o["aqd"], taubar=o["at"]),
+        }
+        self.launches = [(n, table[n]) for n in ops]
         self.B = B
 
     def run(self, events=None):
-        fx, m, d, o = self.fx, self.m, self.d, self.out
-        launches = [
-            ("fk_jac", lambda: fx.frax_jacobian(m, d["q"], self.frames, pose=o["pose"], J=o["J"])),
-            ("rnea", lambda: fx.frax_rnea(m, d["q"], d["qd"], d["qdd"], tau=o["tau"])),
-            ("crba_ltdl", lambda: fx.frax_crba(m, d["q"], M=o["M"], LD=o["LD"])),
-            ("aba", lambda: fx.frax_aba(m, d["q"], d["qd"], d["tau"], qdd=o["qdd"])),
-            ("rnea_vjp", lambda: fx.frax_rnea_vjp(m, d["q"], d["qd"], d["qdd"], d["gbar"], qbar=o["rq"],
-                                                  qdbar=o["rqd"], qddbar=o["rqdd"])),
-            ("aba_vjp", lambda: fx.frax_aba_vjp(m, d["q"], d["qd"], d["tau"], o["qdd"], d["gbar"], qbar=o["aq"],
-                                                qdbar=o["aqd"], taubar=o["at"])),
-        ]
-        for k, (name, fn) in enumerate(launches):
+        for name, fn in self.launches:
             if events is not None:
                 events[name][0].record()
             fn()
             if events is not None:
                 events[name][1].record()
-        return len(launches)
+        return len(self.launches)
+
+
+def time_step(step, steps, warmup, flush, world, dist, clocks=None):
+    """Times `steps` passes of the step with CUDA events (per step and per
+    kernel) on torch's current stream, the stream the kernels are launched
+    on; L2 is flushed between steps outside the events."""
+    import torch
+    for _ in range(warmup):
+        step.run()
+    torch.cuda.synchronize()
+    ev = [{n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in step.ops}
+          for _ in range(steps)]
+    sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.3)
+    t0 = time.perf_counter()
+    launches = 0
+    for k in range(steps):
+        flush.zero_()
+        sev[k][0].record()
+        launches += step.run(ev[k])
+        sev[k][1].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks is not None else None
+    step_ms = sum(a.elapsed_time(b) for a, b in sev)
+    per_op_ms = {n: sum(e[n][0].elapsed_time(e[n][1]) for e in ev) / steps for n in step.ops}
+    return step_ms, per_op_ms, launches, wall, clk
+
+
+def roofline_of(per_op_ms, flops, B, peak):
+    out = {}
+    for n, ms in per_op_ms.items():
+        tf = flops[n] * B / (ms / 1e3) / 1e12
+        out[n] = {"ms": ms, "evals_per_s": B / (ms / 1e3), "flops_per_instance": flops[n], "tflops": tf,
+                  "frac_fp32_peak": tf / peak}
+    return out
 
 
 def cpu_baseline_child(args):
@@ -255,63 +297,31 @@ def frax_arm(args, rank, world, local_rank):
 
     device = torch.device("cuda", local_rank)
     torch.cuda.set_device(device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2 (129 MB)
+    peak = fp32_peak_tflops(2070.0)
+    phys = local_rank
+    if "CUDA_VISIBLE_DEVICES" in os.environ and os.environ["CUDA_VISIBLE_DEVICES"]:
+        phys = int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank])
+
+    # main workload: the 7-DoF chain, 2^20 instances per GPU, the whole path
     robot = gen.chain7(0)
     B = args.batch
     model = fx.Model.from_robot(robot)
     host, dev = make_inputs(robot, B, 1001 + rank, device)
-    step = Step(fx, model, robot, dev, device)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)  # > L2 (129 MB)
-
-    for _ in range(args.warmup):
-        step.run()
-    torch.cuda.synchronize()
-    events = [{n: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for n in OPS}
-              for _ in range(args.steps)]
-    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else
-                          int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]))
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    t0 = time.perf_counter()
-    launches = 0
-    for k in range(args.steps):
-        flush.zero_()  # L2 flush between steps, outside the step's events
-        step_ev[k][0].record()
-        launches += step.run(events[k])
-        step_ev[k][1].record()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    step_ms = sum(a.elapsed_time(b) for a, b in step_ev)
+    step = Step(fx, model, robot, dev, device, OPS)
+    clocks = ClockSampler(phys)
+    step_ms, per_op_ms, launches, wall, clk = time_step(step, args.steps, args.warmup, flush, world, dist, clocks)
     t = torch.tensor([step_ms], dtype=torch.float64, device=device)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms_max = float(t.item())
-    ms_per_step = step_ms_max / args.steps
+    ms_per_step = float(t.item()) / args.steps
     evals_per_step = len(OPS) * B
     value = world * evals_per_step / (ms_per_step / 1e3)
-
-    per_op_ms = {n: sum(ev[n][0].elapsed_time(ev[n][1]) for ev in events) / args.steps for n in OPS}
-    per_op = {n: {"ms": per_op_ms[n], "evals_per_s": B / (per_op_ms[n] / 1e3),
-                  "flops_per_instance": flops_per_instance(n, list(robot.parent), robot.has_free_root, robot.nv)}
-              for n in OPS}
+    per_op = roofline_of(per_op_ms, FLOPS["chain7"], B, peak)
     dom = max(OPS, key=lambda n: per_op_ms[n])
-    f_inst = per_op[dom]["flops_per_instance"]
-    achieved = f_inst * B / (per_op_ms[dom] / 1e3) / 1e12
-    peak = fp32_peak_tflops(2070.0)
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
-    for n in OPS:
-        fi = per_op[n]["flops_per_instance"]
-        per_op[n]["tflops"] = fi * B / (per_op_ms[n] / 1e3) / 1e12
-        per_op[n]["frac_fp32_peak"] = per_op[n]["tflops"] / peak
+    roofline = {"bound": "alu", "kernel": dom, "achieved": per_op[dom]["tflops"], "peak": peak,
+                "unit": "TFLOP/s", "frac": per_op[dom]["frac_fp32_peak"], "traffic": None,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock (recipe unit counts)"}
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -327,7 +337,8 @@ def frax_arm(args, rank, world, local_rank):
                 te = time.perf_counter()
             for k in dev:
                 dev[k].copy_(pin[k], non_blocking=True)
-            step.run()
+            n_l = step.run()
+            launches += n_l if it >= 2 else 0
             for k in step.out:
                 outs_h[k].copy_(step.out[k], non_blocking=True)
             torch.cuda.synchronize()
@@ -336,7 +347,28 @@ def frax_arm(args, rank, world, local_rank):
         if world > 1:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e = {"value": world * evals_per_step / float(tt.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": float(tt.item()) * 1e3}
+               "d2h_bytes_per_step": d2h, "ms_per_step": float(tt.item()) * 1e3, "steps": n_e2e}
+        del pin, outs_h
+    del step, dev, host
+
+    # second workload: the floating-base humanoid (30 bodies, nv = 35), 2^18
+    humanoid = None
+    if not args.no_humanoid:
+        hrobot = gen.humanoid(0)
+        hB = args.humanoid_batch
+        hmodel = fx.Model.from_robot(hrobot)
+        _, hdev = make_inputs(hrobot, hB, 2002 + rank, device)
+        hops = ["fk_jac", "bias", "crba_ltdl", "aba", "rnea_vjp", "aba_vjp"]
+        hstep = Step(fx, hmodel, hrobot, hdev, device, hops)
+        hsteps = max(5, args.steps // 5)
+        hms, hper, hl, _, _ = time_step(hstep, hsteps, max(3, args.warmup), flush, world, dist)
+        launches += hl
+        humanoid = {"workload": "floating-base humanoid (root + 29 revolute, seed 0), 2^18 instances; FK + 4 "
+                                "end-frame Jacobians, bias forces, CRBA + LTDL, ABA, RNEA-VJP, ABA-VJP",
+                    "batch": hB, "steps": hsteps, "ms_per_step": hms / hsteps,
+                    "evals_per_s": world * len(hops) * hB / (hms / hsteps / 1e3),
+                    "per_op": roofline_of(hper, FLOPS["humanoid"], hB, peak)}
+        del hstep, hdev
 
     serve = None
     if rank == 0 and not args.no_serve:
@@ -350,31 +382,37 @@ def frax_arm(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "7-DoF revolute chain (seed 0), 2^20 instances per GPU, one step = "
+                "config": {"workload": "7-DoF revolute chain (seed 0), 2^20 instances per GPU; one step = "
                                        "FK+EE Jacobian, RNEA, CRBA+LTDL, ABA, RNEA-VJP, ABA-VJP",
                            "global_batch": B * world, "parallelism": f"replicas x{world}",
                            "l2": "256 MB buffer written between steps (L2 flush)"},
                 "clocks": clk, "gpu_launches": launches, "wall_s": wall, "per_op": per_op, "roofline": roofline,
-                "e2e": e2e, "cpu_baseline": cpu, "serving": serve}
+                "e2e": e2e, "humanoid": humanoid, "cpu_baseline": cpu, "serving": serve}
         print(json.dumps(line))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="frax", choices=["frax", "reference"])
     ap.add_argument("--batch", type=int, default=1 << 20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-humanoid", action="store_true")
+    ap.add_argument("--humanoid-batch", type=int, default=1 << 18)
+    ap.add_argument("--count-flops", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--cpu-baseline-child", action="store_true")
     args = ap.parse_args()
     if args.cpu_baseline_child:
         cpu_baseline_child(args)
+        return
+    if args.count_flops:
+        count_flops()
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -1,0 +1,101 @@
+// Counts the FP32 operations of each kernel's formulation per instance by
+// running the device code on the host with `float` replaced by a counting
+// type (fma = 2 flops, add/sub/mul = 1; divisions, sqrt and sincos counted
+// separately, outside the FMA-pipe roofline). Used by bench.py --count-flops.
+//   g++ -std=c++17 -x c++ -I/usr/local/cuda/include -o flopcount flopcount.cu \
+//        paper_2604_04310_gb300/csrc/model.cpp
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "paper_2604_04310_gb300/csrc/model.h"  // model image keeps real floats
+
+struct Counts {
+  long long add = 0, mul = 0, fma = 0, div = 0, sfu = 0;
+};
+static Counts g;
+
+struct CF {
+  float v;
+  CF() = default;
+  CF(float x) : v(x) {}
+  CF(double x) : v(float(x)) {}
+  CF(int x) : v(float(x)) {}
+};
+inline CF operator+(CF a, CF b) { g.add++; return CF(a.v + b.v); }
+inline CF operator-(CF a, CF b) { g.add++; return CF(a.v - b.v); }
+inline CF operator*(CF a, CF b) { g.mul++; return CF(a.v * b.v); }
+inline CF operator/(CF a, CF b) { g.div++; return CF(a.v / b.v); }
+inline CF operator-(CF a) { return CF(-a.v); }
+inline CF& operator+=(CF& a, CF b) { g.add++; a.v += b.v; return a; }
+inline CF& operator-=(CF& a, CF b) { g.add++; a.v -= b.v; return a; }
+inline CF& operator*=(CF& a, CF b) { g.mul++; a.v *= b.v; return a; }
+inline CF fmaf(CF a, CF b, CF c) { g.fma++; return CF(std::fma(a.v, b.v, c.v)); }
+inline CF sqrtf(CF a) { g.sfu++; return CF(std::sqrt(a.v)); }
+inline void sincosf(CF x, CF* s, CF* c) { g.sfu++; s->v = std::sin(x.v); c->v = std::cos(x.v); }
+
+#define float CF
+#include "paper_2604_04310_gb300/csrc/dyn.cuh"
+#undef float
+
+using namespace frax;
+
+template <class T, class Img>
+void count(const Img& M, int nf, const int* frames) {
+  int nq = M.nq, nv = M.nv, nb = M.nb;
+  std::vector<CF> q(nq, CF(0.3f)), qd(nv, CF(0.2f)), qdd(nv, CF(0.1f)), tau(nv, CF(0.5f)), gb(nv, CF(0.7f));
+  if (M.free_root) { q[3] = q[4] = q[5] = CF(0.f); q[6] = CF(1.f); }
+  std::vector<CF> o1(nb * 12 + 64), o2(nf * 6 * nv + 64), o3(nv * nv + 64), o4(nv * (nv + 1) / 2 + 64), o5(nq + 8), o6(nv + 8), o7(nv + 8);
+  Col col{1, 0};
+  Frames fr{nf, {0}};
+  for (int f = 0; f < nf; ++f) fr.body[f] = frames[f];
+  auto rep = [&](const char* name) {
+    printf("  \"%s\": {\"flops\": %lld, \"fma\": %lld, \"add\": %lld, \"mul\": %lld, \"div\": %lld, \"sfu\": %lld},\n",
+           name, 2 * g.fma + g.add + g.mul, g.fma, g.add, g.mul, g.div, g.sfu);
+    g = Counts{};
+  };
+  g = Counts{};
+  fk_one<T>(M, q.data(), o1.data(), fr, o2.data(), col); rep("fk_jac");
+  fk_one<T>(M, q.data(), o1.data(), Frames{0, {0}}, nullptr, col); rep("fk");
+  rnea_one<T>(M, q.data(), qd.data(), qdd.data(), o6.data(), col); rep("rnea");
+  rnea_one<T>(M, q.data(), qd.data(), nullptr, o6.data(), col); rep("bias");
+  crba_one<T>(M, q.data(), o3.data(), o4.data(), col); rep("crba_ltdl");
+  crba_one<T>(M, q.data(), o3.data(), nullptr, col); rep("crba");
+  aba_one<T>(M, q.data(), qd.data(), tau.data(), o6.data(), col); rep("aba");
+  rnea_vjp_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp");
+  aba_vjp_one<T>(M, q.data(), qd.data(), tau.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp");
+}
+
+int main(int argc, char** argv) {
+  // stdin: n, parent[n], joint_type[n], axis[3n], placement[12n], inertia[10n], gravity[3], nf, frames[nf]
+  int n;
+  if (scanf("%d", &n) != 1) return 1;
+  std::vector<int32_t> parent(n), jt(n);
+  std::vector<double> axis(3 * n), plc(12 * n), inr(10 * n), grav(3);
+  for (auto& x : parent) scanf("%d", &x);
+  for (auto& x : jt) scanf("%d", &x);
+  for (auto& x : axis) scanf("%lf", &x);
+  for (auto& x : plc) scanf("%lf", &x);
+  for (auto& x : inr) scanf("%lf", &x);
+  for (auto& x : grav) scanf("%lf", &x);
+  int nf;
+  scanf("%d", &nf);
+  std::vector<int> frames(nf);
+  for (auto& x : frames) scanf("%d", &x);
+  HostModel hm;
+  std::string err = build_model(n, parent.data(), jt.data(), axis.data(), plc.data(), inr.data(), grav.data(), &hm);
+  if (!err.empty()) { fprintf(stderr, "%s\n", err.c_str()); return 1; }
+  printf("{\n");
+  if (hm.kind == kKindChain) {
+    static ModelImage<7> img; hm.pack(&img); count<ChainTopo<7>>(img, nf, frames.data());
+  } else if (hm.free_root) {
+    static ModelImage<64> img; hm.pack(&img); count<TreeTopo<64, true>>(img, nf, frames.data());
+  } else {
+    static ModelImage<64> img; hm.pack(&img); count<TreeTopo<64, false>>(img, nf, frames.data());
+  }
+  printf("  \"nb\": %d, \"nv\": %d\n}\n", hm.nb, hm.nv);
+  return 0;
+}

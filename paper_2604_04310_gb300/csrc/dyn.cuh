@@ -62,7 +62,8 @@ struct Col {
   FD void out(float* __restrict__ p, int k, float v) const { p[k * ld + b] = v; }
 };
 
-FD SV gravity_acc(const float* g) { return SV{mk(0, 0, 0), mk(-g[0], -g[1], -g[2])}; }
+template <class GT>
+FD SV gravity_acc(const GT* g) { return SV{mk(0, 0, 0), mk(-g[0], -g[1], -g[2])}; }
 
 // Free-flyer root: ^0R_0 = R_T R(quat), ^0p_0 = p_T + R_T p_q.
 struct RootPose {

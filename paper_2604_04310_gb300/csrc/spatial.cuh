@@ -39,11 +39,13 @@ FD SV crm(const SV& a, const SV& b) { return SV{cross(a.w, b.w), cross(a.w, b.v)
 FD SV crf(const SV& a, const SV& f) { return SV{cross(a.w, f.w) + cross(a.v, f.v), cross(a.w, f.v)}; }
 
 // --- rotations --------------------------------------------------------------
-FD V3 rot(const float* R, V3 a) {  // R a, R row-major
+template <class RT>
+FD V3 rot(const RT* R, V3 a) {  // R a, R row-major
   return mk(fmaf(R[0], a.x, fmaf(R[1], a.y, R[2] * a.z)), fmaf(R[3], a.x, fmaf(R[4], a.y, R[5] * a.z)),
             fmaf(R[6], a.x, fmaf(R[7], a.y, R[8] * a.z)));
 }
-FD V3 rotT(const float* R, V3 a) {  // R^T a
+template <class RT>
+FD V3 rotT(const RT* R, V3 a) {  // R^T a
   return mk(fmaf(R[0], a.x, fmaf(R[3], a.y, R[6] * a.z)), fmaf(R[1], a.x, fmaf(R[4], a.y, R[7] * a.z)),
             fmaf(R[2], a.x, fmaf(R[5], a.y, R[8] * a.z)));
 }
@@ -60,7 +62,8 @@ FD void quat_to_R(float x, float y, float z, float w, float* R) {
   R[6] = 2.f * (xz - wy);       R[7] = 2.f * (yz + wx);       R[8] = 1.f - 2.f * (xx + yy);
 }
 // C = A B (3x3 row-major)
-FD void mat_mul(const float* A, const float* B, float* C) {
+template <class AT, class BT>
+FD void mat_mul(const AT* A, const BT* B, float* C) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -125,7 +128,8 @@ FD void sym_rotz(float c, float s, float* S) {
   S[5] = fmaf(s, xz, c * yz);
 }
 // symmetric S (xx yy zz xy xz yz) -> R S R^T, R row-major
-FD void sym_rot(const float* R, float* S) {
+template <class RT>
+FD void sym_rot(const RT* R, float* S) {
   float T[9];  // T = S R^T
   float Sf[9] = {S[0], S[3], S[4], S[3], S[1], S[5], S[4], S[5], S[2]};
 #pragma unroll
@@ -139,7 +143,8 @@ FD void sym_rot(const float* R, float* S) {
   S[0] = o(0, 0); S[1] = o(1, 1); S[2] = o(2, 2); S[3] = o(0, 1); S[4] = o(0, 2); S[5] = o(1, 2);
 }
 // general M (row-major 9) -> R M R^T
-FD void gen_rot(const float* R, float* M) {
+template <class RT>
+FD void gen_rot(const RT* R, float* M) {
   float T[9];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
