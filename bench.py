@@ -264,12 +264,159 @@ def run_cpu_baseline(seconds):
     return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
 
 
-def serve_probe(fx, device, seconds):
-    """A short served stream (if the server is built): p50/p99 latency."""
-    if not hasattr(fx, "Server"):
-        return None
-    from paper_2604_04310_gb300 import serving
-    return serving.bench_stream(device, seconds=seconds)
+SERVE_OPS = ["rnea", "crba", "aba", "rnea_grad"]
+
+
+def serve_stream(fx, seconds, check_oracle=True):
+    """Served workload: requests for the 7-DoF chain, the humanoid and 32
+    random trees (3-64 bodies), op uniform over rnea / crba / aba /
+    rnea-gradient, instance count log-uniform in [1, 4096]. First a closed
+    loop measures the saturation request rate; then Poisson arrivals at 50 %
+    and 90 % of it, latency = completion seen by the host - arrival."""
+    import threading
+
+    import numpy as np
+
+    import gen
+    from paper_2604_04310_gb300.serving import Server
+    robots = gen.serving_pool(32)
+    models = [fx.Model.from_robot(r) for r in robots]
+    srv = Server(budget_bytes=2 << 30, idle_exit_ms=20.0)
+    ids = [srv.add_model(m) for m in models]
+    rng = np.random.default_rng(2026)
+    pool = []
+    for k in range(192):
+        mi = int(rng.integers(len(robots)))
+        op = SERVE_OPS[int(rng.integers(4))]
+        B = int(np.clip(np.floor(np.exp(rng.uniform(0.0, np.log(4097.0)))), 1, 4096))
+        r = robots[mi]
+        st = gen.draw_states(r, B, 50000 + k).as_f32()
+        g = gen.draw_gbar(r.nv, B, 60000 + k).astype(np.float32).astype(np.float64)
+        arrays = {"rnea": [st.q, st.qd, st.qdd], "crba": [st.q], "aba": [st.q, st.qd, st.tau],
+                  "rnea_grad": [st.q, st.qd, st.qdd, g]}[op]
+        pool.append((mi, op, B, [gen.to_soa(a) for a in arrays], st, g))
+
+    def closed_loop(duration, depth=64):
+        inflight, done_inst, n = {}, 0, 0
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < duration:
+            while len(inflight) < depth:
+                mi, op, B, inp, _, _ = pool[k % len(pool)]
+                req = srv.submit(ids[mi], op, inp, B)
+                if req is None:
+                    break
+                inflight[req] = (mi, op, B)
+                k += 1
+            r = srv.wait_any(10000.0)
+            mi, op, B = inflight.pop(r)
+            srv.collect(r, ids[mi], op, B)
+            done_inst += B
+            n += 1
+        while inflight:
+            r = srv.wait_any(10000.0)
+            mi, op, B = inflight.pop(r)
+            srv.collect(r, ids[mi], op, B)
+            done_inst += B
+            n += 1
+        el = time.perf_counter() - t0
+        return n / el, done_inst / el
+
+    def open_loop(rate, duration, keep=None):
+        arrivals = {}
+        lat, lat_dev = [], []
+        insts = [0]
+        lock = threading.Lock()
+        stop = [False]
+        meta = {}
+
+        def collector():
+            while True:
+                with lock:
+                    empty = not meta
+                if stop[0] and empty:
+                    return
+                r = srv.wait_any(5.0) if not empty else None
+                if r is None:
+                    if empty:
+                        time.sleep(2e-5)
+                    continue
+                t_seen = time.perf_counter()
+                with lock:
+                    mi, op, B, k = meta.pop(r)
+                outs, ldev = srv.collect(r, ids[mi], op, B)
+                lat.append((t_seen - arrivals.pop(r)) * 1e6)
+                lat_dev.append(ldev)
+                insts[0] += B
+                if keep is not None and len(keep) < 48 and B <= 256:
+                    keep.append((k, outs))
+
+        th = threading.Thread(target=collector, daemon=True)
+        th.start()
+        rs = np.random.default_rng(7)
+        t0 = time.perf_counter()
+        t_next = t0
+        k = 0
+        while t_next - t0 < duration:
+            t_next += rs.exponential(1.0 / rate)
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)  # releases the GIL for the collector
+            mi, op, B, inp, _, _ = pool[k % len(pool)]
+            t_arr = t_next
+            while True:
+                with lock:
+                    req = srv.submit(ids[mi], op, inp, B)
+                    if req is not None:
+                        meta[req] = (mi, op, B, k % len(pool))
+                        arrivals[req] = t_arr
+                if req is not None:
+                    break
+                time.sleep(1e-5)
+            k += 1
+        stop[0] = True
+        th.join(timeout=60)
+        el = time.perf_counter() - t0
+        lat = np.array(lat)
+        return {"offered_rate_hz": rate, "requests": int(len(lat)), "p50_us": float(np.percentile(lat, 50)),
+                "p99_us": float(np.percentile(lat, 99)),
+                "p50_service_us": float(np.percentile(lat_dev, 50)),
+                "p99_service_us": float(np.percentile(lat_dev, 99)),
+                "evals_per_s": insts[0] / el}
+
+    old_switch = sys.getswitchinterval()
+    sys.setswitchinterval(2e-5)
+    sat_req, sat_inst = closed_loop(min(2.0, seconds))
+    kept = []
+    points = []
+    for frac in (0.5, 0.9):
+        pt = open_loop(frac * sat_req, seconds, keep=kept if frac == 0.5 else None)
+        pt["load"] = frac
+        points.append(pt)
+    sys.setswitchinterval(old_switch)
+    err = {}
+    if check_oracle:
+        from oracle import derivatives as dv
+        from oracle import rbd
+        for k, outs in kept:
+            mi, op, B, _, st, g = pool[k]
+            r = robots[mi]
+            refs = {"rnea": lambda: [rbd.rnea(r, st.q, st.qd, st.qdd)],
+                    "crba": lambda: [rbd.crba(r, st.q).reshape(B, -1)],
+                    "aba": lambda: [rbd.aba(r, st.q, st.qd, st.tau)],
+                    "rnea_grad": lambda: list(dv.rnea_vjp(r, st.q, st.qd, st.qdd, g))}[op]()
+            for o, ref in zip(outs, refs):
+                x = gen.from_soa(o, B)
+                d = np.abs(x - ref).reshape(B, -1).max(1) / np.maximum(np.abs(ref).reshape(B, -1).max(1), 1e-12)
+                err[op] = max(err.get(op, 0.0), float(d.max()))
+    info = srv.info()
+    srv.close(force=True)
+    return {"workload": "Poisson stream: chain7 / humanoid / 32 random trees (3-64 bodies), ops rnea, crba, aba, "
+                        "rnea-gradient uniform, 1-4096 instances log-uniform; latency = host-seen completion - "
+                        "arrival",
+            "saturation_req_per_s": sat_req, "saturation_evals_per_s": sat_inst, "points": points,
+            "max_rel_err_vs_oracle": err, "checked_requests": len(kept),
+            "kernel_launches": info["kernel_launches"], "resident_ctas": info["resident_ctas"]}
 
 
 # ---------------------------------------------------------------- main arms
@@ -372,7 +519,7 @@ def frax_arm(args, rank, world, local_rank):
 
     serve = None
     if rank == 0 and not args.no_serve:
-        serve = serve_probe(fx, device, args.serve_seconds)
+        serve = serve_stream(fx, args.serve_seconds)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -405,7 +552,7 @@ def main():
     ap.add_argument("--humanoid-batch", type=int, default=1 << 18)
     ap.add_argument("--count-flops", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--cpu-baseline-child", action="store_true")
     args = ap.parse_args()
     if args.cpu_baseline_child:

@@ -162,6 +162,64 @@ FRAX_API frax_status frax_aba_vjp(frax_model_t model, int64_t B, int64_t ld, con
                          const float* qd, const float* tau, const float* qdd, const float* gbar,
                          float* qbar, float* qdbar, float* taubar, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of dynamics queries for many robots. The
+ * paper has no serving layer; this is the batched evaluation of Sec. III-B
+ * ("thousands of parallel instances") turned into a request loop.
+ *
+ * A server owns one device slab of `budget_bytes` (the HBM budget every
+ * request's inputs and outputs are carved from), a ring of request
+ * descriptors in device memory, completion flags in mapped host memory, and
+ * a persistent kernel (one or two CTAs per SM) that claims 128-instance
+ * tiles of any published request as soon as it appears, so requests that
+ * arrive while others run share the GPU. Every device wait is bounded: the
+ * kernel exits after `idle_exit_ms` without work and is relaunched by the
+ * next submit / wait call. Host buffers are SoA [rows][B] (ld = B); inputs
+ * are copied before submit returns.
+ *
+ * ops and their arrays (rows):
+ *   FRAX_OP_RNEA       in q[nq], qd[nv], qdd[nv]          out tau[nv]
+ *   FRAX_OP_CRBA       in q[nq]                           out M[nv*nv]
+ *   FRAX_OP_ABA        in q[nq], qd[nv], tau[nv]          out qdd[nv]
+ *   FRAX_OP_RNEA_GRAD  in q[nq], qd[nv], qdd[nv], gbar[nv] out qbar[nq], qdbar[nv], qddbar[nv]
+ * ---------------------------------------------------------------------- */
+typedef struct frax_server_s* frax_server_t;
+enum { FRAX_OP_RNEA = 0, FRAX_OP_CRBA = 1, FRAX_OP_ABA = 2, FRAX_OP_RNEA_GRAD = 3 };
+enum { FRAX_SERVER_RING = 1024, FRAX_SERVER_MAX_MODELS = 64 };
+
+typedef struct {
+  int64_t budget_bytes, bytes_in_use;
+  int64_t submitted, completed, in_flight;
+  int64_t kernel_launches;   /* persistent-kernel (re)launches so far     */
+  int32_t device_status;     /* 0, or the first error the kernel recorded */
+  int32_t resident_ctas;
+} frax_server_info_t;
+
+/* Allocates the slab, ring and flags on the current CUDA device (the only
+ * allocations the server makes). FRAX_ENOMEM if the slab does not fit. */
+FRAX_API frax_status frax_server_create(int64_t budget_bytes, double idle_exit_ms, frax_server_t* out);
+/* Copies the model's image to the device model table; returns its id. */
+FRAX_API frax_status frax_server_add_model(frax_server_t srv, frax_model_t model, int* model_id);
+/* Admits a request if slab space and a ring slot are free: FRAX_EBUSY if not
+ * now (retry after collecting), FRAX_ENOMEM if it can never fit. */
+FRAX_API frax_status frax_server_submit(frax_server_t srv, int model_id, int op, int64_t B,
+                                        const float* const* inputs, int64_t* request);
+/* done = 1 once every tile of the request has finished. */
+FRAX_API frax_status frax_server_poll(frax_server_t srv, int64_t request, int* done);
+/* Waits (host side, bounded) until some in-flight request completes;
+ * FRAX_ETIMEOUT if none does within timeout_ms. */
+FRAX_API frax_status frax_server_wait_any(frax_server_t srv, double timeout_ms, int64_t* request);
+/* Copies a completed request's outputs to host arrays, frees its slab space
+ * and ring slot, and reports its latency (submit -> completion seen). */
+FRAX_API frax_status frax_server_collect(frax_server_t srv, int64_t request, float* const* outputs,
+                                         double* latency_us);
+FRAX_API frax_status frax_server_info(frax_server_t srv, frax_server_info_t* info);
+/* Stops the kernel (bounded wait) and frees everything. FRAX_EBUSY if
+ * requests are still in flight and `force` is 0; FRAX_ETIMEOUT if the
+ * kernel did not stop within timeout_ms (resources are then leaked, not
+ * freed under a running kernel). */
+FRAX_API frax_status frax_server_destroy(frax_server_t srv, int force, double timeout_ms);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 FRAX_API const char* frax_last_error(void);
 

@@ -30,6 +30,14 @@ SIGNATURES = {
     "frax_aba": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_rnea_vjp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_aba_vjp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_server_create": (c_int, [c_i64, ctypes.c_double, ctypes.POINTER(c_vp)]),
+    "frax_server_add_model": (c_int, [c_vp, c_vp, ctypes.POINTER(c_int)]),
+    "frax_server_submit": (c_int, [c_vp, c_int, c_int, c_i64, ctypes.POINTER(c_vp), ctypes.POINTER(c_i64)]),
+    "frax_server_poll": (c_int, [c_vp, c_i64, ctypes.POINTER(c_int)]),
+    "frax_server_wait_any": (c_int, [c_vp, ctypes.c_double, ctypes.POINTER(c_i64)]),
+    "frax_server_collect": (c_int, [c_vp, c_i64, ctypes.POINTER(c_vp), ctypes.POINTER(ctypes.c_double)]),
+    "frax_server_info": (c_int, [c_vp, c_vp]),
+    "frax_server_destroy": (c_int, [c_vp, c_int, ctypes.c_double]),
     "frax_last_error": (ctypes.c_char_p, []),
     "frax_version": (ctypes.c_char_p, []),
 }

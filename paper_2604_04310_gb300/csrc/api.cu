@@ -5,26 +5,28 @@
 #include <new>
 #include <string>
 
-#include "../../include/frax.h"
+#include "handles.h"
 #include "launch.h"
-#include "model.h"
-
-struct frax_model_s {
-  frax::HostModel m;
-};
 
 namespace {
-
 thread_local std::string g_last_error;
+}
 
-frax_status fail(frax_status s, const std::string& msg) {
+namespace frax {
+frax_status set_error(frax_status s, const std::string& msg) {
   g_last_error = msg;
   return s;
 }
-frax_status ok() {
+frax_status clear_error() {
   g_last_error.clear();
   return FRAX_OK;
 }
+}  // namespace frax
+
+namespace {
+
+frax_status fail(frax_status s, const std::string& msg) { return frax::set_error(s, msg); }
+frax_status ok() { return frax::clear_error(); }
 
 frax_status check_batch(frax_model_t model, int64_t B, int64_t ld, const char* fn) {
   if (!model) return fail(FRAX_EINVAL, std::string(fn) + ": model is NULL");

@@ -50,17 +50,22 @@ template <class T>
 FD int iq_of(int i) { return (T::kFree && i > 0) ? i + 6 : i; }
 
 // One instance's column in the SoA arrays: element k at p[k * ld + b].
-struct Col {
+// kNC = true loads through the read-only (non-coherent) path; false loads
+// through L2 only (ld.cg), for memory a running kernel sees rewritten by
+// copies (the serving slab).
+template <bool kNC>
+struct ColT {
   int64_t ld, b;
   FD float in(const float* __restrict__ p, int k) const {
 #ifdef __CUDA_ARCH__
-    return __ldg(p + k * ld + b);
+    return kNC ? __ldg(p + k * ld + b) : __ldcg(p + k * ld + b);
 #else
     return p[k * ld + b];
 #endif
   }
   FD void out(float* __restrict__ p, int k, float v) const { p[k * ld + b] = v; }
 };
+using Col = ColT<true>;
 
 template <class GT>
 FD SV gravity_acc(const GT* g) { return SV{mk(0, 0, 0), mk(-g[0], -g[1], -g[2])}; }
@@ -70,8 +75,8 @@ struct RootPose {
   float E[9];
   V3 r;
 };
-template <class Img>
-FD RootPose root_pose(const Img& M, const float* q, const Col& c) {
+template <class Img, class C>
+FD RootPose root_pose(const Img& M, const float* q, const C& c) {
   float Rq[9];
   quat_to_R(c.in(q, 3), c.in(q, 4), c.in(q, 5), c.in(q, 6), Rq);
   RootPose P;
@@ -80,10 +85,12 @@ FD RootPose root_pose(const Img& M, const float* q, const Col& c) {
   P.r = mk(M.body[0].p[0], M.body[0].p[1], M.body[0].p[2]) + rot(M.body[0].R, pq);
   return P;
 }
-FD SV load6(const float* p, int k0, const Col& c) {
+template <class C>
+FD SV load6(const float* p, int k0, const C& c) {
   return SV{mk(c.in(p, k0), c.in(p, k0 + 1), c.in(p, k0 + 2)), mk(c.in(p, k0 + 3), c.in(p, k0 + 4), c.in(p, k0 + 5))};
 }
-FD void store6(float* p, int k0, const Col& c, const SV& v) {
+template <class C>
+FD void store6(float* p, int k0, const C& c, const SV& v) {
   c.out(p, k0, v.w.x); c.out(p, k0 + 1, v.w.y); c.out(p, k0 + 2, v.w.z);
   c.out(p, k0 + 3, v.v.x); c.out(p, k0 + 4, v.v.y); c.out(p, k0 + 5, v.v.z);
 }
@@ -94,9 +101,9 @@ struct Frames {
   int body[8];
 };
 
-template <class T, class Img>
+template <class T, class Img, class C>
 FD void fk_one(const Img& M, const float* __restrict__ q, float* __restrict__ pose, const Frames& fr,
-               float* __restrict__ J, const Col& col) {
+               float* __restrict__ J, const C& col) {
   const int nb = T::nb(M);
   float Rw[T::NBMAX][9];  // world rotation of the internal frames
   V3 pw[T::NBMAX];
@@ -190,9 +197,9 @@ FD void fk_one(const Img& M, const float* __restrict__ q, float* __restrict__ po
 }
 
 // ====================================================================== RNEA
-template <class T, class Img>
+template <class T, class Img, class C>
 FD void rnea_one(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
-                 const float* __restrict__ qdd, float* __restrict__ tau, const Col& col) {
+                 const float* __restrict__ qdd, float* __restrict__ tau, const C& col) {
   const int nb = T::nb(M);
   SV v[T::NBMAX], a[T::NBMAX], f[T::NBMAX];
   float cq[T::NBMAX], sq[T::NBMAX];
@@ -245,9 +252,9 @@ struct MSink {
   FD static int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 };
 
-template <class T, class Img>
+template <class T, class Img, class C>
 FD void crba_one(const Img& M, const float* __restrict__ q, float* __restrict__ Mout,
-                 float* __restrict__ LD, const Col& col) {
+                 float* __restrict__ LD, const C& col) {
   const int nb = T::nb(M);
   const int nv = T::kFree ? nb + 5 : nb;
   float cq[T::NBMAX], sq[T::NBMAX];
@@ -282,13 +289,13 @@ FD void crba_one(const Img& M, const float* __restrict__ q, float* __restrict__ 
     if (i >= nb) break;
     if (T::kFree && i == 0) {
       // 6x6 block = the root composite inertia [[I, [h]x], [[h]x^T, m 1]]
-      const RBI& C = Ic[0];
-      const float blk[6][6] = {{C.xx, C.xy, C.xz, 0.f, -C.h.z, C.h.y},
-                               {C.xy, C.yy, C.yz, C.h.z, 0.f, -C.h.x},
-                               {C.xz, C.yz, C.zz, -C.h.y, C.h.x, 0.f},
-                               {0.f, C.h.z, -C.h.y, C.m, 0.f, 0.f},
-                               {-C.h.z, 0.f, C.h.x, 0.f, C.m, 0.f},
-                               {C.h.y, -C.h.x, 0.f, 0.f, 0.f, C.m}};
+      const RBI& Cc = Ic[0];
+      const float blk[6][6] = {{Cc.xx, Cc.xy, Cc.xz, 0.f, -Cc.h.z, Cc.h.y},
+                               {Cc.xy, Cc.yy, Cc.yz, Cc.h.z, 0.f, -Cc.h.x},
+                               {Cc.xz, Cc.yz, Cc.zz, -Cc.h.y, Cc.h.x, 0.f},
+                               {0.f, Cc.h.z, -Cc.h.y, Cc.m, 0.f, 0.f},
+                               {-Cc.h.z, 0.f, Cc.h.x, 0.f, Cc.m, 0.f},
+                               {Cc.h.y, -Cc.h.x, 0.f, 0.f, 0.f, Cc.m}};
 #pragma unroll
       for (int r = 0; r < 6; ++r)
 #pragma unroll
@@ -296,8 +303,8 @@ FD void crba_one(const Img& M, const float* __restrict__ q, float* __restrict__ 
       continue;
     }
     const int di = iv_of<T>(i);
-    const RBI& C = Ic[i];
-    SV F{mk(C.xz, C.yz, C.zz), mk(-C.h.y, C.h.x, 0.f)};  // I^c_i e_z
+    const RBI& Cc = Ic[i];
+    SV F{mk(Cc.xz, Cc.yz, Cc.zz), mk(-Cc.h.y, Cc.h.x, 0.f)};  // I^c_i e_z
     put(di, di, F.w.z);
     int j = i;
     uint64_t done = 1ull << i;
@@ -417,9 +424,9 @@ FD SV spd6_solve(const AI& I, const SV& rhs) {
 // Articulated-body algorithm. With `with_velocity` false the same sweeps solve
 // M x = rhs (zero velocity, no gravity): the M^-1 of the ABA adjoint.
 // rhs_at(i) gives tau for revolute body i; rhs0 the root wrench.
-template <class T, class Img, bool VEL, class Rhs, class Out>
+template <class T, class Img, bool VEL, class Rhs, class Out, class C>
 FD void aba_core(const Img& M, const float* __restrict__ q, const float* __restrict__ qd, const Rhs& rhs_at,
-                 const Out& out_at, const Col& col) {
+                 const Out& out_at, const C& col) {
   const int nb = T::nb(M);
   float cq[T::NBMAX], sq[T::NBMAX];
   SV v[T::NBMAX], cb[T::NBMAX], pA[T::NBMAX], U[T::NBMAX], a[T::NBMAX];
@@ -492,25 +499,25 @@ FD void aba_core(const Img& M, const float* __restrict__ q, const float* __restr
   }
 }
 
-template <class T>
+template <class T, class C>
 struct RhsFromGlobal {
   const float* p;
-  Col col;
+  C col;
   FD float operator()(int i) const { return col.in(p, iv_of<T>(i)); }
   FD SV root() const { return load6(p, 0, col); }
 };
-template <class T>
+template <class T, class C>
 struct OutToGlobal {
   float* p;
-  Col col;
+  C col;
   FD void operator()(int i, float x) const { col.out(p, iv_of<T>(i), x); }
   FD void root(const SV& x) const { store6(p, 0, col, x); }
 };
 
-template <class T, class Img>
+template <class T, class Img, class C>
 FD void aba_one(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
-                const float* __restrict__ tau, float* __restrict__ qdd, const Col& col) {
-  aba_core<T, Img, true>(M, q, qd, RhsFromGlobal<T>{tau, col}, OutToGlobal<T>{qdd, col}, col);
+                const float* __restrict__ tau, float* __restrict__ qdd, const C& col) {
+  aba_core<T, Img, true>(M, q, qd, RhsFromGlobal<T, C>{tau, col}, OutToGlobal<T, C>{qdd, col}, col);
 }
 
 // ================================================================ RNEA VJP
@@ -521,9 +528,9 @@ FD void aba_one(const Img& M, const float* __restrict__ q, const float* __restri
 //          + sum X_c^T vbar_c;
 // qbar_i = Fb_i.(e x* F_i) - abar_i.(e x X_i a_par) - vbar_i.(e x X_i v_par),
 // qdbar_i = e.vbar_i + abar_i.(v_i x e), qddbar_i = e.abar_i.
-template <class T, class Img, class Seed, class Sink>
+template <class T, class Img, class Seed, class Sink, class C>
 FD void rnea_vjp_core(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
-                      const float* __restrict__ qdd, const Seed& gb_at, const Sink& sink, const Col& col) {
+                      const float* __restrict__ qdd, const Seed& gb_at, const Sink& sink, const C& col) {
   const int nb = T::nb(M);
   float cq[T::NBMAX], sq[T::NBMAX];
   SV v[T::NBMAX], xa[T::NBMAX], F[T::NBMAX], Fb[T::NBMAX], ab[T::NBMAX], vb[T::NBMAX];
@@ -593,14 +600,14 @@ FD void rnea_vjp_core(const Img& M, const float* __restrict__ q, const float* __
 // root's tangent q-gradient goes to the ambient layout: position slots get
 // R * 0 (tau does not depend on the root position) and the quaternion slots
 // 2 quat (x) [w_bar; 0].
-template <class T>
+template <class T, class C>
 struct VjpToGlobal {
   float* qbar;
   float* qdbar;
   float* qddbar;
   float sign;
   float quat[4];
-  Col col;
+  C col;
   FD void operator()(int i, float qb, float qdb, float qddb) const {
     if (qbar) col.out(qbar, iq_of<T>(i), sign * qb);
     if (qdbar) col.out(qdbar, iv_of<T>(i), sign * qdb);
@@ -626,10 +633,10 @@ struct VjpToGlobal {
   }
 };
 
-template <class T, class Img>
-FD VjpToGlobal<T> vjp_sink(const Img& M, const float* q, float* qbar, float* qdbar, float* qddbar,
-                           float sign, const Col& col) {
-  VjpToGlobal<T> s{qbar, qdbar, qddbar, sign, {0, 0, 0, 1}, col};
+template <class T, class Img, class C>
+FD VjpToGlobal<T, C> vjp_sink(const Img& M, const float* q, float* qbar, float* qdbar, float* qddbar,
+                              float sign, const C& col) {
+  VjpToGlobal<T, C> s{qbar, qdbar, qddbar, sign, {0, 0, 0, 1}, col};
   if (T::kFree) {
     s.quat[0] = col.in(q, 3);
     s.quat[1] = col.in(q, 4);
@@ -639,10 +646,10 @@ FD VjpToGlobal<T> vjp_sink(const Img& M, const float* q, float* qbar, float* qdb
   return s;
 }
 
-template <class T, class Img>
+template <class T, class Img, class C>
 FD void rnea_vjp_one(const Img& M, const float* q, const float* qd, const float* qdd, const float* gbar,
-                     float* qbar, float* qdbar, float* qddbar, const Col& col) {
-  rnea_vjp_core<T>(M, q, qd, qdd, RhsFromGlobal<T>{gbar, col}, vjp_sink<T>(M, q, qbar, qdbar, qddbar, 1.f, col),
+                     float* qbar, float* qdbar, float* qddbar, const C& col) {
+  rnea_vjp_core<T>(M, q, qd, qdd, RhsFromGlobal<T, C>{gbar, col}, vjp_sink<T>(M, q, qbar, qdbar, qddbar, 1.f, col),
                    col);
 }
 
@@ -665,12 +672,12 @@ struct OutToLocal {
   }
 };
 
-template <class T, class Img>
+template <class T, class Img, class C>
 FD void aba_vjp_one(const Img& M, const float* q, const float* qd, const float* tau, const float* qdd,
-                    const float* gbar, float* qbar, float* qdbar, float* taubar, const Col& col) {
+                    const float* gbar, float* qbar, float* qdbar, float* taubar, const C& col) {
   (void)tau;  // the derivative is evaluated at the saved qdd = ABA(q, qd, tau)
   LocalVec<T> w;
-  aba_core<T, Img, false>(M, q, qd, RhsFromGlobal<T>{gbar, col}, OutToLocal<T>{&w}, col);
+  aba_core<T, Img, false>(M, q, qd, RhsFromGlobal<T, C>{gbar, col}, OutToLocal<T>{&w}, col);
   const int nv = T::kFree ? T::nb(M) + 5 : T::nb(M);
   if (taubar) {
 #pragma unroll(T::kStatic ? T::NVMAX : 1)

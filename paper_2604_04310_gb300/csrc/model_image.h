@@ -25,7 +25,7 @@ struct BodyImage {
 };
 
 template <int NB>
-struct ModelImage {
+struct alignas(16) ModelImage {
   int32_t nb, nq, nv, free_root;
   float g[3];                       // world gravity
   int8_t parent[NB];                // parent body, -1 = world

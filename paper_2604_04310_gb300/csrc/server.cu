@@ -1,0 +1,617 @@
+// Serving: a persistent kernel that continuously batches dynamics requests
+// for many robots. Requests are carved from one HBM slab (admission by
+// budget), described in a device ring, and split into 128-instance tiles.
+// Each resident CTA claims the next published tile with a CAS on one global
+// counter, finds its request, runs the op for its 128 instances (the same
+// per-instance device code as the batched kernels) and, as the last tile of
+// a request finishes, raises the request's completion flag in mapped host
+// memory. Every device wait is bounded: a CTA that sees no work for
+// idle_exit_ms returns; the host relaunches the kernel when work is pending
+// and it is not running.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "dyn.cuh"
+#include "handles.h"
+
+namespace frax {
+namespace {
+
+constexpr int kRing = FRAX_SERVER_RING;
+constexpr int kMaxModels = FRAX_SERVER_MAX_MODELS;
+constexpr int kTile = 128;
+constexpr int64_t kAlign = 256;
+
+enum ServeKind { kServeChain7 = 0, kServeTree = 1, kServeTreeFree = 2 };
+enum DeviceError { kDevOk = 0, kDevBadOp = 1, kDevLookup = 2 };
+
+struct ReqDesc {
+  long long tile_begin, tile_end;  // global tile range of the request
+  long long B;
+  long long seq;                   // request number
+  int model_id, op, kind, slot;
+  unsigned long long in_off[4], out_off[3];
+};
+
+struct ServeCtl {
+  unsigned long long next_tile;        // tiles claimed so far (monotonic)
+  unsigned long long tiles_published;  // tiles whose request is visible
+  unsigned int stop;                   // set by the host to end the kernel
+  unsigned int pad;
+  unsigned int done[kRing];            // finished tiles of the request in each slot
+};
+
+struct ServeArgs {
+  const ReqDesc* ring;
+  ServeCtl* ctl;
+  const ModelImage<64>* models;
+  char* slab;
+  unsigned long long* flags;  // mapped host memory: seq + 1 once done
+  int* status;                // mapped host memory: first device error
+  unsigned long long idle_ns;
+  long long first_req;        // oldest request possibly owning unclaimed tiles
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+template <class T>
+__device__ void serve_tile(const ModelImage<64>& M, const ReqDesc& d, char* slab, long long b) {
+  const ColT<false> col{d.B, b};
+  auto in = [&](int k) { return reinterpret_cast<const float*>(slab + d.in_off[k]); };
+  auto out = [&](int k) { return reinterpret_cast<float*>(slab + d.out_off[k]); };
+  switch (d.op) {
+    case FRAX_OP_RNEA: rnea_one<T>(M, in(0), in(1), in(2), out(0), col); break;
+    case FRAX_OP_CRBA: crba_one<T>(M, in(0), out(0), static_cast<float*>(nullptr), col); break;
+    case FRAX_OP_ABA: aba_one<T>(M, in(0), in(1), in(2), out(0), col); break;
+    case FRAX_OP_RNEA_GRAD: rnea_vjp_one<T>(M, in(0), in(1), in(2), in(3), out(0), out(1), out(2), col); break;
+    default: break;
+  }
+}
+
+__global__ void __launch_bounds__(kTile) k_serve(const ServeArgs a) {
+  __shared__ ModelImage<64> model;
+  __shared__ ReqDesc desc;
+  __shared__ long long s_tile;
+  long long hint = a.first_req;  // per-CTA request cursor (thread 0 only)
+  while (true) {
+    if (threadIdx.x == 0) {
+      long long got = -1;
+      const unsigned long long t0 = global_ns();
+      while (true) {
+        const unsigned long long pub = ld_volatile(&a.ctl->tiles_published);
+        const unsigned long long cur = ld_volatile(&a.ctl->next_tile);
+        if (cur < pub) {
+          if (atomicCAS(&a.ctl->next_tile, cur, cur + 1) == cur) {
+            got = static_cast<long long>(cur);
+            break;
+          }
+          continue;
+        }
+        if (*reinterpret_cast<volatile unsigned int*>(&a.ctl->stop)) break;
+        if (global_ns() - t0 > a.idle_ns) break;  // bounded idle wait
+        __nanosleep(500);
+      }
+      if (got >= 0) {
+        // find the request that owns tile `got`: ranges grow with the request
+        // number, and the owner is still in flight, so its slot is intact
+        long long r = hint;
+        bool found = false;
+        for (int it = 0; it < 4 * kRing + 4; ++it, ++r) {
+          const ReqDesc* rd = &a.ring[r % kRing];
+          const long long seq = __ldcg(&rd->seq);
+          if (seq == r && got >= __ldcg(&rd->tile_begin) && got < __ldcg(&rd->tile_end)) {
+            found = true;
+            break;
+          }
+        }
+        if (!found) {
+          atomicCAS(a.status, kDevOk, kDevLookup);
+          __threadfence_system();
+          got = -1;
+        } else {
+          hint = r;
+          const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&a.ring[r % kRing]);
+          unsigned long long* dst = reinterpret_cast<unsigned long long*>(&desc);
+          for (int k = 0; k < int(sizeof(ReqDesc) / 8); ++k) dst[k] = __ldcg(src + k);
+        }
+      }
+      s_tile = got;
+    }
+    __syncthreads();
+    const long long t = s_tile;
+    if (t < 0) return;
+    // stage the request's model image in shared memory
+    {
+      const float4* src = reinterpret_cast<const float4*>(&a.models[desc.model_id]);
+      float4* dst = reinterpret_cast<float4*>(&model);
+      for (int k = threadIdx.x; k < int(sizeof(ModelImage<64>) / 16); k += kTile) dst[k] = __ldcg(src + k);
+    }
+    __syncthreads();
+    const long long b = (t - desc.tile_begin) * kTile + threadIdx.x;
+    if (b < desc.B) {
+      if (desc.op < FRAX_OP_RNEA || desc.op > FRAX_OP_RNEA_GRAD) {
+        if (threadIdx.x == 0) atomicCAS(a.status, kDevOk, kDevBadOp);
+      } else if (desc.kind == kServeChain7) {
+        serve_tile<ChainTopo<7>>(model, desc, a.slab, b);
+      } else if (desc.kind == kServeTreeFree) {
+        serve_tile<TreeTopo<64, true>>(model, desc, a.slab, b);
+      } else {
+        serve_tile<TreeTopo<64, false>>(model, desc, a.slab, b);
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int ntiles = static_cast<unsigned int>(desc.tile_end - desc.tile_begin);
+      const unsigned int prev = atomicAdd(&a.ctl->done[desc.slot], 1u);
+      if (prev + 1 == ntiles) {
+        a.ctl->done[desc.slot] = 0;
+        __threadfence_system();
+        *reinterpret_cast<volatile unsigned long long*>(&a.flags[desc.slot]) =
+            static_cast<unsigned long long>(desc.seq) + 1ull;
+        __threadfence_system();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int op_arrays(int op, int nq, int nv, int* in_rows, int* out_rows, int* nin, int* nout) {
+  switch (op) {
+    case FRAX_OP_RNEA:
+      *nin = 3; in_rows[0] = nq; in_rows[1] = nv; in_rows[2] = nv;
+      *nout = 1; out_rows[0] = nv;
+      return 0;
+    case FRAX_OP_CRBA:
+      *nin = 1; in_rows[0] = nq;
+      *nout = 1; out_rows[0] = nv * nv;
+      return 0;
+    case FRAX_OP_ABA:
+      *nin = 3; in_rows[0] = nq; in_rows[1] = nv; in_rows[2] = nv;
+      *nout = 1; out_rows[0] = nv;
+      return 0;
+    case FRAX_OP_RNEA_GRAD:
+      *nin = 4; in_rows[0] = nq; in_rows[1] = nv; in_rows[2] = nv; in_rows[3] = nv;
+      *nout = 3; out_rows[0] = nq; out_rows[1] = nv; out_rows[2] = nv;
+      return 0;
+    default:
+      return -1;
+  }
+}
+
+int64_t round_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+}  // namespace frax
+
+using namespace frax;
+
+struct frax_server_s {
+  struct Req {
+    int64_t seq = 0;
+    int slot = 0, op = 0, model = 0, nin = 0, nout = 0;
+    int64_t B = 0, off = 0, bytes = 0, ntiles = 0;
+    int out_rows[3] = {0, 0, 0};
+    int64_t out_off[3] = {0, 0, 0};
+    std::chrono::steady_clock::time_point t0;
+    bool done = false;
+    double latency_us = 0;
+  };
+  std::mutex mu;
+  int device = 0;
+  cudaStream_t kstream = nullptr, cstream = nullptr;
+  char* slab = nullptr;
+  int64_t budget = 0, in_use = 0;
+  ReqDesc* ring = nullptr;
+  ServeCtl* ctl = nullptr;
+  ModelImage<64>* models = nullptr;
+  unsigned long long* flags_h = nullptr;
+  unsigned long long* flags_d = nullptr;
+  int* status_h = nullptr;
+  int* status_d = nullptr;
+  ReqDesc* desc_stage = nullptr;          // pinned
+  unsigned long long* pub_stage = nullptr;  // pinned, one per slot
+  ModelImage<64>* model_stage = nullptr;    // pinned
+  int n_models = 0;
+  int model_kind[kMaxModels] = {};
+  int model_nq[kMaxModels] = {};
+  int model_nv[kMaxModels] = {};
+  std::map<int64_t, int64_t> free_list;  // offset -> size
+  std::map<int64_t, Req> inflight;
+  int64_t slot_owner[kRing];
+  int64_t next_seq = 0, tiles_total = 0;
+  int64_t submitted = 0, completed = 0, launches = 0;
+  int ctas = 0;
+  double idle_ms = 50.0;
+  bool kernel_ever = false;
+};
+
+namespace {
+
+frax_status cuda_fail(const char* what, cudaError_t e) {
+  return set_error(FRAX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SRV_CUDA(call)                                       \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(#call, e_);      \
+  } while (0)
+
+bool kernel_running(frax_server_s* s) {
+  cudaError_t e = cudaStreamQuery(s->kstream);
+  if (e == cudaErrorNotReady) return true;
+  if (e != cudaSuccess) cudaGetLastError();
+  return false;
+}
+
+// Relaunches the persistent kernel if work is pending and it is not running.
+frax_status ensure_running(frax_server_s* s) {
+  if (s->inflight.empty() || kernel_running(s)) return FRAX_OK;
+  int64_t first = s->next_seq;
+  for (auto& kv : s->inflight)
+    if (!kv.second.done) first = std::min(first, kv.first);
+  ServeArgs a;
+  a.ring = s->ring;
+  a.ctl = s->ctl;
+  a.models = s->models;
+  a.slab = s->slab;
+  a.flags = s->flags_d;
+  a.status = s->status_d;
+  a.idle_ns = static_cast<unsigned long long>(s->idle_ms * 1e6);
+  a.first_req = first;
+  k_serve<<<s->ctas, kTile, 0, s->kstream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail("k_serve launch", e);
+  s->launches++;
+  s->kernel_ever = true;
+  return FRAX_OK;
+}
+
+bool slab_alloc(frax_server_s* s, int64_t bytes, int64_t* off) {
+  for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
+    if (it->second >= bytes) {
+      *off = it->first;
+      int64_t rest = it->second - bytes;
+      int64_t start = it->first + bytes;
+      s->free_list.erase(it);
+      if (rest > 0) s->free_list[start] = rest;
+      s->in_use += bytes;
+      return true;
+    }
+  }
+  return false;
+}
+
+void slab_free(frax_server_s* s, int64_t off, int64_t bytes) {
+  s->in_use -= bytes;
+  auto it = s->free_list.emplace(off, bytes).first;
+  auto nx = std::next(it);
+  if (nx != s->free_list.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    s->free_list.erase(nx);
+  }
+  if (it != s->free_list.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      s->free_list.erase(it);
+    }
+  }
+}
+
+void release_all(frax_server_s* s) {
+  if (s->slab) cudaFree(s->slab);
+  if (s->ring) cudaFree(s->ring);
+  if (s->ctl) cudaFree(s->ctl);
+  if (s->models) cudaFree(s->models);
+  if (s->flags_h) cudaFreeHost(s->flags_h);
+  if (s->status_h) cudaFreeHost(s->status_h);
+  if (s->desc_stage) cudaFreeHost(s->desc_stage);
+  if (s->pub_stage) cudaFreeHost(s->pub_stage);
+  if (s->model_stage) cudaFreeHost(s->model_stage);
+  if (s->kstream) cudaStreamDestroy(s->kstream);
+  if (s->cstream) cudaStreamDestroy(s->cstream);
+}
+
+// Marks requests whose completion flag is up; returns how many were new.
+int scan_flags(frax_server_s* s, int64_t* first_done) {
+  int n = 0;
+  for (auto& kv : s->inflight) {
+    auto& r = kv.second;
+    if (r.done) continue;
+    volatile unsigned long long* f = s->flags_h + r.slot;
+    if (*f == static_cast<unsigned long long>(r.seq) + 1ull) {
+      r.done = true;
+      r.latency_us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - r.t0).count();
+      s->completed++;
+      if (n == 0 && first_done) *first_done = r.seq;
+      ++n;
+    }
+  }
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+frax_status frax_server_create(int64_t budget_bytes, double idle_exit_ms, frax_server_t* out) {
+  if (!out) return set_error(FRAX_EINVAL, "frax_server_create: out is NULL");
+  *out = nullptr;
+  if (budget_bytes < kAlign) return set_error(FRAX_EINVAL, "frax_server_create: budget_bytes too small");
+  if (!(idle_exit_ms > 0) || idle_exit_ms > 60000)
+    return set_error(FRAX_EINVAL, "frax_server_create: idle_exit_ms must be in (0, 60000]");
+  frax_server_s* s = new (std::nothrow) frax_server_s;
+  if (!s) return set_error(FRAX_ENOMEM, "frax_server_create: out of host memory");
+  s->budget = round_up(budget_bytes);
+  s->idle_ms = idle_exit_ms;
+  for (auto& o : s->slot_owner) o = -1;
+  auto bail = [&](frax_status st) {
+    release_all(s);
+    delete s;
+    return st;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&s->device)) != cudaSuccess) return bail(cuda_fail("cudaGetDevice", e));
+  if ((e = cudaMalloc(&s->slab, s->budget)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(set_error(FRAX_ENOMEM, "frax_server_create: slab of budget_bytes does not fit on the device"));
+  }
+  if ((e = cudaMalloc(&s->ring, sizeof(ReqDesc) * kRing)) != cudaSuccess) return bail(cuda_fail("cudaMalloc ring", e));
+  if ((e = cudaMalloc(&s->ctl, sizeof(ServeCtl))) != cudaSuccess) return bail(cuda_fail("cudaMalloc ctl", e));
+  if ((e = cudaMalloc(&s->models, sizeof(ModelImage<64>) * kMaxModels)) != cudaSuccess)
+    return bail(cuda_fail("cudaMalloc models", e));
+  if ((e = cudaMemset(s->ring, 0xff, sizeof(ReqDesc) * kRing)) != cudaSuccess) return bail(cuda_fail("memset", e));
+  if ((e = cudaMemset(s->ctl, 0, sizeof(ServeCtl))) != cudaSuccess) return bail(cuda_fail("memset", e));
+  if ((e = cudaHostAlloc(&s->flags_h, sizeof(unsigned long long) * kRing, cudaHostAllocMapped)) != cudaSuccess)
+    return bail(cuda_fail("cudaHostAlloc flags", e));
+  if ((e = cudaHostAlloc(&s->status_h, sizeof(int), cudaHostAllocMapped)) != cudaSuccess)
+    return bail(cuda_fail("cudaHostAlloc status", e));
+  if ((e = cudaHostAlloc(&s->desc_stage, sizeof(ReqDesc) * kRing, cudaHostAllocDefault)) != cudaSuccess)
+    return bail(cuda_fail("cudaHostAlloc", e));
+  if ((e = cudaHostAlloc(&s->pub_stage, sizeof(unsigned long long) * kRing, cudaHostAllocDefault)) != cudaSuccess)
+    return bail(cuda_fail("cudaHostAlloc", e));
+  if ((e = cudaHostAlloc(&s->model_stage, sizeof(ModelImage<64>), cudaHostAllocDefault)) != cudaSuccess)
+    return bail(cuda_fail("cudaHostAlloc", e));
+  std::memset(s->flags_h, 0, sizeof(unsigned long long) * kRing);
+  *s->status_h = 0;
+  if ((e = cudaHostGetDevicePointer(&s->flags_d, s->flags_h, 0)) != cudaSuccess) return bail(cuda_fail("map", e));
+  if ((e = cudaHostGetDevicePointer(&s->status_d, s->status_h, 0)) != cudaSuccess) return bail(cuda_fail("map", e));
+  if ((e = cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail("stream", e));
+  if ((e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail("stream", e));
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, kTile, 0);
+  s->ctas = std::max(1, sms) * std::max(1, std::min(per_sm, 2));
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(cuda_fail("sync", e));
+  s->free_list[0] = s->budget;
+  *out = s;
+  return clear_error();
+}
+
+frax_status frax_server_add_model(frax_server_t s, frax_model_t model, int* model_id) {
+  if (!s || !model || !model_id) return set_error(FRAX_EINVAL, "frax_server_add_model: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->n_models >= kMaxModels) return set_error(FRAX_ENOMEM, "frax_server_add_model: model table full");
+  const HostModel& m = model->m;
+  m.pack(s->model_stage);
+  const int id = s->n_models;
+  SRV_CUDA(cudaMemcpyAsync(s->models + id, s->model_stage, sizeof(ModelImage<64>), cudaMemcpyHostToDevice,
+                           s->cstream));
+  SRV_CUDA(cudaStreamSynchronize(s->cstream));
+  s->model_kind[id] = m.kind == kKindChain ? kServeChain7 : (m.free_root ? kServeTreeFree : kServeTree);
+  s->model_nq[id] = m.nq;
+  s->model_nv[id] = m.nv;
+  s->n_models++;
+  *model_id = id;
+  return clear_error();
+}
+
+frax_status frax_server_submit(frax_server_t s, int model_id, int op, int64_t B, const float* const* inputs,
+                               int64_t* request) {
+  if (!s || !request) return set_error(FRAX_EINVAL, "frax_server_submit: NULL argument");
+  const auto t_arrive = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (model_id < 0 || model_id >= s->n_models) return set_error(FRAX_EINVAL, "frax_server_submit: bad model_id");
+  if (B < 1 || B > (int64_t(1) << 24)) return set_error(FRAX_EINVAL, "frax_server_submit: B must be in [1, 2^24]");
+  int in_rows[4], out_rows[3], nin, nout;
+  if (op_arrays(op, s->model_nq[model_id], s->model_nv[model_id], in_rows, out_rows, &nin, &nout) != 0)
+    return set_error(FRAX_EINVAL, "frax_server_submit: unknown op");
+  if (!inputs) return set_error(FRAX_EINVAL, "frax_server_submit: inputs is NULL");
+  for (int k = 0; k < nin; ++k)
+    if (!inputs[k]) return set_error(FRAX_EINVAL, "frax_server_submit: an input array is NULL");
+  int64_t in_bytes[4], out_bytes[3], total = 0;
+  for (int k = 0; k < nin; ++k) total += (in_bytes[k] = round_up(int64_t(in_rows[k]) * B * 4));
+  for (int k = 0; k < nout; ++k) total += (out_bytes[k] = round_up(int64_t(out_rows[k]) * B * 4));
+  if (total > s->budget) return set_error(FRAX_ENOMEM, "frax_server_submit: request exceeds the whole HBM budget");
+  const int64_t seq = s->next_seq;
+  const int slot = static_cast<int>(seq % kRing);
+  if (s->slot_owner[slot] >= 0) return set_error(FRAX_EBUSY, "frax_server_submit: request ring full");
+  int64_t off;
+  if (!slab_alloc(s, total, &off)) return set_error(FRAX_EBUSY, "frax_server_submit: HBM budget in use");
+  ReqDesc& d = s->desc_stage[slot];
+  const int64_t ntiles = (B + kTile - 1) / kTile;
+  d.tile_begin = s->tiles_total;
+  d.tile_end = s->tiles_total + ntiles;
+  d.B = B;
+  d.seq = seq;
+  d.model_id = model_id;
+  d.op = op;
+  d.kind = s->model_kind[model_id];
+  d.slot = slot;
+  int64_t cur = off;
+  for (int k = 0; k < 4; ++k) d.in_off[k] = 0;
+  for (int k = 0; k < 3; ++k) d.out_off[k] = 0;
+  for (int k = 0; k < nin; ++k) {
+    d.in_off[k] = cur;
+    cudaError_t e = cudaMemcpyAsync(s->slab + cur, inputs[k], size_t(in_rows[k]) * B * 4, cudaMemcpyHostToDevice,
+                                    s->cstream);
+    if (e != cudaSuccess) {
+      slab_free(s, off, total);
+      return cuda_fail("frax_server_submit: input copy", e);
+    }
+    cur += in_bytes[k];
+  }
+  frax_server_s::Req r;
+  for (int k = 0; k < nout; ++k) {
+    d.out_off[k] = cur;
+    r.out_off[k] = cur;
+    r.out_rows[k] = out_rows[k];
+    cur += out_bytes[k];
+  }
+  s->pub_stage[slot] = static_cast<unsigned long long>(s->tiles_total + ntiles);
+  cudaError_t e = cudaMemcpyAsync(s->ring + slot, &d, sizeof(ReqDesc), cudaMemcpyHostToDevice, s->cstream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&s->ctl->tiles_published, &s->pub_stage[slot], sizeof(unsigned long long),
+                        cudaMemcpyHostToDevice, s->cstream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->cstream);
+  if (e != cudaSuccess) {
+    slab_free(s, off, total);
+    return cuda_fail("frax_server_submit: publish", e);
+  }
+  r.seq = seq;
+  r.slot = slot;
+  r.op = op;
+  r.model = model_id;
+  r.nin = nin;
+  r.nout = nout;
+  r.B = B;
+  r.off = off;
+  r.bytes = total;
+  r.ntiles = ntiles;
+  r.t0 = t_arrive;
+  s->inflight[seq] = r;
+  s->slot_owner[slot] = seq;
+  s->tiles_total += ntiles;
+  s->next_seq++;
+  s->submitted++;
+  *request = seq;
+  frax_status st = ensure_running(s);
+  if (st != FRAX_OK) return st;
+  return clear_error();
+}
+
+frax_status frax_server_poll(frax_server_t s, int64_t request, int* done) {
+  if (!s || !done) return set_error(FRAX_EINVAL, "frax_server_poll: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->inflight.find(request);
+  if (it == s->inflight.end()) return set_error(FRAX_EINVAL, "frax_server_poll: unknown request");
+  scan_flags(s, nullptr);
+  if (*s->status_h) return set_error(FRAX_EINTERNAL, "frax_server_poll: device error " + std::to_string(*s->status_h));
+  *done = it->second.done ? 1 : 0;
+  if (!*done) {
+    frax_status st = ensure_running(s);
+    if (st != FRAX_OK) return st;
+  }
+  return clear_error();
+}
+
+frax_status frax_server_wait_any(frax_server_t s, double timeout_ms, int64_t* request) {
+  if (!s || !request) return set_error(FRAX_EINVAL, "frax_server_wait_any: NULL argument");
+  const auto t_end = std::chrono::steady_clock::now() + std::chrono::microseconds(int64_t(timeout_ms * 1e3));
+  while (true) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      // a request already seen complete but not collected
+      for (auto& kv : s->inflight)
+        if (kv.second.done) {
+          *request = kv.first;
+          return clear_error();
+        }
+      if (s->inflight.empty()) return set_error(FRAX_EINVAL, "frax_server_wait_any: nothing in flight");
+      int64_t first = -1;
+      if (scan_flags(s, &first) > 0) {
+        *request = first;
+        return clear_error();
+      }
+      if (*s->status_h)
+        return set_error(FRAX_EINTERNAL, "frax_server_wait_any: device error " + std::to_string(*s->status_h));
+      frax_status st = ensure_running(s);
+      if (st != FRAX_OK) return st;
+    }
+    if (std::chrono::steady_clock::now() > t_end)
+      return set_error(FRAX_ETIMEOUT, "frax_server_wait_any: no request completed within the timeout");
+    std::this_thread::yield();
+  }
+}
+
+frax_status frax_server_collect(frax_server_t s, int64_t request, float* const* outputs, double* latency_us) {
+  if (!s) return set_error(FRAX_EINVAL, "frax_server_collect: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->inflight.find(request);
+  if (it == s->inflight.end()) return set_error(FRAX_EINVAL, "frax_server_collect: unknown request");
+  scan_flags(s, nullptr);
+  frax_server_s::Req& r = it->second;
+  if (!r.done) return set_error(FRAX_EBUSY, "frax_server_collect: request not complete");
+  if (outputs) {
+    for (int k = 0; k < r.nout; ++k) {
+      if (!outputs[k]) continue;
+      SRV_CUDA(cudaMemcpyAsync(outputs[k], s->slab + r.out_off[k], size_t(r.out_rows[k]) * r.B * 4,
+                               cudaMemcpyDeviceToHost, s->cstream));
+    }
+    SRV_CUDA(cudaStreamSynchronize(s->cstream));
+  }
+  if (latency_us) *latency_us = r.latency_us;
+  slab_free(s, r.off, r.bytes);
+  s->slot_owner[r.slot] = -1;
+  s->inflight.erase(it);
+  return clear_error();
+}
+
+frax_status frax_server_info(frax_server_t s, frax_server_info_t* info) {
+  if (!s || !info) return set_error(FRAX_EINVAL, "frax_server_info: NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  scan_flags(s, nullptr);
+  info->budget_bytes = s->budget;
+  info->bytes_in_use = s->in_use;
+  info->submitted = s->submitted;
+  info->completed = s->completed;
+  info->in_flight = static_cast<int64_t>(s->inflight.size());
+  info->kernel_launches = s->launches;
+  info->device_status = *s->status_h;
+  info->resident_ctas = s->ctas;
+  return clear_error();
+}
+
+frax_status frax_server_destroy(frax_server_t s, int force, double timeout_ms) {
+  if (!s) return clear_error();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    scan_flags(s, nullptr);
+    bool pending = false;
+    for (auto& kv : s->inflight) pending = pending || !kv.second.done;
+    if (pending && !force) return set_error(FRAX_EBUSY, "frax_server_destroy: requests still in flight");
+    static const unsigned int one = 1;
+    cudaMemcpyAsync(&s->ctl->stop, &one, sizeof(one), cudaMemcpyHostToDevice, s->cstream);
+    cudaStreamSynchronize(s->cstream);
+  }
+  const auto t_end = std::chrono::steady_clock::now() + std::chrono::microseconds(int64_t(timeout_ms * 1e3));
+  while (kernel_running(s)) {
+    if (std::chrono::steady_clock::now() > t_end)
+      return set_error(FRAX_ETIMEOUT, "frax_server_destroy: kernel did not stop in time; resources kept");
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  release_all(s);
+  delete s;
+  return clear_error();
+}
+
+}  // extern "C"
