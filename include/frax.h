@@ -220,6 +220,37 @@ FRAX_API frax_status frax_server_info(frax_server_t srv, frax_server_info_t* inf
  * freed under a running kernel). */
 FRAX_API frax_status frax_server_destroy(frax_server_t srv, int force, double timeout_ms);
 
+/* ------------------------------------------------------------------------
+ * frax_serve_batch_noalloc — one launch that evaluates a mixed batch of
+ * requests (different robots and ops, each with its own instance count) and
+ * allocates no memory at all. The paper has no counterpart; this exists for
+ * callers that may not allocate device memory: real-time control loops
+ * (cudaMalloc can block for an unbounded time and synchronise the device),
+ * and code running inside a framework that has already reserved nearly all
+ * of HBM for its own pool. It is the serving kernel's tile loop without the
+ * server: the caller passes device input and output buffers per request
+ * (SoA [rows][B], ld = B; arrays as listed for the FRAX_OP_* ops above).
+ *
+ * Scratch: a fixed device array inside the library (about 165 KB: up to
+ * FRAX_NOALLOC_MAX_REQUESTS descriptors and FRAX_NOALLOC_MAX_MODELS model
+ * images) that every GPU loading the library keeps until the process exits.
+ * Larger batches are rejected with FRAX_EINVAL. All calls on a device share
+ * it; each call rewrites what it uses and clears the tile counter first, so
+ * calls ordered on one stream are correct, but calls whose kernels overlap
+ * (unordered streams) race on it. The first call on each device looks up the
+ * array's address (cudaGetSymbolAddress) and caches it: make that first call
+ * before any stream capture. Asynchronous on `stream`.
+ * ---------------------------------------------------------------------- */
+enum { FRAX_NOALLOC_MAX_REQUESTS = 256, FRAX_NOALLOC_MAX_MODELS = 16 };
+typedef struct {
+  frax_model_t model;
+  int op;             /* FRAX_OP_RNEA, _CRBA, _ABA or _RNEA_GRAD */
+  int64_t B;          /* instances; 0 allowed                    */
+  const float* in[4]; /* device inputs, unused entries NULL      */
+  float* out[3];      /* device outputs, unused entries NULL     */
+} frax_batch_request_t;
+FRAX_API frax_status frax_serve_batch_noalloc(const frax_batch_request_t* reqs, int n_reqs, void* stream);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 FRAX_API const char* frax_last_error(void);
 

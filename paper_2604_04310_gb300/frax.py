@@ -217,6 +217,43 @@ def frax_aba_vjp(model: Model, q, qd, tau, qdd, gbar, qbar=None, qdbar=None, tau
     return qbar, qdbar, taubar
 
 
+# ------------------------------------------------------- allocation-free batch
+
+class BatchRequest(ctypes.Structure):
+    """frax_batch_request_t"""
+    _fields_ = [("model", ctypes.c_void_p), ("op", ctypes.c_int), ("B", ctypes.c_int64),
+                ("inputs", ctypes.c_void_p * 4), ("outputs", ctypes.c_void_p * 3)]
+
+
+NOALLOC_OPS = {"rnea": 0, "crba": 1, "aba": 2, "rnea_grad": 3}
+
+
+def frax_serve_batch_noalloc(requests):
+    """Evaluates a mixed batch in one launch without allocating: each request
+    is (model, op, inputs, outputs) with CUDA float32 tensors of shape
+    (rows, B), ld = B, supplied by the caller (outputs included)."""
+    n = len(requests)
+    arr = (BatchRequest * max(1, n))()
+    stream = None
+    for i, (model, op, inputs, outputs) in enumerate(requests):
+        r = arr[i]
+        r.model = model.handle.value
+        r.op = NOALLOC_OPS[op]
+        B = inputs[0].shape[1]
+        r.B = B
+        for k, t in enumerate(list(inputs) + list(outputs)):
+            if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2 or t.shape[1] != B or (
+                    B > 1 and t.stride(1) != 1) or (t.shape[0] > 1 and B > 0 and t.stride(0) != B):
+                raise FraxError(1, "frax_serve_batch_noalloc: tensors must be contiguous float32 CUDA (rows, B)")
+        for k, t in enumerate(inputs):
+            r.inputs[k] = t.data_ptr()
+        for k, t in enumerate(outputs):
+            r.outputs[k] = t.data_ptr()
+        stream = stream or _stream(inputs[0])
+    _check(lib().frax_serve_batch_noalloc(ctypes.cast(arr, ctypes.c_void_p), n,
+                                          stream if stream is not None else ctypes.c_void_p(0)))
+
+
 # ------------------------------------------------------------- autograd wrappers
 
 class RneaFn(torch.autograd.Function):
