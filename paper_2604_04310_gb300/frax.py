@@ -107,10 +107,9 @@ def _soa(t, rows, name, ld=None, B=None):
         return None
     if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
         raise FraxError(1, f"{name} must be a float32 CUDA tensor")
-    if t.dim() != 2 or t.shape[0] != rows or (t.shape[0] > 1 and t.stride(1) != 1) or (
-            t.shape[0] > 0 and t.shape[1] > 1 and t.stride(1) != 1):
+    if t.dim() != 2 or t.shape[0] != rows or (rows > 0 and t.shape[1] > 1 and t.stride(1) != 1):
         raise FraxError(1, f"{name} must have shape ({rows}, B) with unit stride along B")
-    if ld is not None and rows > 1 and t.stride(0) != ld:
+    if ld is not None and rows > 1 and t.shape[1] > 0 and t.stride(0) != ld:
         raise FraxError(1, f"{name}: every tensor of one call must share the same leading dimension")
     if B is not None and t.shape[1] != B:
         raise FraxError(1, f"{name}: batch size {t.shape[1]} != {B}")
@@ -118,7 +117,7 @@ def _soa(t, rows, name, ld=None, B=None):
 
 
 def _ld(t):
-    return t.stride(0) if t.shape[0] > 1 else t.shape[1]
+    return t.stride(0) if t.shape[0] > 1 and t.shape[1] > 0 else t.shape[1]
 
 
 def _out(rows, like, ld, B):

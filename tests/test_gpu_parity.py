@@ -169,6 +169,9 @@ def test_empty_batch_is_noop(fxm):
     h = fxm["chain7"]
     z = torch.empty((7, 0), device="cuda")
     assert fx.frax_rnea(h, torch.empty((7, 0), device="cuda"), z, z).shape == (7, 0)
+    e = dev(np.zeros((0, 7)))  # empty arrays made the way the other tests make inputs
+    assert fx.frax_crba(h, e)[0].shape == (49, 0)
+    assert fx.frax_aba(h, e, e, e).shape == (7, 0)
 
 
 def test_argument_errors(fxm):
