@@ -38,7 +38,7 @@ inline CF sqrtf(CF a) { g.sfu++; return CF(std::sqrt(a.v)); }
 inline void sincosf(CF x, CF* s, CF* c) { g.sfu++; s->v = std::sin(x.v); c->v = std::cos(x.v); }
 
 #define float CF
-#include "paper_2604_04310_gb300/csrc/dyn.cuh"
+#include "paper_2604_04310_gb300/csrc/seg.cuh"
 #undef float
 
 using namespace frax;
@@ -58,13 +58,24 @@ void count(const Img& M, int nf, const int* frames) {
     g = Counts{};
   };
   g = Counts{};
-  fk_one<T>(M, q.data(), o1.data(), fr, o2.data(), col); rep("fk_jac");
-  fk_one<T>(M, q.data(), o1.data(), Frames{0, {0}}, nullptr, col); rep("fk");
-  rnea_one<T>(M, q.data(), qd.data(), qdd.data(), o6.data(), col); rep("rnea");
-  rnea_one<T>(M, q.data(), qd.data(), nullptr, o6.data(), col); rep("bias");
-  crba_one<T>(M, q.data(), o3.data(), o4.data(), col); rep("crba_ltdl");
-  crba_one<T>(M, q.data(), o3.data(), nullptr, col); rep("crba");
-  aba_one<T>(M, q.data(), qd.data(), tau.data(), o6.data(), col); rep("aba");
+  if constexpr (T::kSeg) {
+    static P3Local<T::NBMAX> P3;
+    fk_seg<T>(M, q.data(), o1.data(), fr, o2.data(), col); rep("fk_jac");
+    fk_seg<T>(M, q.data(), o1.data(), Frames{0, {0}}, nullptr, col); rep("fk");
+    rnea_seg<T>(M, q.data(), qd.data(), qdd.data(), o6.data(), col); rep("rnea");
+    rnea_seg<T>(M, q.data(), qd.data(), nullptr, o6.data(), col); rep("bias");
+    crba_seg<T>(M, q.data(), o3.data(), o4.data(), col); rep("crba_ltdl");
+    crba_seg<T>(M, q.data(), o3.data(), nullptr, col); rep("crba");
+    aba_seg<T>(M, q.data(), qd.data(), tau.data(), o6.data(), col, P3); rep("aba");
+  } else {
+    fk_one<T>(M, q.data(), o1.data(), fr, o2.data(), col); rep("fk_jac");
+    fk_one<T>(M, q.data(), o1.data(), Frames{0, {0}}, nullptr, col); rep("fk");
+    rnea_one<T>(M, q.data(), qd.data(), qdd.data(), o6.data(), col); rep("rnea");
+    rnea_one<T>(M, q.data(), qd.data(), nullptr, o6.data(), col); rep("bias");
+    crba_one<T>(M, q.data(), o3.data(), o4.data(), col); rep("crba_ltdl");
+    crba_one<T>(M, q.data(), o3.data(), nullptr, col); rep("crba");
+    aba_one<T>(M, q.data(), qd.data(), tau.data(), o6.data(), col); rep("aba");
+  }
   rnea_vjp_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp");
   aba_vjp_one<T>(M, q.data(), qd.data(), tau.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp");
 }
@@ -92,9 +103,9 @@ int main(int argc, char** argv) {
   if (hm.kind == kKindChain) {
     static ModelImage<7> img; hm.pack(&img); count<ChainTopo<7>>(img, nf, frames.data());
   } else if (hm.free_root) {
-    static ModelImage<64> img; hm.pack(&img); count<TreeTopo<64, true>>(img, nf, frames.data());
+    static ModelImage<64> img; hm.pack(&img); count<SegTopo<64, true>>(img, nf, frames.data());
   } else {
-    static ModelImage<64> img; hm.pack(&img); count<TreeTopo<64, false>>(img, nf, frames.data());
+    static ModelImage<64> img; hm.pack(&img); count<SegTopo<64, false>>(img, nf, frames.data());
   }
   printf("  \"nb\": %d, \"nv\": %d\n}\n", hm.nb, hm.nv);
   return 0;

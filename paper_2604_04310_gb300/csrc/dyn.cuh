@@ -22,6 +22,7 @@ struct ChainTopo {
   static constexpr int NVMAX = N;
   static constexpr bool kFree = false;
   static constexpr bool kStatic = true;
+  static constexpr bool kSeg = false;
   template <class Img>
   FD static int nb(const Img&) { return N; }
   template <class Img>
@@ -36,6 +37,7 @@ struct TreeTopo {
   static constexpr int NVMAX = NBM + (FREE ? 5 : 0);
   static constexpr bool kFree = FREE;
   static constexpr bool kStatic = false;
+  static constexpr bool kSeg = false;
   template <class Img>
   FD static int nb(const Img& M) { return M.nb; }
   template <class Img>

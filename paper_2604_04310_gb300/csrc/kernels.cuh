@@ -2,6 +2,7 @@
 // image as a __grid_constant__ parameter (read through the constant bank).
 #pragma once
 #include "dyn.cuh"
+#include "seg.cuh"
 #include "launch.h"
 
 namespace frax {
@@ -60,6 +61,39 @@ __global__ void __launch_bounds__(kBlock) k_aba_vjp(const __grid_constant__ Mode
   aba_vjp_one<T>(M, q, qd, tau, qdd, gbar, qbar, qdbar, taubar, col);
 }
 
+// Trees (segment-unrolled): register use capped so that 6 (FK, RNEA, CRBA)
+// or 4 (ABA, which keeps 8 floats per body in thread-local memory between
+// its sweeps) 128-thread blocks fit on an SM.
+template <class T>
+__global__ void __launch_bounds__(kBlock, 6) k_fk_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                       int64_t ld, const float* q, float* pose,
+                                                       const __grid_constant__ Frames fr, float* J) {
+  FRAX_TID();
+  fk_seg<T>(M, q, pose, fr, J, col);
+}
+template <class T>
+__global__ void __launch_bounds__(kBlock, 6) k_rnea_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
+                                                         int64_t B, int64_t ld, const float* q, const float* qd,
+                                                         const float* qdd, float* tau) {
+  FRAX_TID();
+  rnea_seg<T>(M, q, qd, qdd, tau, col);
+}
+template <class T>
+__global__ void __launch_bounds__(kBlock, 6) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
+                                                         int64_t B, int64_t ld, const float* q, float* Mout,
+                                                         float* LD) {
+  FRAX_TID();
+  crba_seg<T>(M, q, Mout, LD, col);
+}
+template <class T>
+__global__ void __launch_bounds__(kBlock, 4) k_aba_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                        int64_t ld, const float* q, const float* qd,
+                                                        const float* tau, float* qdd) {
+  FRAX_TID();
+  P3Local<T::NBMAX> P;
+  aba_seg<T>(M, q, qd, tau, qdd, col, P);
+}
+
 template <class T>
 cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a) {
   const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock)), block(kBlock);
@@ -68,16 +102,20 @@ cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a)
   switch (op) {
     case kOpFk:
     case kOpJac:
-      k_fk<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, fr, a.out1);
+      if constexpr (T::kSeg) k_fk_seg<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, fr, a.out1);
+      else k_fk<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, fr, a.out1);
       break;
     case kOpRnea:
-      k_rnea<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.out0);
+      if constexpr (T::kSeg) k_rnea_seg<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.out0);
+      else k_rnea<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.out0);
       break;
     case kOpCrba:
-      k_crba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
+      if constexpr (T::kSeg) k_crba_seg<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
+      else k_crba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
       break;
     case kOpAba:
-      k_aba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.out0);
+      if constexpr (T::kSeg) k_aba_seg<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.out0);
+      else k_aba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.out0);
       break;
     case kOpRneaVjp:
       k_rnea_vjp<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1,

@@ -188,6 +188,68 @@ std::string build_model(int n, const int32_t* parent, const int32_t* joint_type,
     b.I[4] = static_cast<float>(Io(0, 2));
     b.I[5] = static_cast<float>(Io(1, 2));
   }
+  // segments (see model_image.h), numbered in topological order
+  {
+    std::vector<int> nchild(n, 0), seg_of(n, -1);
+    for (int i = 0; i < n; ++i)
+      if (parent[i] >= 0) nchild[parent[i]]++;
+    std::vector<std::vector<int>> segs;
+    for (int i = 0; i < n; ++i) {
+      const int k = parent[i];
+      bool extend = k >= 0 && nchild[k] == 1 && !(m.free_root && k == 0) && !(m.free_root && i == 0);
+      if (extend) {
+        auto& sg = segs[seg_of[k]];
+        extend = sg.back() == k && static_cast<int>(sg.size()) < kMaxSeg;
+      }
+      if (extend) {
+        segs[seg_of[k]].push_back(i);
+        seg_of[i] = seg_of[k];
+      } else {
+        seg_of[i] = static_cast<int>(segs.size());
+        segs.push_back({i});
+      }
+    }
+    const int ns = static_cast<int>(segs.size());
+    m.seg_of.assign(n, 0);
+    m.pos_of.assign(n, 0);
+    for (int s2 = 0; s2 < ns; ++s2)
+      for (int k = 0; k < static_cast<int>(segs[s2].size()); ++k) {
+        m.seg_of[segs[s2][k]] = s2;
+        m.pos_of[segs[s2][k]] = k;
+      }
+    std::vector<std::vector<int>> kids(ns);
+    for (int s2 = 0; s2 < ns; ++s2) {
+      const int p = parent[segs[s2][0]];
+      m.seg_start.push_back(static_cast<int>(m.order.size()));
+      m.seg_len.push_back(static_cast<int>(segs[s2].size()));
+      m.seg_parent.push_back(p);
+      for (int b : segs[s2]) m.order.push_back(b);
+      if (p >= 0) kids[seg_of[p]].push_back(s2);
+    }
+    // depth-first schedule; explicit stack of (segment, next child)
+    std::vector<std::pair<int, int>> stack;
+    for (int s2 = 0; s2 < ns; ++s2) {
+      if (m.seg_parent[s2] >= 0) continue;
+      stack.push_back({s2, 0});
+      while (!stack.empty()) {
+        auto& top = stack.back();
+        const int cur = top.first;
+        if (kids[cur].empty()) {
+          m.act.push_back((kActLeaf << 6) | cur);
+          stack.pop_back();
+          continue;
+        }
+        if (top.second == 0) m.act.push_back((kActOpen << 6) | cur);
+        if (top.second < static_cast<int>(kids[cur].size())) {
+          const int c = kids[cur][top.second++];
+          stack.push_back({c, 0});
+        } else {
+          m.act.push_back((kActClose << 6) | cur);
+          stack.pop_back();
+        }
+      }
+    }
+  }
   bool chain = !m.free_root;
   for (int i = 0; i < n; ++i) chain = chain && parent[i] == i - 1;
   m.kind = (chain && n == 7) ? kKindChain : kKindTree;

@@ -21,6 +21,8 @@ struct HostModel {
   std::vector<int> dof_parent;   // per dof: previous dof on the path to the root
   std::vector<uint64_t> anc;     // per body ancestor bit mask (self included)
   std::vector<int> depth;        // per body, root = 0
+  std::vector<int> order, seg_start, seg_len, seg_parent, act;  // segment schedule
+  std::vector<int> seg_of, pos_of;
   double gravity[3] = {0, 0, 0};
   std::vector<BodyImage> bodies;  // FP32 internal-frame image
 
@@ -40,6 +42,20 @@ void HostModel::pack(ModelImage<NB>* img) const {
   img->nv = nv;
   img->free_root = free_root ? 1 : 0;
   for (int k = 0; k < 3; ++k) img->g[k] = static_cast<float>(gravity[k]);
+  img->n_seg = static_cast<int32_t>(seg_start.size());
+  img->n_act = static_cast<int32_t>(act.size());
+  for (int i = 0; i < NB; ++i) {
+    img->order[i] = static_cast<int8_t>(i < nb ? order[i] : 0);
+    const bool has = i < img->n_seg;
+    img->seg_start[i] = static_cast<int8_t>(has ? seg_start[i] : 0);
+    img->seg_len[i] = static_cast<int8_t>(has ? seg_len[i] : 0);
+    img->seg_parent[i] = static_cast<int8_t>(has ? seg_parent[i] : -1);
+  }
+  for (int i = 0; i < NB; ++i) {
+    img->seg_of[i] = static_cast<int8_t>(i < nb ? seg_of[i] : 0);
+    img->pos_of[i] = static_cast<int8_t>(i < nb ? pos_of[i] : 0);
+  }
+  for (int i = 0; i < 2 * NB; ++i) img->act[i] = static_cast<uint8_t>(i < img->n_act ? act[i] : 0);
   for (int i = NB; i < NB + 5; ++i)
     img->dparent[i] = static_cast<int8_t>(i < nv ? dof_parent[i] : -1);
   for (int i = 0; i < NB; ++i) {

@@ -24,12 +24,30 @@ struct BodyImage {
                // xx, yy, zz, xy, xz, yz
 };
 
+// Segments: maximal runs of bodies in which every body but the last has
+// exactly one child, the next body of the run (at most kMaxSeg bodies; a
+// free-flyer root is a segment of its own). Kernels unroll a segment so its
+// per-body state stays in registers. Segments are numbered in topological
+// order; `act` lists them depth-first: a leaf segment runs its outward and
+// inward sweeps back to back, a segment with child segments runs its outward
+// sweep, then its children, then its inward sweep.
+constexpr int kMaxSeg = 8;
+enum SegAction { kActLeaf = 0, kActOpen = 1, kActClose = 2 };
+
 template <int NB>
 struct alignas(16) ModelImage {
   int32_t nb, nq, nv, free_root;
   float g[3];                       // world gravity
+  int32_t n_seg, n_act;
   int8_t parent[NB];                // parent body, -1 = world
   int8_t dparent[NB + 5];           // per dof: previous dof towards the root
+  int8_t order[NB];                 // bodies grouped by segment
+  int8_t seg_start[NB];             // first slot of segment s in `order`
+  int8_t seg_len[NB];               // bodies in segment s
+  int8_t seg_parent[NB];            // parent body of the segment's first body
+  int8_t seg_of[NB];                // segment of body i
+  int8_t pos_of[NB];                // slot of body i within its segment
+  uint8_t act[2 * NB];              // (action << 6) | segment
   uint64_t anc[NB];                 // bit j set iff j in Anc(i) (i included)
   BodyImage body[NB];
 };

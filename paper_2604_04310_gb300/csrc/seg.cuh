@@ -1,0 +1,607 @@
+// Segment-unrolled tree algorithms, one thread per instance.
+//
+// A tree is cut into segments (model_image.h): runs of single-child bodies,
+// at most kMaxSeg long. A segment's sweep is unrolled like the chain kernel,
+// so its per-body state sits in registers (slot k = k-th body of the
+// segment); only what crosses segment boundaries lives in small per-thread
+// arrays indexed by body: the velocity/acceleration/pose of bodies that have
+// child segments, the force or inertia that child segments hand back, and
+// the sweep state of segments whose inward sweep has to wait for their
+// children. Segments are visited depth-first (M.act), so that waiting state
+// is bounded by the depth of the segment tree, and outward-only passes run
+// over the segments in topological order.
+#pragma once
+#include "dyn.cuh"
+
+namespace frax {
+
+template <int NBM, bool FREE>
+struct SegTopo {
+  static constexpr int NBMAX = NBM;
+  static constexpr int NVMAX = NBM + (FREE ? 5 : 0);
+  static constexpr bool kFree = FREE;
+  static constexpr bool kStatic = false;
+  static constexpr bool kSeg = true;
+  template <class Img>
+  FD static int nb(const Img& M) { return M.nb; }
+  template <class Img>
+  FD static int parent(const Img& M, int i) { return M.parent[i]; }
+  template <class Img>
+  FD static int dparent(const Img& M, int k) { return M.dparent[k]; }
+};
+
+// v x (e_z qd): the velocity-product acceleration of a revolute joint
+FD SV ez_velprod(const SV& v, float qd) { return qd * SV{mk(v.w.y, -v.w.x, 0.f), mk(v.v.y, -v.v.x, 0.f)}; }
+
+// ====================================================================== RNEA
+template <class T, class Img, class C>
+FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
+                 const float* __restrict__ qdd, float* __restrict__ tau, const C& col) {
+  constexpr int NB = T::NBMAX;
+  SV bv[NB], ba[NB], Fa[NB], sf[NB];
+  float sc[NB], ss[NB];
+  const SV ag = gravity_acc(M.g);
+#pragma unroll 1
+  for (int t = 0; t < M.n_act; ++t) {
+    const int act = M.act[t];
+    const int s = act & 63, kind = act >> 6;
+    const int st = M.seg_start[s], len = M.seg_len[s];
+    if (T::kFree && s == 0) {  // the free-flyer root is a one-body segment
+      if (kind != kActClose) {
+        const RootPose P = root_pose(M, q, col);
+        const SV v0 = load6(qd, 0, col);
+        SV a0 = SV{mk(0, 0, 0), rotT(P.E, ag.v)};
+        if (qdd) a0 = a0 + load6(qdd, 0, col);
+        const RBI I = rbi_of(M.body[0]);
+        const SV f0 = rbi_mul(I, a0) + crf(v0, rbi_mul(I, v0));
+        if (kind == kActLeaf) {
+          store6(tau, 0, col, f0);
+        } else {
+          bv[0] = v0;
+          ba[0] = a0;
+          sf[0] = f0;
+          Fa[0] = szero();
+        }
+      } else {
+        store6(tau, 0, col, sf[0] + Fa[0]);
+      }
+      continue;
+    }
+    SV f[kMaxSeg];
+    float cc[kMaxSeg], sn[kMaxSeg];
+    if (kind != kActClose) {
+      const int p = M.seg_parent[s];
+      SV v = p < 0 ? szero() : bv[p];
+      SV a = p < 0 ? ag : ba[p];
+#pragma unroll
+      for (int k = 0; k < kMaxSeg; ++k) {
+        if (k < len) {
+          const int i = M.order[st + k];
+          const BodyImage& b = M.body[i];
+          sincosf(col.in(q, iq_of<T>(i)), &sn[k], &cc[k]);
+          const float qdi = col.in(qd, iv_of<T>(i));
+          const float qddi = qdd ? col.in(qdd, iv_of<T>(i)) : 0.f;
+          v = mot_in(b, cc[k], sn[k], v);
+          v.w.z += qdi;
+          a = mot_in(b, cc[k], sn[k], a);
+          a.w.z += qddi;
+          a = a + ez_velprod(v, qdi);
+          const RBI I = rbi_of(b);
+          f[k] = rbi_mul(I, a) + crf(v, rbi_mul(I, v));
+        }
+      }
+      if (kind == kActOpen) {
+        const int last = M.order[st + len - 1];
+        bv[last] = v;
+        ba[last] = a;
+        Fa[last] = szero();
+#pragma unroll
+        for (int k = 0; k < kMaxSeg; ++k)
+          if (k < len) {
+            const int i = M.order[st + k];
+            sf[i] = f[k];
+            sc[i] = cc[k];
+            ss[i] = sn[k];
+          }
+        continue;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kMaxSeg; ++k)
+        if (k < len) {
+          const int i = M.order[st + k];
+          f[k] = sf[i];
+          cc[k] = sc[i];
+          sn[k] = ss[i];
+        }
+    }
+    SV F = kind == kActClose ? Fa[M.order[st + len - 1]] : szero();
+#pragma unroll
+    for (int k = kMaxSeg - 1; k >= 0; --k) {
+      if (k < len) {
+        const int i = M.order[st + k];
+        F = F + f[k];
+        col.out(tau, iv_of<T>(i), F.w.z);
+        F = frc_out(M.body[i], cc[k], sn[k], F);
+      }
+    }
+    const int p = M.seg_parent[s];
+    if (p >= 0) Fa[p] = Fa[p] + F;
+  }
+}
+
+// ======================================================================= ABA
+// Between the inward and the final outward sweep every body needs U, 1/D and
+// u (8 floats). They go to a per-thread slice of shared memory (P3Smem,
+// [body][field][thread] so a warp's accesses hit 32 banks) when the kernel
+// provides one, else to thread-local memory (P3Local). The outward sweep
+// recomputes the joint sin/cos and velocities rather than storing them.
+struct P3Smem {
+  float* base;  // this thread's first word
+  int stride;   // threads per block
+  FD float& at(int i, int f) const { return base[(i * 8 + f) * stride]; }
+};
+template <int NB>
+struct P3Local {
+  float v[NB * 8];
+  FD float& at(int i, int f) { return v[i * 8 + f]; }
+};
+
+template <class T, class Img, bool VEL, class Rhs, class Out, class C, class P3>
+FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __restrict__ qd, const Rhs& rhs_at,
+                     const Out& out_at, const C& col, P3& P) {
+  constexpr int NB = T::NBMAX;
+  SV bv[NB], bA[NB], pAa[NB], sv[NB];
+  AI IAa[NB];
+  float sc[NB], ss[NB];
+  const SV ag = VEL ? gravity_acc(M.g) : szero();
+  V3 gam = mk(0, 0, 0);  // root: E^T (-g)
+  AI azero;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) { azero.A[k] = 0.f; azero.C[k] = 0.f; }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) azero.B[k] = 0.f;
+#pragma unroll 1
+  for (int t = 0; t < M.n_act; ++t) {
+    const int act = M.act[t];
+    const int s = act & 63, kind = act >> 6;
+    const int st = M.seg_start[s], len = M.seg_len[s];
+    if (T::kFree && s == 0) {
+      const RBI I0 = rbi_of(M.body[0]);
+      if (kind != kActClose) {
+        const RootPose RP = root_pose(M, q, col);
+        gam = rotT(RP.E, ag.v);
+        bv[0] = VEL ? load6(qd, 0, col) : szero();
+        IAa[0] = azero;
+        pAa[0] = szero();
+        if (kind == kActOpen) continue;
+      }
+      AI IA0 = ai_of(I0);
+      ai_add(IA0, IAa[0]);
+      const SV pA0 = VEL ? crf(bv[0], rbi_mul(I0, bv[0])) : szero();
+      const SV a0 = spd6_solve(IA0, rhs_at.root() - (pA0 + pAa[0]));
+      out_at.root(a0 - SV{mk(0, 0, 0), gam});
+      bA[0] = a0;
+      continue;
+    }
+    const int last = M.order[st + len - 1];
+    if (kind != kActClose) {
+      const int p = M.seg_parent[s];
+      SV vv = (!VEL || p < 0) ? szero() : bv[p];
+#pragma unroll 1
+      for (int k = 0; k < len; ++k) {
+        const int i = M.order[st + k];
+        float sn, cs;
+        sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
+        if (VEL) {
+          vv = mot_in(M.body[i], cs, sn, vv);
+          vv.w.z += col.in(qd, iv_of<T>(i));
+        }
+        sv[i] = vv;
+        sc[i] = cs;
+        ss[i] = sn;
+      }
+      if (kind == kActOpen) {
+        bv[last] = vv;
+        pAa[last] = szero();
+        IAa[last] = azero;
+        continue;
+      }
+    }
+    // inward sweep: articulated inertias and bias forces
+    AI Ia;
+    SV pa;
+    const bool closing = kind == kActClose;
+#pragma unroll 1
+    for (int k = len - 1; k >= 0; --k) {
+      {
+        const int i = M.order[st + k];
+        const BodyImage& b = M.body[i];
+        const RBI Ib = rbi_of(b);
+        const SV vk = sv[i];
+        const float ck = sc[i], sk = ss[i];
+        AI IA = ai_of(Ib);
+        SV pAt = szero();
+        SV cb = szero();
+        if (VEL) {
+          const float qdi = col.in(qd, iv_of<T>(i));
+          cb = ez_velprod(vk, qdi);
+          pAt = crf(vk, rbi_mul(Ib, vk));
+        }
+        if (k == len - 1) {
+          if (closing) {
+            ai_add(IA, IAa[last]);
+            pAt = pAt + pAa[last];
+          }
+        } else {
+          ai_add(IA, Ia);
+          pAt = pAt + pa;
+        }
+        const SV U = ai_col_z(IA);
+        const float dinv = 1.f / U.w.z;
+        const float u = rhs_at(i) - pAt.w.z;
+        P.at(i, 0) = U.w.x;
+        P.at(i, 1) = U.w.y;
+        P.at(i, 2) = U.w.z;
+        P.at(i, 3) = U.v.x;
+        P.at(i, 4) = U.v.y;
+        P.at(i, 5) = U.v.z;
+        P.at(i, 6) = dinv;
+        P.at(i, 7) = u;
+        Ia = IA;
+        ai_rank1_sub(Ia, U, dinv);
+        pa = pAt + ai_mul(Ia, cb) + (u * dinv) * U;
+        ai_out(b, ck, sk, Ia);
+        pa = frc_out(b, ck, sk, pa);
+      }
+    }
+    const int p = M.seg_parent[s];
+    if (p >= 0) {
+      ai_add(IAa[p], Ia);
+      pAa[p] = pAa[p] + pa;
+    }
+  }
+  // outward sweep: accelerations, segment by segment in topological order
+#pragma unroll 1
+  for (int s = (T::kFree ? 1 : 0); s < M.n_seg; ++s) {
+    const int st = M.seg_start[s], len = M.seg_len[s];
+    const int p = M.seg_parent[s];
+    SV a = p < 0 ? ag : bA[p];
+    SV vv = (!VEL || p < 0) ? szero() : bv[p];
+#pragma unroll 1
+    for (int k = 0; k < len; ++k) {
+      {
+        const int i = M.order[st + k];
+        const BodyImage& b = M.body[i];
+        float sn, cs;
+        sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
+        SV cb = szero();
+        if (VEL) {
+          const float qdi = col.in(qd, iv_of<T>(i));
+          vv = mot_in(b, cs, sn, vv);
+          vv.w.z += qdi;
+          cb = ez_velprod(vv, qdi);
+        }
+        a = mot_in(b, cs, sn, a) + cb;
+        const SV U{mk(P.at(i, 0), P.at(i, 1), P.at(i, 2)), mk(P.at(i, 3), P.at(i, 4), P.at(i, 5))};
+        const float x = (P.at(i, 7) - dot(U, a)) * P.at(i, 6);
+        a.w.z += x;
+        out_at(i, x);
+      }
+    }
+    bA[M.order[st + len - 1]] = a;
+  }
+}
+
+template <class T, class Img, class C, class P3>
+FD void aba_seg(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
+                const float* __restrict__ tau, float* __restrict__ qdd, const C& col, P3& P) {
+  aba_seg_core<T, Img, true>(M, q, qd, RhsFromGlobal<T, C>{tau, col}, OutToGlobal<T, C>{qdd, col}, col, P);
+}
+
+// ============================================================= CRBA + LTDL
+// M from composite inertias (Algorithm 2's result) and, when asked, the
+// factor M = L^T D L of the same tree from articulated-body inertias: with
+// dofs eliminated from the leaves up, D_i = S_i^T I^A_i S_i and
+// L_ij = S_j^T (^jX_i)^* U_i / D_i for j in Anc(i), U_i = I^A_i S_i, where
+// I^A is the articulated inertia of ABA at zero velocity (the Schur
+// complement of M's trailing block). A free-flyer root's own 6x6 block is
+// the root's articulated inertia, factored densely. No matrix entry is
+// updated in place.
+// Emits body i's row of M and/or L: S_j^T F at every ancestor dof j (the
+// forces carried to the root through the joint transforms) and zeros at the
+// dofs of non-ancestors. Not inlined: called once per body, it keeps the
+// kernel's code small.
+template <class T, class Img, class C>
+FRAX_NOINLINE void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mout,
+                                           float* __restrict__ LD, const float* sc, const float* ss, C col) {
+  const int nv = T::kFree ? M.nb + 5 : M.nb;
+  const int di = iv_of<T>(i);
+  const bool wM = Mout != nullptr, wL = LD != nullptr;
+  auto put = [&](int c, float m, float l) {  // c < di
+    if (wM) {
+      col.out(Mout, di * nv + c, m);
+      col.out(Mout, c * nv + di, m);
+    }
+    if (wL) col.out(LD, MSink::tri(di, c), l);
+  };
+  int j = i;
+  while (true) {
+    const int k = M.parent[j];
+    if (k < 0) break;
+    const BodyImage& b = M.body[j];
+    if (wM) FM = frc_out(b, sc[j], ss[j], FM);
+    if (wL) FL = frc_out(b, sc[j], ss[j], FL);
+    j = k;
+    if (T::kFree && j == 0) {
+      put(0, FM.w.x, FL.w.x); put(1, FM.w.y, FL.w.y); put(2, FM.w.z, FL.w.z);
+      put(3, FM.v.x, FL.v.x); put(4, FM.v.y, FL.v.y); put(5, FM.v.z, FL.v.z);
+    } else {
+      put(iv_of<T>(j), FM.w.z, FL.w.z);
+    }
+  }
+  const uint64_t anc = M.anc[i];
+  for (int jj = 0; jj < i; ++jj) {
+    if ((anc >> jj) & 1ull) continue;
+    if (T::kFree && jj == 0) {
+      for (int m = 0; m < 6; ++m) put(m, 0.f, 0.f);
+    } else {
+      put(iv_of<T>(jj), 0.f, 0.f);
+    }
+  }
+}
+
+template <class T, class Img, class C>
+FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ Mout, float* __restrict__ LD,
+                 const C& col) {
+  constexpr int NB = T::NBMAX;
+  RBI ICa[NB];
+  AI IAa[NB];
+  float sc[NB], ss[NB];
+  const int nb = M.nb;
+  const int nv = T::kFree ? nb + 5 : nb;
+  const bool wantL = LD != nullptr;
+  auto putM = [&](int r, int c, float val) {  // r >= c
+    col.out(Mout, r * nv + c, val);
+    if (r != c) col.out(Mout, c * nv + r, val);
+  };
+  auto putL = [&](int r, int c, float val) { col.out(LD, MSink::tri(r, c), val); };
+  const RBI rzero{0.f, mk(0, 0, 0), 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  AI azero;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) { azero.A[k] = 0.f; azero.C[k] = 0.f; }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) azero.B[k] = 0.f;
+#pragma unroll 1
+  for (int t = 0; t < M.n_act; ++t) {
+    const int act = M.act[t];
+    const int s = act & 63, kind = act >> 6;
+    const int st = M.seg_start[s], len = M.seg_len[s];
+    if (T::kFree && s == 0) {
+      if (kind != kActClose) {
+        ICa[0] = rzero;
+        IAa[0] = azero;
+      }
+      if (kind == kActOpen) continue;
+      if (Mout) {
+        const RBI Cc = rbi_add(rbi_of(M.body[0]), ICa[0]);
+        const float blk[6][6] = {{Cc.xx, Cc.xy, Cc.xz, 0.f, -Cc.h.z, Cc.h.y},
+                                 {Cc.xy, Cc.yy, Cc.yz, Cc.h.z, 0.f, -Cc.h.x},
+                                 {Cc.xz, Cc.yz, Cc.zz, -Cc.h.y, Cc.h.x, 0.f},
+                                 {0.f, Cc.h.z, -Cc.h.y, Cc.m, 0.f, 0.f},
+                                 {-Cc.h.z, 0.f, Cc.h.x, 0.f, Cc.m, 0.f},
+                                 {Cc.h.y, -Cc.h.x, 0.f, 0.f, 0.f, Cc.m}};
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+          for (int c = 0; c <= r; ++c) putM(r, c, blk[r][c]);
+      }
+      if (wantL) {
+        AI A0 = ai_of(rbi_of(M.body[0]));
+        ai_add(A0, IAa[0]);
+        const float* Af = A0.A;
+        const float* Cf = A0.C;
+        float H[6][6] = {{Af[0], Af[3], Af[4], A0.B[0], A0.B[1], A0.B[2]},
+                         {Af[3], Af[1], Af[5], A0.B[3], A0.B[4], A0.B[5]},
+                         {Af[4], Af[5], Af[2], A0.B[6], A0.B[7], A0.B[8]},
+                         {A0.B[0], A0.B[3], A0.B[6], Cf[0], Cf[3], Cf[4]},
+                         {A0.B[1], A0.B[4], A0.B[7], Cf[3], Cf[1], Cf[5]},
+                         {A0.B[2], A0.B[5], A0.B[8], Cf[4], Cf[5], Cf[2]}};
+        // dense L^T D L of the root block, last dof first
+#pragma unroll
+        for (int k = 5; k >= 0; --k) {
+          const float rk = 1.f / H[k][k];
+#pragma unroll
+          for (int i = k - 1; i >= 0; --i) {
+            const float a = H[k][i] * rk;
+#pragma unroll
+            for (int j = i; j >= 0; --j) H[i][j] = fmaf(-a, H[k][j], H[i][j]);
+            H[k][i] = a;
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+          for (int c = 0; c <= r; ++c) putL(r, c, H[r][c]);
+      }
+      continue;
+    }
+    const int last = M.order[st + len - 1];
+    if (kind != kActClose) {
+#pragma unroll 1
+      for (int k = 0; k < len; ++k) {
+        const int i = M.order[st + k];
+        sincosf(col.in(q, iq_of<T>(i)), &ss[i], &sc[i]);
+      }
+      if (kind == kActOpen) {
+        ICa[last] = rzero;
+        if (wantL) IAa[last] = azero;
+        continue;
+      }
+    }
+    RBI Cc = rbi_of(M.body[last]);
+    AI IA = ai_of(Cc);
+    if (kind == kActClose) {
+      Cc = rbi_add(Cc, ICa[last]);
+      if (wantL) ai_add(IA, IAa[last]);
+    }
+#pragma unroll 1
+    for (int k = len - 1; k >= 0; --k) {
+      {
+        const int i = M.order[st + k];
+        const int di = iv_of<T>(i);
+        const BodyImage& b = M.body[i];
+        const SV FM{mk(Cc.xz, Cc.yz, Cc.zz), mk(-Cc.h.y, Cc.h.x, 0.f)};  // I^c_i e_z
+        if (Mout) col.out(Mout, di * nv + di, FM.w.z);
+        SV FL = szero();
+        AI Ia;
+        if (wantL) {
+          const SV U = ai_col_z(IA);
+          const float dinv = 1.f / U.w.z;
+          putL(di, di, U.w.z);
+          FL = dinv * U;
+          Ia = IA;
+          ai_rank1_sub(Ia, U, dinv);
+          ai_out(b, sc[i], ss[i], Ia);
+        }
+        crba_emit_row<T>(M, i, FM, FL, Mout, LD, sc, ss, col);
+        const RBI up = rbi_out(b, sc[i], ss[i], Cc);
+        if (k > 0) {
+          const RBI Ip = rbi_of(M.body[M.order[st + k - 1]]);
+          Cc = rbi_add(Ip, up);
+          if (wantL) {
+            IA = ai_of(Ip);
+            ai_add(IA, Ia);
+          }
+        } else {
+          Cc = up;
+          if (wantL) IA = Ia;
+        }
+      }
+    }
+    const int p = M.seg_parent[s];
+    if (p >= 0) {
+      ICa[p] = rbi_add(ICa[p], Cc);
+      if (wantL) ai_add(IAa[p], IA);
+    }
+  }
+}
+
+// ============================================================ FK + Jacobians
+// Poses segment by segment (depth-first), each segment's frames in
+// registers; the joint axes and origins of the bodies of open ancestor
+// segments are kept per body so a frame's Jacobian is written as soon as its
+// segment is done. Column j of frame k: [z_j; z_j x (p_k - p_j)], 0 off Anc(k).
+template <class T, class Img, class C>
+FD void fk_seg(const Img& M, const float* __restrict__ q, float* __restrict__ pose, const Frames& fr,
+               float* __restrict__ J, const C& col) {
+  constexpr int NB = T::NBMAX;
+  float bR[NB][9];    // world rotation (internal frame) of bodies with child segments
+  V3 bp[NB];
+  V3 zs[NB], ps[NB];  // joint axis and origin of every body reached so far
+  float R0[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+  V3 p0 = mk(0, 0, 0);
+  const int nb = M.nb;
+  const int nv = T::kFree ? nb + 5 : nb;
+  auto pose_out = [&](int i, const float* R, V3 p) {
+    const BodyImage& b = M.body[i];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+        col.out(pose, 12 * i + 3 * r + cc,
+                fmaf(R[3 * r], b.Q[3 * cc], fmaf(R[3 * r + 1], b.Q[3 * cc + 1], R[3 * r + 2] * b.Q[3 * cc + 2])));
+    col.out(pose, 12 * i + 9, p.x);
+    col.out(pose, 12 * i + 10, p.y);
+    col.out(pose, 12 * i + 11, p.z);
+  };
+  auto jcol = [&](int base, int cj, bool on, V3 z, V3 lin) {
+    col.out(J, base + 0 * nv + cj, on ? z.x : 0.f);
+    col.out(J, base + 1 * nv + cj, on ? z.y : 0.f);
+    col.out(J, base + 2 * nv + cj, on ? z.z : 0.f);
+    col.out(J, base + 3 * nv + cj, on ? lin.x : 0.f);
+    col.out(J, base + 4 * nv + cj, on ? lin.y : 0.f);
+    col.out(J, base + 5 * nv + cj, on ? lin.z : 0.f);
+  };
+#pragma unroll 1
+  for (int t = 0; t < M.n_act; ++t) {
+    const int act = M.act[t];
+    const int s = act & 63, kind = act >> 6;
+    if (kind == kActClose) continue;
+    const int st = M.seg_start[s], len = M.seg_len[s];
+    float R[9];
+    V3 p;
+    if (T::kFree && s == 0) {
+      const RootPose P = root_pose(M, q, col);
+#pragma unroll
+      for (int u = 0; u < 9; ++u) R[u] = R0[u] = P.E[u];
+      p = p0 = P.r;
+      ps[0] = p;
+      if (pose) pose_out(0, R, p);
+    } else {
+      const int par = M.seg_parent[s];
+      if (par >= 0) {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) R[u] = bR[par][u];
+        p = bp[par];
+      } else {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) R[u] = (u % 4 == 0) ? 1.f : 0.f;
+        p = mk(0, 0, 0);
+      }
+#pragma unroll 1
+      for (int k = 0; k < len; ++k) {
+        const int i = M.order[st + k];
+        const BodyImage& b = M.body[i];
+        float sn, cs;
+        sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
+        float A[9];
+        mat_mul(R, b.R, A);
+        p = p + rot(R, mk(b.p[0], b.p[1], b.p[2]));
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          R[3 * r] = fmaf(cs, A[3 * r], sn * A[3 * r + 1]);
+          R[3 * r + 1] = fmaf(-sn, A[3 * r], cs * A[3 * r + 1]);
+          R[3 * r + 2] = A[3 * r + 2];
+        }
+        zs[i] = mk(R[2], R[5], R[8]);
+        ps[i] = p;
+        if (pose) pose_out(i, R, p);
+      }
+    }
+    const int last = M.order[st + len - 1];
+    if (kind == kActOpen) {
+#pragma unroll
+      for (int u = 0; u < 9; ++u) bR[last][u] = R[u];
+      bp[last] = p;
+    }
+    if (!J) continue;
+    // frames in this segment: every ancestor has been reached already
+    for (int f = 0; f < fr.n; ++f) {
+      const int kf = fr.body[f];
+      if (M.seg_of[kf] != s) continue;
+      const uint64_t anc = M.anc[kf];
+      const int base = f * 6 * nv;
+      const V3 pk = ps[kf];
+#pragma unroll 1
+      for (int j = 0; j < nb; ++j) {
+        const bool on = (anc >> j) & 1ull;
+        if (T::kFree && j == 0) {
+          const V3 d = pk - p0;
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            const V3 zr = mk(R0[m], R0[3 + m], R0[6 + m]);
+            jcol(base, m, on, zr, cross(zr, d));
+            jcol(base, 3 + m, on, mk(0, 0, 0), zr);
+          }
+        } else {
+          const V3 zj = on ? zs[j] : mk(0, 0, 0);
+          const V3 pj = on ? ps[j] : mk(0, 0, 0);
+          jcol(base, iv_of<T>(j), on, zj, cross(zj, pk - pj));
+        }
+      }
+    }
+  }
+}
+
+}  // namespace frax

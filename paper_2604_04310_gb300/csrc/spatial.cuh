@@ -10,6 +10,11 @@
 namespace frax {
 
 #define FD __host__ __device__ __forceinline__
+#if defined(__CUDACC__)
+#define FRAX_NOINLINE __host__ __device__ __noinline__
+#else
+#define FRAX_NOINLINE __attribute__((noinline))
+#endif
 
 struct V3 {
   float x, y, z;
