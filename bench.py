@@ -43,9 +43,9 @@ FP32_LANES_PER_SM = 128
 # reprints this table.
 FLOPS = {
     "chain7": {"fk_jac": 903, "fk": 819, "rnea": 2000, "bias": 2000, "crba_ltdl": 2305, "crba": 2172,
-               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 9331},
+               "aba": 5302, "rnea_vjp": 6192, "aba_vjp": 11233},
     "humanoid": {"fk_jac": 5304, "fk": 3792, "rnea": 9028, "bias": 9022, "crba_ltdl": 35751, "crba": 12921,
-                 "aba": 27054, "rnea_vjp": 22034, "aba_vjp": 43301},
+                 "aba": 27054, "rnea_vjp": 25969, "aba_vjp": 47290},
 }
 
 

@@ -76,8 +76,28 @@ void count(const Img& M, int nf, const int* frames) {
     crba_one<T>(M, q.data(), o3.data(), nullptr, col); rep("crba");
     aba_one<T>(M, q.data(), qd.data(), tau.data(), o6.data(), col); rep("aba");
   }
-  rnea_vjp_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp");
-  aba_vjp_one<T>(M, q.data(), qd.data(), tau.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp");
+  if constexpr (T::kSeg) {
+    rnea_vjp_seg_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp");
+    aba_vjp_seg_one<T>(M, q.data(), qd.data(), tau.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp");
+  }
+}
+
+// The chain's adjoints run on the segment code (SegTopo<8, false>).
+template <class Img>
+void count_chain_vjp(const Img& M) {
+  using T = SegTopo<8, false>;
+  int nq = M.nq, nv = M.nv;
+  std::vector<CF> q(nq, CF(0.3f)), qd(nv, CF(0.2f)), qdd(nv, CF(0.1f)), tau(nv, CF(0.5f)), gb(nv, CF(0.7f));
+  std::vector<CF> o5(nq + 8), o6(nv + 8), o7(nv + 8);
+  Col col{1, 0};
+  auto rep = [&](const char* name) {
+    printf("  \"%s\": {\"flops\": %lld, \"fma\": %lld, \"add\": %lld, \"mul\": %lld, \"div\": %lld, \"sfu\": %lld},\n",
+           name, 2 * g.fma + g.add + g.mul, g.fma, g.add, g.mul, g.div, g.sfu);
+    g = Counts{};
+  };
+  g = Counts{};
+  rnea_vjp_seg_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp");
+  aba_vjp_seg_one<T>(M, q.data(), qd.data(), tau.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp");
 }
 
 int main(int argc, char** argv) {
@@ -102,6 +122,7 @@ int main(int argc, char** argv) {
   printf("{\n");
   if (hm.kind == kKindChain) {
     static ModelImage<7> img; hm.pack(&img); count<ChainTopo<7>>(img, nf, frames.data());
+    static ModelImage<8> img8; hm.pack(&img8); count_chain_vjp(img8);
   } else if (hm.free_root) {
     static ModelImage<64> img; hm.pack(&img); count<SegTopo<64, true>>(img, nf, frames.data());
   } else {

@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(kBlock) k_rnea_vjp(const __grid_constant__ Mod
                                                       const float* qdd, const float* gbar, float* qbar,
                                                       float* qdbar, float* qddbar) {
   FRAX_TID();
-  rnea_vjp_one<T>(M, q, qd, qdd, gbar, qbar, qdbar, qddbar, col);
+  if constexpr (T::kSeg) rnea_vjp_seg_one<T>(M, q, qd, qdd, gbar, qbar, qdbar, qddbar, col);
+  else rnea_vjp_one<T>(M, q, qd, qdd, gbar, qbar, qdbar, qddbar, col);
 }
 
 template <class T>
@@ -58,7 +59,8 @@ __global__ void __launch_bounds__(kBlock) k_aba_vjp(const __grid_constant__ Mode
                                                      const float* tau, const float* qdd, const float* gbar,
                                                      float* qbar, float* qdbar, float* taubar) {
   FRAX_TID();
-  aba_vjp_one<T>(M, q, qd, tau, qdd, gbar, qbar, qdbar, taubar, col);
+  if constexpr (T::kSeg) aba_vjp_seg_one<T>(M, q, qd, tau, qdd, gbar, qbar, qdbar, taubar, col);
+  else aba_vjp_one<T>(M, q, qd, tau, qdd, gbar, qbar, qdbar, taubar, col);
 }
 
 // Trees (segment-unrolled): register use capped so that 6 (FK, RNEA, CRBA)

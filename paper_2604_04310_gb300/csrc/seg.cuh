@@ -604,4 +604,142 @@ FD void fk_seg(const Img& M, const float* __restrict__ q, float* __restrict__ po
   }
 }
 
+// ================================================================ RNEA VJP
+// The adjoint of RNEA (see rnea_vjp_core) on segments. Outward: v, a and the
+// adjoint force Fb = X Fb_parent + e gbar. Inward, inside a segment, the
+// per-body forward state is not stored but stepped back from the segment's
+// tip by inverting each joint transform (v_parent = X^-1 (v - e qd),
+// a_parent = X^-1 (a - e qdd - v x e qd), Fb_parent = X^-1 (Fb - e gbar)),
+// and the body force is recomputed; only segment tips and the accumulated
+// adjoints handed to branch bodies are kept per body.
+template <class T, class Img, class Seed, class Sink, class C>
+FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
+                     const float* __restrict__ qdd, const Seed& gb_at, const Sink& sink, const C& col) {
+  constexpr int NB = T::NBMAX;
+  SV bv[NB], ba[NB], bF[NB];     // tip state of bodies with child segments
+  SV aF[NB], aab[NB], avb[NB];   // adjoint contributions of child segments
+  float sc[NB], ss[NB];
+  const SV ag = gravity_acc(M.g);
+  V3 gam = mk(0, 0, 0);
+  auto body_force = [&](const RBI& I, const SV& v, const SV& a) { return rbi_mul(I, a) + crf(v, rbi_mul(I, v)); };
+#pragma unroll 1
+  for (int t = 0; t < M.n_act; ++t) {
+    const int act = M.act[t];
+    const int s = act & 63, kind = act >> 6;
+    const int st = M.seg_start[s], len = M.seg_len[s];
+    if (T::kFree && s == 0) {
+      const RBI I = rbi_of(M.body[0]);
+      if (kind != kActClose) {
+        const RootPose P = root_pose(M, q, col);
+        gam = rotT(P.E, ag.v);
+        bv[0] = load6(qd, 0, col);
+        ba[0] = SV{mk(0, 0, 0), gam} + load6(qdd, 0, col);
+        bF[0] = gb_at.root();
+        aF[0] = aab[0] = avb[0] = szero();
+        if (kind == kActOpen) continue;
+      }
+      const SV v0 = bv[0], Fb0 = bF[0];
+      const SV ab = rbi_mul(I, Fb0) + aab[0];
+      const SV vb = avb[0] - crf(Fb0, rbi_mul(I, v0)) - rbi_mul(I, crm(v0, Fb0));
+      sink.root(cross(ab.v, gam), vb, ab);
+      continue;
+    }
+    const int last = M.order[st + len - 1];
+    SV v, a, Fb;
+    if (kind != kActClose) {
+      const int p = M.seg_parent[s];
+      v = p < 0 ? szero() : bv[p];
+      a = p < 0 ? ag : ba[p];
+      Fb = p < 0 ? szero() : bF[p];
+#pragma unroll 1
+      for (int k = 0; k < len; ++k) {
+        const int i = M.order[st + k];
+        const BodyImage& b = M.body[i];
+        float sn, cs;
+        sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
+        sc[i] = cs;
+        ss[i] = sn;
+        const float qdi = col.in(qd, iv_of<T>(i));
+        v = mot_in(b, cs, sn, v);
+        v.w.z += qdi;
+        a = mot_in(b, cs, sn, a);
+        a.w.z += col.in(qdd, iv_of<T>(i));
+        a = a + ez_velprod(v, qdi);
+        Fb = mot_in(b, cs, sn, Fb);
+        Fb.w.z += gb_at(i);
+      }
+      if (kind == kActOpen) {
+        bv[last] = v;
+        ba[last] = a;
+        bF[last] = Fb;
+        aF[last] = aab[last] = avb[last] = szero();
+        continue;
+      }
+    } else {
+      v = bv[last];
+      a = ba[last];
+      Fb = bF[last];
+    }
+    const bool closing = kind == kActClose;
+    SV Fc = closing ? aF[last] : szero();
+    SV abc = closing ? aab[last] : szero();
+    SV vbc = closing ? avb[last] : szero();
+#pragma unroll 1
+    for (int k = len - 1; k >= 0; --k) {
+      const int i = M.order[st + k];
+      const BodyImage& b = M.body[i];
+      const RBI I = rbi_of(b);
+      const float cs = sc[i], sn = ss[i];
+      const float qdi = col.in(qd, iv_of<T>(i));
+      SV xa = a - ez_velprod(v, qdi);
+      xa.w.z -= col.in(qdd, iv_of<T>(i));
+      const SV F = body_force(I, v, a) + Fc;
+      const SV ab = rbi_mul(I, Fb) + abc;
+      const SV vb = vbc - crf(Fb, rbi_mul(I, v)) - rbi_mul(I, crm(v, Fb)) + qdi * ez_crf(ab);
+      sink(i, dot(Fb, ez_crf(F)) - dot(ab, ez_crm(xa)) - dot(vb, ez_crm(v)), vb.w.z - dot(ab, ez_crm(v)),
+           ab.w.z);
+      Fc = frc_out(b, cs, sn, F);
+      abc = frc_out(b, cs, sn, ab);
+      vbc = frc_out(b, cs, sn, vb);
+      if (k > 0) {
+        SV vp = v;
+        vp.w.z -= qdi;
+        v = mot_out(b, cs, sn, vp);
+        a = mot_out(b, cs, sn, xa);
+        SV Fp = Fb;
+        Fp.w.z -= gb_at(i);
+        Fb = mot_out(b, cs, sn, Fp);
+      }
+    }
+    const int p = M.seg_parent[s];
+    if (p >= 0) {
+      aF[p] = aF[p] + Fc;
+      aab[p] = aab[p] + abc;
+      avb[p] = avb[p] + vbc;
+    }
+  }
+}
+
+template <class T, class Img, class C>
+FD void rnea_vjp_seg_one(const Img& M, const float* q, const float* qd, const float* qdd, const float* gbar,
+                         float* qbar, float* qdbar, float* qddbar, const C& col) {
+  rnea_vjp_seg<T>(M, q, qd, qdd, RhsFromGlobal<T, C>{gbar, col},
+                  vjp_sink<T>(M, q, qbar, qdbar, qddbar, 1.f, col), col);
+}
+
+// ABA VJP on segments: w = M^-1 gbar by the articulated-body sweeps at zero
+// velocity and gravity (kept per dof), then the RNEA adjoint seeded with w.
+template <class T, class Img, class C>
+FD void aba_vjp_seg_one(const Img& M, const float* q, const float* qd, const float* tau, const float* qdd,
+                        const float* gbar, float* qbar, float* qdbar, float* taubar, const C& col) {
+  (void)tau;
+  LocalVec<T> w;
+  P3Local<T::NBMAX> P;
+  aba_seg_core<T, Img, false>(M, q, qd, RhsFromGlobal<T, C>{gbar, col}, OutToLocal<T>{&w}, col, P);
+  const int nv = T::kFree ? M.nb + 5 : M.nb;
+  if (taubar)
+    for (int k = 0; k < nv; ++k) col.out(taubar, k, w.x[k]);
+  rnea_vjp_seg<T>(M, q, qd, qdd, w, vjp_sink<T>(M, q, qbar, qdbar, nullptr, -1.f, col), col);
+}
+
 }  // namespace frax
