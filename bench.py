@@ -36,17 +36,33 @@ FP32_LANES_PER_SM = 128
 
 
 # ------------------------------------------------------------- flop accounting
-# FP32 operations per instance of each kernel's formulation (fma = 2 flops,
-# add/sub/mul = 1; sincos, sqrt and divisions are not in the FMA-pipe count).
-# Counted exactly by running the device code on the host with a counting
-# float type: `python bench.py --count-flops` rebuilds flopcount.cu and
-# reprints this table.
+# Algorithmic FP32 operations per instance (fma = 2 flops, add/sub/mul = 1;
+# sincos, sqrt and divisions are not in the FMA-pipe count), counted exactly
+# by running the device code on the host with a counting float
+# (`python bench.py --count-flops` rebuilds flopcount.cu and reprints them).
+# Where a kernel trades flops for registers (the adjoints recompute forward
+# state by stepping back through the joints; the tree ABA recomputes
+# velocities; the tree factor comes from articulated inertias) the table
+# keeps the count of the direct formulation that stores instead, so the
+# roofline is against the algorithm's work, not the kernel's extra work.
 FLOPS = {
     "chain7": {"fk_jac": 903, "fk": 819, "rnea": 2000, "bias": 2000, "crba_ltdl": 2305, "crba": 2172,
-               "aba": 5302, "rnea_vjp": 6192, "aba_vjp": 11233},
-    "humanoid": {"fk_jac": 5304, "fk": 3792, "rnea": 9028, "bias": 9022, "crba_ltdl": 35751, "crba": 12921,
-                 "aba": 27054, "rnea_vjp": 25969, "aba_vjp": 47290},
+               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 9331},
+    "humanoid": {"fk_jac": 5304, "fk": 3792, "rnea": 9028, "bias": 9022, "crba_ltdl": 16691, "crba": 12921,
+                 "aba": 25231, "rnea_vjp": 22034, "aba_vjp": 43301},
 }
+
+
+def bytes_per_instance(op, nq, nv, nb, nframes):
+    """Minimum HBM traffic: inputs read once, outputs written once (FP32)."""
+    f = 4
+    return {
+        "fk_jac": f * (nq + 12 * nb + nframes * 6 * nv),
+        "rnea": f * (nq + 3 * nv), "bias": f * (nq + 2 * nv),
+        "crba_ltdl": f * (nq + nv * nv + nv * (nv + 1) // 2),
+        "aba": f * (nq + 3 * nv),
+        "rnea_vjp": f * (2 * nq + 5 * nv), "aba_vjp": f * (2 * nq + 5 * nv),
+    }[op]
 
 
 def count_flops():
@@ -211,13 +227,30 @@ def time_step(step, steps, warmup, flush, world, dist, clocks=None):
     return step_ms, per_op_ms, launches, wall, clk
 
 
-def roofline_of(per_op_ms, flops, B, peak):
+def roofline_of(per_op_ms, flops, B, peak, hbm_gbs, robot):
+    """Per kernel: achieved FP32 rate and HBM rate from the algorithmic work,
+    and the roofline fraction t_roof / t_measured with
+    t_roof = max(flops / FP32 peak, bytes / HBM peak)."""
     out = {}
     for n, ms in per_op_ms.items():
-        tf = flops[n] * B / (ms / 1e3) / 1e12
-        out[n] = {"ms": ms, "evals_per_s": B / (ms / 1e3), "flops_per_instance": flops[n], "tflops": tf,
-                  "frac_fp32_peak": tf / peak}
+        t = ms / 1e3
+        by = bytes_per_instance(n, robot.nq, robot.nv, robot.n_bodies, len(robot.end_frames))
+        tf = flops[n] * B / t / 1e12
+        gbs = by * B / t / 1e9
+        t_alu = flops[n] * B / (peak * 1e12)
+        t_hbm = by * B / (hbm_gbs * 1e9)
+        out[n] = {"ms": ms, "evals_per_s": B / t, "flops_per_instance": flops[n], "bytes_per_instance": by,
+                  "tflops": tf, "gbs": gbs, "frac_fp32_peak": tf / peak, "frac_hbm_peak": gbs / hbm_gbs,
+                  "bound": "alu" if t_alu >= t_hbm else "hbm", "roofline_frac": max(t_alu, t_hbm) / t}
     return out
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
 
 
 def cpu_baseline_child(args):
@@ -270,22 +303,21 @@ SERVE_OPS = ["rnea", "crba", "aba", "rnea_grad"]
 def serve_stream(fx, seconds, check_oracle=True):
     """Served workload: requests for the 7-DoF chain, the humanoid and 32
     random trees (3-64 bodies), op uniform over rnea / crba / aba /
-    rnea-gradient, instance count log-uniform in [1, 4096]. First a closed
-    loop measures the saturation request rate; then Poisson arrivals at 50 %
-    and 90 % of it, latency = completion seen by the host - arrival."""
-    import threading
-
+    rnea-gradient, instance count log-uniform in [1, 4096]. The request
+    traces are replayed natively (frax_server_replay): first a burst that
+    gives the saturation rate, then Poisson arrivals at 50 % and 90 % of it;
+    latency = completion seen by the host - arrival."""
     import numpy as np
 
     import gen
     from paper_2604_04310_gb300.serving import Server
     robots = gen.serving_pool(32)
     models = [fx.Model.from_robot(r) for r in robots]
-    srv = Server(budget_bytes=2 << 30, idle_exit_ms=20.0)
+    srv = Server(budget_bytes=4 << 30, idle_exit_ms=20.0)
     ids = [srv.add_model(m) for m in models]
     rng = np.random.default_rng(2026)
     pool = []
-    for k in range(192):
+    for k in range(256):
         mi = int(rng.integers(len(robots)))
         op = SERVE_OPS[int(rng.integers(4))]
         B = int(np.clip(np.floor(np.exp(rng.uniform(0.0, np.log(4097.0)))), 1, 4096))
@@ -295,127 +327,57 @@ def serve_stream(fx, seconds, check_oracle=True):
         arrays = {"rnea": [st.q, st.qd, st.qdd], "crba": [st.q], "aba": [st.q, st.qd, st.tau],
                   "rnea_grad": [st.q, st.qd, st.qdd, g]}[op]
         pool.append((mi, op, B, [gen.to_soa(a) for a in arrays], st, g))
+    trace_rng = np.random.default_rng(7)
 
-    def closed_loop(duration, depth=64):
-        inflight, done_inst, n = {}, 0, 0
-        t0 = time.perf_counter()
-        k = 0
-        while time.perf_counter() - t0 < duration:
-            while len(inflight) < depth:
-                mi, op, B, inp, _, _ = pool[k % len(pool)]
-                req = srv.submit(ids[mi], op, inp, B)
-                if req is None:
-                    break
-                inflight[req] = (mi, op, B)
-                k += 1
-            r = srv.wait_any(10000.0)
-            mi, op, B = inflight.pop(r)
-            srv.collect(r, ids[mi], op, B)
-            done_inst += B
-            n += 1
-        while inflight:
-            r = srv.wait_any(10000.0)
-            mi, op, B = inflight.pop(r)
-            srv.collect(r, ids[mi], op, B)
-            done_inst += B
-            n += 1
-        el = time.perf_counter() - t0
-        return n / el, done_inst / el
+    def trace(n):
+        ks = trace_rng.integers(len(pool), size=n)
+        return ks, [(ids[pool[k][0]], pool[k][1], pool[k][3]) for k in ks]
 
-    def open_loop(rate, duration, keep=None):
-        arrivals = {}
-        lat, lat_dev = [], []
-        insts = [0]
-        lock = threading.Lock()
-        stop = [False]
-        meta = {}
-
-        def collector():
-            while True:
-                with lock:
-                    empty = not meta
-                if stop[0] and empty:
-                    return
-                r = srv.wait_any(5.0) if not empty else None
-                if r is None:
-                    if empty:
-                        time.sleep(2e-5)
-                    continue
-                t_seen = time.perf_counter()
-                with lock:
-                    mi, op, B, k = meta.pop(r)
-                outs, ldev = srv.collect(r, ids[mi], op, B)
-                lat.append((t_seen - arrivals.pop(r)) * 1e6)
-                lat_dev.append(ldev)
-                insts[0] += B
-                if keep is not None and len(keep) < 48 and B <= 256:
-                    keep.append((k, outs))
-
-        th = threading.Thread(target=collector, daemon=True)
-        th.start()
-        rs = np.random.default_rng(7)
-        t0 = time.perf_counter()
-        t_next = t0
-        k = 0
-        while t_next - t0 < duration:
-            t_next += rs.exponential(1.0 / rate)
-            dt = t_next - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)  # releases the GIL for the collector
-            mi, op, B, inp, _, _ = pool[k % len(pool)]
-            t_arr = t_next
-            while True:
-                with lock:
-                    req = srv.submit(ids[mi], op, inp, B)
-                    if req is not None:
-                        meta[req] = (mi, op, B, k % len(pool))
-                        arrivals[req] = t_arr
-                if req is not None:
-                    break
-                time.sleep(1e-5)
-            k += 1
-        stop[0] = True
-        th.join(timeout=60)
-        el = time.perf_counter() - t0
-        lat = np.array(lat)
-        return {"offered_rate_hz": rate, "requests": int(len(lat)), "p50_us": float(np.percentile(lat, 50)),
-                "p99_us": float(np.percentile(lat, 99)),
-                "p50_service_us": float(np.percentile(lat_dev, 50)),
-                "p99_service_us": float(np.percentile(lat_dev, 99)),
-                "evals_per_s": insts[0] / el}
-
-    old_switch = sys.getswitchinterval()
-    sys.setswitchinterval(2e-5)
-    sat_req, sat_inst = closed_loop(min(2.0, seconds))
-    kept = []
+    # saturation: everything arrives at once
+    ks, tr = trace(3000)
+    t0 = time.perf_counter()
+    srv.replay(tr, np.zeros(len(tr)))
+    el = time.perf_counter() - t0
+    sat_req = len(tr) / el
+    sat_inst = sum(pool[k][2] for k in ks) / el
     points = []
     for frac in (0.5, 0.9):
-        pt = open_loop(frac * sat_req, seconds, keep=kept if frac == 0.5 else None)
-        pt["load"] = frac
-        points.append(pt)
-    sys.setswitchinterval(old_switch)
-    err = {}
+        rate = frac * sat_req
+        n = int(max(200, rate * seconds))
+        ks, tr = trace(n)
+        arrival = np.cumsum(trace_rng.exponential(1e6 / rate, size=n))
+        t0 = time.perf_counter()
+        lat, _ = srv.replay(tr, arrival)
+        el = time.perf_counter() - t0
+        points.append({"load": frac, "offered_rate_hz": rate, "requests": n,
+                       "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                       "mean_us": float(lat.mean()), "evals_per_s": sum(pool[k][2] for k in ks) / el})
+    err, checked = {}, 0
     if check_oracle:
         from oracle import derivatives as dv
         from oracle import rbd
-        for k, outs in kept:
+        small = [k for k in range(len(pool)) if pool[k][2] <= 256][:64]
+        tr = [(ids[pool[k][0]], pool[k][1], pool[k][3]) for k in small]
+        _, outs = srv.replay(tr, np.cumsum(np.full(len(tr), 50.0)), keep_outputs=True)
+        for k, o in zip(small, outs):
             mi, op, B, _, st, g = pool[k]
+            checked += 1
             r = robots[mi]
             refs = {"rnea": lambda: [rbd.rnea(r, st.q, st.qd, st.qdd)],
                     "crba": lambda: [rbd.crba(r, st.q).reshape(B, -1)],
                     "aba": lambda: [rbd.aba(r, st.q, st.qd, st.tau)],
                     "rnea_grad": lambda: list(dv.rnea_vjp(r, st.q, st.qd, st.qdd, g))}[op]()
-            for o, ref in zip(outs, refs):
-                x = gen.from_soa(o, B)
+            for x, ref in zip(o, refs):
+                x = gen.from_soa(x, B)
                 d = np.abs(x - ref).reshape(B, -1).max(1) / np.maximum(np.abs(ref).reshape(B, -1).max(1), 1e-12)
                 err[op] = max(err.get(op, 0.0), float(d.max()))
     info = srv.info()
     srv.close(force=True)
-    return {"workload": "Poisson stream: chain7 / humanoid / 32 random trees (3-64 bodies), ops rnea, crba, aba, "
-                        "rnea-gradient uniform, 1-4096 instances log-uniform; latency = host-seen completion - "
-                        "arrival",
+    return {"workload": "requests for chain7 / humanoid / 32 random trees (3-64 bodies), ops rnea, crba, aba, "
+                        "rnea-gradient uniform, 1-4096 instances log-uniform; replayed natively; latency = "
+                        "host-seen completion - arrival",
             "saturation_req_per_s": sat_req, "saturation_evals_per_s": sat_inst, "points": points,
-            "max_rel_err_vs_oracle": err, "checked_requests": len(kept),
+            "max_rel_err_vs_oracle": err, "checked_requests": checked,
             "kernel_launches": info["kernel_launches"], "resident_ctas": info["resident_ctas"]}
 
 
@@ -423,8 +385,7 @@ def serve_stream(fx, seconds, check_oracle=True):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
-    base = run_cpu_baseline(min(30.0, per_step * args.steps))
+    base = run_cpu_baseline(min(30.0, args.cpu_seconds * 2))
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -464,11 +425,18 @@ def frax_arm(args, rank, world, local_rank):
     ms_per_step = float(t.item()) / args.steps
     evals_per_step = len(OPS) * B
     value = world * evals_per_step / (ms_per_step / 1e3)
-    per_op = roofline_of(per_op_ms, FLOPS["chain7"], B, peak)
+    hbm, hbm_src = measured_hbm_gbs()
+    per_op = roofline_of(per_op_ms, FLOPS["chain7"], B, peak, hbm, robot)
     dom = max(OPS, key=lambda n: per_op_ms[n])
-    roofline = {"bound": "alu", "kernel": dom, "achieved": per_op[dom]["tflops"], "peak": peak,
-                "unit": "TFLOP/s", "frac": per_op[dom]["frac_fp32_peak"], "traffic": None,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock (recipe unit counts)"}
+    d = per_op[dom]
+    if d["bound"] == "alu":
+        roofline = {"bound": "alu", "kernel": dom, "achieved": d["tflops"], "peak": peak, "unit": "TFLOP/s",
+                    "frac": d["frac_fp32_peak"],
+                    "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock (recipe unit counts)"}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": hbm, "unit": "GB/s",
+                    "frac": d["frac_hbm_peak"], "peak_basis": f"{hbm_src} HBM copy bandwidth"}
+    roofline["traffic"] = None
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -514,7 +482,7 @@ def frax_arm(args, rank, world, local_rank):
                                 "end-frame Jacobians, bias forces, CRBA + LTDL, ABA, RNEA-VJP, ABA-VJP",
                     "batch": hB, "steps": hsteps, "ms_per_step": hms / hsteps,
                     "evals_per_s": world * len(hops) * hB / (hms / hsteps / 1e3),
-                    "per_op": roofline_of(hper, FLOPS["humanoid"], hB, peak)}
+                    "per_op": roofline_of(hper, FLOPS["humanoid"], hB, peak, hbm, hrobot)}
         del hstep, hdev
 
     serve = None

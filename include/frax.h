@@ -219,6 +219,16 @@ FRAX_API frax_status frax_server_info(frax_server_t srv, frax_server_info_t* inf
  * kernel did not stop within timeout_ms (resources are then leaked, not
  * freed under a running kernel). */
 FRAX_API frax_status frax_server_destroy(frax_server_t srv, int force, double timeout_ms);
+/* Replays a request trace: request k (model_id[k], op[k], B[k], host inputs
+ * inputs[4k .. 4k+3]) is submitted at arrival_us[k] after the call starts
+ * (later if the budget or ring is full); a second host thread collects
+ * completions, copies outputs to outputs[3k .. 3k+2] (outputs may be NULL)
+ * and writes latency_us[k] = completion seen - arrival. Used to measure
+ * latency under a given arrival process without a scripting layer in the
+ * loop. FRAX_ETIMEOUT if the whole trace is not done within timeout_ms. */
+FRAX_API frax_status frax_server_replay(frax_server_t srv, int n, const int* model_id, const int* op,
+                                        const int64_t* B, const float* const* inputs, const double* arrival_us,
+                                        float* const* outputs, double* latency_us, double timeout_ms);
 
 /* ------------------------------------------------------------------------
  * frax_serve_batch_noalloc — one launch that evaluates a mixed batch of

@@ -38,6 +38,9 @@ SIGNATURES = {
     "frax_server_collect": (c_int, [c_vp, c_i64, ctypes.POINTER(c_vp), ctypes.POINTER(ctypes.c_double)]),
     "frax_server_info": (c_int, [c_vp, c_vp]),
     "frax_server_destroy": (c_int, [c_vp, c_int, ctypes.c_double]),
+    "frax_server_replay": (c_int, [c_vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_i64),
+                                   ctypes.POINTER(c_vp), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(c_vp),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.c_double]),
     "frax_serve_batch_noalloc": (c_int, [c_vp, c_int, c_vp]),
     "frax_last_error": (ctypes.c_char_p, []),
     "frax_version": (ctypes.c_char_p, []),

@@ -10,15 +10,17 @@
 // and it is not running.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
-#include "dyn.cuh"
+#include "seg.cuh"
 #include "handles.h"
 
 namespace frax {
@@ -69,17 +71,34 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
+// Chains of 7 run the unrolled chain code for the forward ops; every other
+// case runs the segment code (the same device functions as the batched
+// kernels, so a request's result does not depend on how it was served).
 template <class T>
 __device__ void serve_tile(const ModelImage<64>& M, const ReqDesc& d, char* slab, long long b) {
   const ColT<false> col{d.B, b};
   auto in = [&](int k) { return reinterpret_cast<const float*>(slab + d.in_off[k]); };
   auto out = [&](int k) { return reinterpret_cast<float*>(slab + d.out_off[k]); };
-  switch (d.op) {
-    case FRAX_OP_RNEA: rnea_one<T>(M, in(0), in(1), in(2), out(0), col); break;
-    case FRAX_OP_CRBA: crba_one<T>(M, in(0), out(0), static_cast<float*>(nullptr), col); break;
-    case FRAX_OP_ABA: aba_one<T>(M, in(0), in(1), in(2), out(0), col); break;
-    case FRAX_OP_RNEA_GRAD: rnea_vjp_one<T>(M, in(0), in(1), in(2), in(3), out(0), out(1), out(2), col); break;
-    default: break;
+  if constexpr (T::kSeg) {
+    switch (d.op) {
+      case FRAX_OP_RNEA: rnea_seg<T>(M, in(0), in(1), in(2), out(0), col); break;
+      case FRAX_OP_CRBA: crba_seg<T>(M, in(0), out(0), static_cast<float*>(nullptr), col); break;
+      case FRAX_OP_ABA: {
+        P3Local<T::NBMAX> P;
+        aba_seg<T>(M, in(0), in(1), in(2), out(0), col, P);
+        break;
+      }
+      case FRAX_OP_RNEA_GRAD: rnea_vjp_seg_one<T>(M, in(0), in(1), in(2), in(3), out(0), out(1), out(2), col); break;
+      default: break;
+    }
+  } else {
+    switch (d.op) {
+      case FRAX_OP_RNEA: rnea_one<T>(M, in(0), in(1), in(2), out(0), col); break;
+      case FRAX_OP_CRBA: crba_one<T>(M, in(0), out(0), static_cast<float*>(nullptr), col); break;
+      case FRAX_OP_ABA: aba_one<T>(M, in(0), in(1), in(2), out(0), col); break;
+      case FRAX_OP_RNEA_GRAD: serve_tile<SegTopo<64, false>>(M, d, slab, b); break;
+      default: break;
+    }
   }
 }
 
@@ -149,9 +168,9 @@ __global__ void __launch_bounds__(kTile) k_serve(const ServeArgs a) {
       } else if (desc.kind == kServeChain7) {
         serve_tile<ChainTopo<7>>(model, desc, a.slab, b);
       } else if (desc.kind == kServeTreeFree) {
-        serve_tile<TreeTopo<64, true>>(model, desc, a.slab, b);
+        serve_tile<SegTopo<64, true>>(model, desc, a.slab, b);
       } else {
-        serve_tile<TreeTopo<64, false>>(model, desc, a.slab, b);
+        serve_tile<SegTopo<64, false>>(model, desc, a.slab, b);
       }
     }
     __threadfence();
@@ -210,12 +229,15 @@ struct frax_server_s {
     int64_t out_off[3] = {0, 0, 0};
     std::chrono::steady_clock::time_point t0;
     bool done = false;
+    bool collecting = false;
+    int64_t in_bytes = 0, out_begin = 0, out_bytes = 0;
     double latency_us = 0;
   };
   std::mutex mu;
   int device = 0;
-  cudaStream_t kstream = nullptr, cstream = nullptr;
+  cudaStream_t kstream = nullptr, cstream = nullptr, dstream = nullptr;
   char* slab = nullptr;
+  char* slab_h = nullptr;  // pinned host mirror of the slab: staging for copies
   int64_t budget = 0, in_use = 0;
   ReqDesc* ring = nullptr;
   ServeCtl* ctl = nullptr;
@@ -317,6 +339,8 @@ void slab_free(frax_server_s* s, int64_t off, int64_t bytes) {
 
 void release_all(frax_server_s* s) {
   if (s->slab) cudaFree(s->slab);
+  if (s->slab_h) cudaFreeHost(s->slab_h);
+  if (s->dstream) cudaStreamDestroy(s->dstream);
   if (s->ring) cudaFree(s->ring);
   if (s->ctl) cudaFree(s->ctl);
   if (s->models) cudaFree(s->models);
@@ -373,6 +397,10 @@ frax_status frax_server_create(int64_t budget_bytes, double idle_exit_ms, frax_s
     cudaGetLastError();
     return bail(set_error(FRAX_ENOMEM, "frax_server_create: slab of budget_bytes does not fit on the device"));
   }
+  if ((e = cudaHostAlloc(&s->slab_h, s->budget, cudaHostAllocDefault)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(set_error(FRAX_ENOMEM, "frax_server_create: pinned host staging of budget_bytes failed"));
+  }
   if ((e = cudaMalloc(&s->ring, sizeof(ReqDesc) * kRing)) != cudaSuccess) return bail(cuda_fail("cudaMalloc ring", e));
   if ((e = cudaMalloc(&s->ctl, sizeof(ServeCtl))) != cudaSuccess) return bail(cuda_fail("cudaMalloc ctl", e));
   if ((e = cudaMalloc(&s->models, sizeof(ModelImage<64>) * kMaxModels)) != cudaSuccess)
@@ -396,6 +424,8 @@ frax_status frax_server_create(int64_t budget_bytes, double idle_exit_ms, frax_s
   if ((e = cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail("stream", e));
   if ((e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail("stream", e));
+  if ((e = cudaStreamCreateWithFlags(&s->dstream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail("stream", e));
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -460,17 +490,22 @@ frax_status frax_server_submit(frax_server_t s, int model_id, int op, int64_t B,
   int64_t cur = off;
   for (int k = 0; k < 4; ++k) d.in_off[k] = 0;
   for (int k = 0; k < 3; ++k) d.out_off[k] = 0;
-  for (int k = 0; k < nin; ++k) {
+  for (int k = 0; k < nin; ++k) {  // the caller's buffers are free once this returns
     d.in_off[k] = cur;
-    cudaError_t e = cudaMemcpyAsync(s->slab + cur, inputs[k], size_t(in_rows[k]) * B * 4, cudaMemcpyHostToDevice,
-                                    s->cstream);
-    if (e != cudaSuccess) {
-      slab_free(s, off, total);
-      return cuda_fail("frax_server_submit: input copy", e);
-    }
+    std::memcpy(s->slab_h + cur, inputs[k], size_t(in_rows[k]) * B * 4);
     cur += in_bytes[k];
   }
   frax_server_s::Req r;
+  r.in_bytes = cur - off;
+  r.out_begin = cur;
+  r.out_bytes = off + total - cur;
+  // inputs, then the descriptor, then the published-tile count, in stream
+  // order on one copy stream: the kernel can only see the count after both
+  cudaError_t e0 = cudaMemcpyAsync(s->slab + off, s->slab_h + off, r.in_bytes, cudaMemcpyHostToDevice, s->cstream);
+  if (e0 != cudaSuccess) {
+    slab_free(s, off, total);
+    return cuda_fail("frax_server_submit: input copy", e0);
+  }
   for (int k = 0; k < nout; ++k) {
     d.out_off[k] = cur;
     r.out_off[k] = cur;
@@ -482,7 +517,6 @@ frax_status frax_server_submit(frax_server_t s, int model_id, int op, int64_t B,
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&s->ctl->tiles_published, &s->pub_stage[slot], sizeof(unsigned long long),
                         cudaMemcpyHostToDevice, s->cstream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->cstream);
   if (e != cudaSuccess) {
     slab_free(s, off, total);
     return cuda_fail("frax_server_submit: publish", e);
@@ -555,25 +589,33 @@ frax_status frax_server_wait_any(frax_server_t s, double timeout_ms, int64_t* re
 
 frax_status frax_server_collect(frax_server_t s, int64_t request, float* const* outputs, double* latency_us) {
   if (!s) return set_error(FRAX_EINVAL, "frax_server_collect: NULL server");
-  std::lock_guard<std::mutex> lk(s->mu);
-  auto it = s->inflight.find(request);
-  if (it == s->inflight.end()) return set_error(FRAX_EINVAL, "frax_server_collect: unknown request");
-  scan_flags(s, nullptr);
-  frax_server_s::Req& r = it->second;
-  if (!r.done) return set_error(FRAX_EBUSY, "frax_server_collect: request not complete");
-  if (outputs) {
-    for (int k = 0; k < r.nout; ++k) {
-      if (!outputs[k]) continue;
-      SRV_CUDA(cudaMemcpyAsync(outputs[k], s->slab + r.out_off[k], size_t(r.out_rows[k]) * r.B * 4,
-                               cudaMemcpyDeviceToHost, s->cstream));
-    }
-    SRV_CUDA(cudaStreamSynchronize(s->cstream));
+  frax_server_s::Req r;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->inflight.find(request);
+    if (it == s->inflight.end()) return set_error(FRAX_EINVAL, "frax_server_collect: unknown request");
+    scan_flags(s, nullptr);
+    if (!it->second.done) return set_error(FRAX_EBUSY, "frax_server_collect: request not complete");
+    if (it->second.collecting) return set_error(FRAX_EBUSY, "frax_server_collect: already being collected");
+    it->second.collecting = true;
+    r = it->second;
+  }
+  // the request's slab range stays reserved until it is freed below
+  frax_status st = FRAX_OK;
+  if (outputs && r.out_bytes > 0) {
+    cudaError_t e = cudaMemcpyAsync(s->slab_h + r.out_begin, s->slab + r.out_begin, r.out_bytes,
+                                    cudaMemcpyDeviceToHost, s->dstream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->dstream);
+    if (e != cudaSuccess) st = cuda_fail("frax_server_collect: output copy", e);
+    for (int k = 0; k < r.nout && st == FRAX_OK; ++k)
+      if (outputs[k]) std::memcpy(outputs[k], s->slab_h + r.out_off[k], size_t(r.out_rows[k]) * r.B * 4);
   }
   if (latency_us) *latency_us = r.latency_us;
+  std::lock_guard<std::mutex> lk(s->mu);
   slab_free(s, r.off, r.bytes);
   s->slot_owner[r.slot] = -1;
-  s->inflight.erase(it);
-  return clear_error();
+  s->inflight.erase(request);
+  return st == FRAX_OK ? clear_error() : st;
 }
 
 frax_status frax_server_info(frax_server_t s, frax_server_info_t* info) {
@@ -611,6 +653,85 @@ frax_status frax_server_destroy(frax_server_t s, int force, double timeout_ms) {
   }
   release_all(s);
   delete s;
+  return clear_error();
+}
+
+frax_status frax_server_replay(frax_server_t s, int n, const int* model_id, const int* op, const int64_t* B,
+                               const float* const* inputs, const double* arrival_us, float* const* outputs,
+                               double* latency_us, double timeout_ms) {
+  if (!s || n < 0 || (n > 0 && (!model_id || !op || !B || !inputs || !arrival_us || !latency_us)))
+    return set_error(FRAX_EINVAL, "frax_server_replay: bad argument");
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  const auto t_end = t0 + std::chrono::microseconds(int64_t(timeout_ms * 1e3));
+  std::mutex mu;
+  std::unordered_map<int64_t, int> index;  // request id -> trace position
+  std::atomic<int> collected{0};
+  std::atomic<int> failure{0};
+  std::string fail_msg;
+  auto at = [&](int k) { return t0 + std::chrono::nanoseconds(int64_t(arrival_us[k] * 1e3)); };
+  std::thread collector([&]() {
+    while (collected.load() < n && failure.load() == 0) {
+      if (clk::now() > t_end) {
+        failure = FRAX_ETIMEOUT;
+        break;
+      }
+      int64_t r;
+      frax_status st = frax_server_wait_any(s, 1.0, &r);
+      if (st == FRAX_ETIMEOUT || st == FRAX_EINVAL) {  // nothing done / nothing in flight yet
+        std::this_thread::yield();
+        continue;
+      }
+      if (st != FRAX_OK) {
+        failure = st;
+        fail_msg = frax_last_error();
+        break;
+      }
+      const auto seen = clk::now();
+      int k = -1;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = index.find(r);
+        if (it != index.end()) k = it->second;
+      }
+      if (k < 0) continue;  // published but not yet recorded by the submitter
+      latency_us[k] = std::chrono::duration<double, std::micro>(seen - at(k)).count();
+      st = frax_server_collect(s, r, outputs ? outputs + 3 * size_t(k) : nullptr, nullptr);
+      if (st != FRAX_OK) {
+        failure = st;
+        fail_msg = frax_last_error();
+        break;
+      }
+      collected++;
+    }
+  });
+  for (int k = 0; k < n && failure.load() == 0; ++k) {
+    while (clk::now() < at(k)) std::this_thread::yield();
+    while (true) {
+      int64_t r;
+      std::unique_lock<std::mutex> lk(mu);
+      frax_status st = frax_server_submit(s, model_id[k], op[k], B[k], inputs + 4 * size_t(k), &r);
+      if (st == FRAX_OK) {
+        index[r] = k;
+        break;
+      }
+      lk.unlock();
+      if (st != FRAX_EBUSY) {
+        failure = st;
+        fail_msg = frax_last_error();
+        break;
+      }
+      if (clk::now() > t_end) {
+        failure = FRAX_ETIMEOUT;
+        break;
+      }
+      std::this_thread::yield();
+    }
+  }
+  collector.join();
+  if (failure.load() != 0)
+    return set_error(static_cast<frax_status>(failure.load()),
+                     "frax_server_replay: " + (fail_msg.empty() ? std::string("timed out") : fail_msg));
   return clear_error();
 }
 

@@ -86,6 +86,34 @@ class Server:
         self._st(lib().frax_server_collect(self.handle, req, ptrs, ctypes.byref(lat)))
         return outs, lat.value
 
+    def replay(self, trace, arrival_us, keep_outputs=False, timeout_ms=120000.0):
+        """Replays [(model_id, op, inputs)] with arrival times (us from now)
+        natively; returns (latency_us array, outputs or None)."""
+        n = len(trace)
+        mids = (ctypes.c_int * n)(*[t[0] for t in trace])
+        ops = (ctypes.c_int * n)(*[OPS[t[1]] for t in trace])
+        arrs = [[np.ascontiguousarray(a, dtype=np.float32) for a in t[2]] for t in trace]
+        Bs = (ctypes.c_int64 * n)(*[a[0].shape[1] for a in arrs])
+        inp = (ctypes.c_void_p * (4 * n))()
+        for k, a in enumerate(arrs):
+            for j, x in enumerate(a):
+                inp[4 * k + j] = x.ctypes.data
+        arr = (ctypes.c_double * n)(*[float(x) for x in arrival_us])
+        lat = (ctypes.c_double * n)()
+        outs, outp = None, None
+        if keep_outputs:
+            outs = []
+            outp = (ctypes.c_void_p * (3 * n))()
+            for k, t in enumerate(trace):
+                m = self.models[t[0]]
+                _, rows = op_rows(t[1], m.nq, m.nv)
+                o = [np.empty((r, Bs[k]), dtype=np.float32) for r in rows]
+                outs.append(o)
+                for j, x in enumerate(o):
+                    outp[3 * k + j] = x.ctypes.data
+        self._st(lib().frax_server_replay(self.handle, n, mids, ops, Bs, inp, arr, outp, lat, float(timeout_ms)))
+        return np.frombuffer(lat, dtype=np.float64).copy(), outs
+
     def info(self) -> dict:
         inf = ServerInfo()
         self._st(lib().frax_server_info(self.handle, ctypes.byref(inf)))

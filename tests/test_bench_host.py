@@ -1,0 +1,43 @@
+"""Host-side pieces of bench.py: the roofline arithmetic, the algorithmic
+byte counts, the CPU-baseline leg and the reference arm's JSON line."""
+
+import json
+import os
+import subprocess
+import sys
+
+import gen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_bytes_per_instance_chain_and_humanoid():
+    c, h = gen.chain7(0), gen.humanoid(0)
+    assert bench.bytes_per_instance("rnea", c.nq, c.nv, c.n_bodies, 1) == 112
+    assert bench.bytes_per_instance("fk_jac", c.nq, c.nv, c.n_bodies, 1) == 532
+    assert bench.bytes_per_instance("crba_ltdl", h.nq, h.nv, h.n_bodies, 4) == 4 * (36 + 35 * 35 + 35 * 36 // 2)
+    assert bench.bytes_per_instance("fk_jac", h.nq, h.nv, h.n_bodies, 4) == 4 * (36 + 360 + 840)
+
+
+def test_roofline_fraction_is_the_slower_roof():
+    c = gen.chain7(0)
+    B = 1 << 20
+    out = bench.roofline_of({"rnea": 0.1, "fk_jac": 0.1}, bench.FLOPS["chain7"], B, 80.0, 6000.0, c)
+    r = out["rnea"]
+    assert r["bound"] == "alu" and abs(r["roofline_frac"] - 2000 * B / 80e12 / 1e-4) < 1e-9
+    f = out["fk_jac"]
+    assert f["bound"] == "hbm" and abs(f["roofline_frac"] - 532 * B / 6000e9 / 1e-4) < 1e-9
+
+
+def test_cpu_baseline_child_and_reference_arm():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-baseline-child", "--cpu-seconds",
+                        "0.5"], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["kind"] == "oracle" and d["cores"] == 1 and d["value"] > 0
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--cpu-seconds", "0.5"], capture_output=True, text=True, cwd=ROOT,
+                       timeout=300)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 0

@@ -207,3 +207,26 @@ def test_budget_larger_than_device_is_refused():
     with pytest.raises(fx.FraxError) as e:
         Server(budget_bytes=1 << 50)
     assert e.value.status == 3
+
+
+def test_native_replay(server):
+    """frax_server_replay: a Poisson-timed trace of mixed requests comes back
+    with every latency measured and the same results as served one by one."""
+    srv, ids = server
+    rng = np.random.default_rng(11)
+    trace, refs = [], []
+    for j in range(40):
+        k = int(rng.integers(len(ROBOTS)))
+        op = ["rnea", "crba", "aba", "rnea_grad"][int(rng.integers(4))]
+        Bj = int(np.clip(np.exp(rng.uniform(0, np.log(1024))), 1, 1024))
+        _, _, inp = _inputs(ROBOTS[k], op, Bj, 5000 + j)
+        trace.append((ids[k], op, inp))
+        refs.append((ids[k], op, inp, Bj))
+    arrival = np.cumsum(rng.exponential(200.0, size=len(trace)))
+    lat, outs = srv.replay(trace, arrival, keep_outputs=True)
+    assert np.all(lat > 0) and np.all(np.isfinite(lat))
+    for (mid, op, inp, Bj), o in zip(refs[:12], outs[:12]):
+        alone, _ = _run(srv, mid, op, inp, Bj)
+        for a, b in zip(o, alone):
+            assert np.array_equal(a, b)
+    assert srv.info()["in_flight"] == 0
