@@ -1,5 +1,7 @@
 // __global__ wrappers: one thread per instance, 128-thread blocks, the model
 // image as a __grid_constant__ parameter (read through the constant bank).
+// The chain kernels' register caps (blocks per SM in __launch_bounds__) were
+// chosen by measurement: more resident warps beat the few spills they cause.
 #pragma once
 #include "dyn.cuh"
 #include "seg.cuh"
@@ -13,7 +15,7 @@ namespace frax {
   const Col col{ld, b};
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_fk(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_fk(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                 int64_t ld, const float* q, float* pose,
                                                 const __grid_constant__ Frames fr, float* J) {
   FRAX_TID();
@@ -21,7 +23,7 @@ __global__ void __launch_bounds__(kBlock) k_fk(const __grid_constant__ ModelImag
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_rnea(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_rnea(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                   int64_t ld, const float* q, const float* qd,
                                                   const float* qdd, float* tau) {
   FRAX_TID();
@@ -29,14 +31,14 @@ __global__ void __launch_bounds__(kBlock) k_rnea(const __grid_constant__ ModelIm
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_crba(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_crba(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                   int64_t ld, const float* q, float* Mout, float* LD) {
   FRAX_TID();
   crba_one<T>(M, q, Mout, LD, col);
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_aba(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 4) k_aba(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                  int64_t ld, const float* q, const float* qd,
                                                  const float* tau, float* qdd) {
   FRAX_TID();
