@@ -44,10 +44,12 @@ FP32_LANES_PER_SM = 128
 # state by stepping back through the joints; the tree ABA recomputes
 # velocities; the tree factor comes from articulated inertias) the table
 # keeps the count of the direct formulation that stores instead, so the
-# roofline is against the algorithm's work, not the kernel's extra work.
+# roofline is against the algorithm's work, not the kernel's extra work. The
+# chain ABA adjoint = its M^-1 solve through the mass-matrix factor (2389)
+# plus the stored-state RNEA adjoint (4913).
 FLOPS = {
     "chain7": {"fk_jac": 903, "fk": 819, "rnea": 2000, "bias": 2000, "crba_ltdl": 2305, "crba": 2172,
-               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 9331},
+               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 7302},
     "humanoid": {"fk_jac": 5304, "fk": 3792, "rnea": 9028, "bias": 9022, "crba_ltdl": 16691, "crba": 12921,
                  "aba": 25231, "rnea_vjp": 22034, "aba_vjp": 43301},
 }

@@ -96,8 +96,10 @@ void count_chain_vjp(const Img& M) {
     g = Counts{};
   };
   g = Counts{};
-  rnea_vjp_seg_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp");
-  aba_vjp_seg_one<T>(M, q.data(), qd.data(), tau.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp");
+  rnea_vjp_seg_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp_seg");
+  aba_vjp_chain_one<7>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp_chain");
+  std::vector<CF> w(8);
+  chain_minv<7>(M, q.data(), gb.data(), w.data(), col); rep("minv_factor");
 }
 
 int main(int argc, char** argv) {

@@ -742,4 +742,77 @@ FD void aba_vjp_seg_one(const Img& M, const float* q, const float* qd, const flo
   rnea_vjp_seg<T>(M, q, qd, qdd, w, vjp_sink<T>(M, q, qbar, qdbar, nullptr, -1.f, col), col);
 }
 
+// ============================================= chain ABA VJP via the factor
+// For a short serial chain the solve w = M^-1 gbar is cheaper through the
+// mass matrix than through articulated inertias: composite inertias give M's
+// lower triangle (registers), factored in place as M = L^T D L, then
+// L^T u = gbar (back substitution), L w = D^-1 u (forward substitution).
+// The rest is the segment RNEA adjoint seeded with w.
+template <int N, class Img, class C>
+FD void chain_minv(const Img& M, const float* __restrict__ q, const float* __restrict__ g, float* w,
+                   const C& col) {
+  using T = ChainTopo<N>;
+  constexpr int NT = N * (N + 1) / 2;
+  float H[NT];
+  float cq[N], sq[N];
+  RBI Ic[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    Ic[i] = rbi_of(M.body[i]);
+    sincosf(col.in(q, i), &sq[i], &cq[i]);
+  }
+#pragma unroll
+  for (int i = N - 1; i >= 1; --i) Ic[i - 1] = rbi_add(Ic[i - 1], rbi_out(M.body[i], cq[i], sq[i], Ic[i]));
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    SV F{mk(Ic[i].xz, Ic[i].yz, Ic[i].zz), mk(-Ic[i].h.y, Ic[i].h.x, 0.f)};
+    H[MSink::tri(i, i)] = F.w.z;
+#pragma unroll
+    for (int j = i; j >= 1; --j) {
+      F = frc_out(M.body[j], cq[j], sq[j], F);
+      H[MSink::tri(i, j - 1)] = F.w.z;
+    }
+  }
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    const float rk = 1.f / H[MSink::tri(k, k)];
+#pragma unroll
+    for (int i = k - 1; i >= 0; --i) {
+      const float a = H[MSink::tri(k, i)] * rk;
+#pragma unroll
+      for (int j = i; j >= 0; --j) H[MSink::tri(i, j)] = fmaf(-a, H[MSink::tri(k, j)], H[MSink::tri(i, j)]);
+      H[MSink::tri(k, i)] = a;
+    }
+  }
+  float u[N];
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    float x = col.in(g, k);
+#pragma unroll
+    for (int i = k + 1; i < N; ++i) x = fmaf(-H[MSink::tri(i, k)], u[i], x);
+    u[k] = x;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    float x = u[k] / H[MSink::tri(k, k)];
+#pragma unroll
+    for (int j = 0; j < k; ++j) x = fmaf(-H[MSink::tri(k, j)], w[j], x);
+    w[k] = x;
+  }
+  (void)sizeof(T);
+}
+
+template <int N, class Img, class C>
+FD void aba_vjp_chain_one(const Img& M, const float* q, const float* qd, const float* qdd, const float* gbar,
+                          float* qbar, float* qdbar, float* taubar, const C& col) {
+  using S = SegTopo<N + 1, false>;
+  LocalVec<S> w;
+  chain_minv<N>(M, q, gbar, w.x, col);
+  if (taubar) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) col.out(taubar, k, w.x[k]);
+  }
+  rnea_vjp_seg<S>(M, q, qd, qdd, w, vjp_sink<S>(M, q, qbar, qdbar, nullptr, -1.f, col), col);
+}
+
 }  // namespace frax
