@@ -151,9 +151,8 @@ template <class T, class Img, bool VEL, class Rhs, class Out, class C, class P3>
 FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __restrict__ qd, const Rhs& rhs_at,
                      const Out& out_at, const C& col, P3& P) {
   constexpr int NB = T::NBMAX;
-  SV bv[NB], bA[NB], pAa[NB], sv[NB];
+  SV bv[NB], bA[NB], pAa[NB];
   AI IAa[NB];
-  float sc[NB], ss[NB];
   const SV ag = VEL ? gravity_acc(M.g) : szero();
   V3 gam = mk(0, 0, 0);  // root: E^T (-g)
   AI azero;
@@ -185,28 +184,29 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
       continue;
     }
     const int last = M.order[st + len - 1];
+    SV vtip = szero();
     if (kind != kActClose) {
       const int p = M.seg_parent[s];
       SV vv = (!VEL || p < 0) ? szero() : bv[p];
+      if (VEL) {
 #pragma unroll 1
-      for (int k = 0; k < len; ++k) {
-        const int i = M.order[st + k];
-        float sn, cs;
-        sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
-        if (VEL) {
+        for (int k = 0; k < len; ++k) {
+          const int i = M.order[st + k];
+          float sn, cs;
+          sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
           vv = mot_in(M.body[i], cs, sn, vv);
           vv.w.z += col.in(qd, iv_of<T>(i));
         }
-        sv[i] = vv;
-        sc[i] = cs;
-        ss[i] = sn;
       }
+      vtip = vv;
       if (kind == kActOpen) {
         bv[last] = vv;
         pAa[last] = szero();
         IAa[last] = azero;
         continue;
       }
+    } else {
+      vtip = bv[last];
     }
     // inward sweep: articulated inertias and bias forces
     AI Ia;
@@ -218,8 +218,9 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
         const RBI Ib = rbi_of(b);
-        const SV vk = sv[i];
-        const float ck = sc[i], sk = ss[i];
+        const SV vk = vtip;  // velocity of body i, stepped back from the segment's tip
+        float sk, ck;
+        sincosf(col.in(q, iq_of<T>(i)), &sk, &ck);
         AI IA = ai_of(Ib);
         SV pAt = szero();
         SV cb = szero();
@@ -253,6 +254,11 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         pa = pAt + ai_mul(Ia, cb) + (u * dinv) * U;
         ai_out(b, ck, sk, Ia);
         pa = frc_out(b, ck, sk, pa);
+        if (VEL && k > 0) {
+          SV vp = vk;
+          vp.w.z -= col.in(qd, iv_of<T>(i));
+          vtip = mot_out(b, ck, sk, vp);
+        }
       }
     }
     const int p = M.seg_parent[s];
