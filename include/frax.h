@@ -162,6 +162,25 @@ FRAX_API frax_status frax_aba_vjp(frax_model_t model, int64_t B, int64_t ld, con
                          const float* qd, const float* tau, const float* qdd, const float* gbar,
                          float* qbar, float* qdbar, float* taubar, void* stream);
 
+/*
+ * frax_ltdl_solve — x = M^-1 b from the packed factor M = L^T D L that
+ * frax_crba writes (the Cholesky-based solve the paper's Sec. VI footnote
+ * recommends over inverting M): L^T y = b, then L x = D^-1 y, walking only
+ * the dof-parent chains (L is zero outside the ancestor pattern).
+ *   LD [nv*(nv+1)/2][ld], b [nv][ld] in; x [nv][ld] out (must not alias b).
+ */
+FRAX_API frax_status frax_ltdl_solve(frax_model_t model, int64_t B, int64_t ld, const float* LD, const float* b,
+                                     float* x, void* stream);
+
+/*
+ * frax_ltdl_inverse — M^-1 (dense, symmetric, row-major nv x nv) from the
+ * same factor, one sparse solve per unit vector (the direct inversion of the
+ * mass matrix listed as future work in Sec. VI).
+ *   LD [nv*(nv+1)/2][ld] in; Minv [nv*nv][ld] out.
+ */
+FRAX_API frax_status frax_ltdl_inverse(frax_model_t model, int64_t B, int64_t ld, const float* LD, float* Minv,
+                                       void* stream);
+
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of dynamics queries for many robots. The
  * paper has no serving layer; this is the batched evaluation of Sec. III-B

@@ -204,4 +204,27 @@ frax_status frax_aba_vjp(frax_model_t model, int64_t B, int64_t ld, const float*
   return dispatch(model, frax::kOpAbaVjp, a, "frax_aba_vjp");
 }
 
+frax_status frax_ltdl_solve(frax_model_t model, int64_t B, int64_t ld, const float* LD, const float* b, float* x,
+                            void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_ltdl_solve"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(LD, "frax_ltdl_solve", "LD"));
+  FRAX_TRY(need(b, "frax_ltdl_solve", "b"));
+  FRAX_TRY(need(x, "frax_ltdl_solve", "x"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.in_LD = LD; a.qd = b; a.out0 = x; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpLtdlSolve, a, "frax_ltdl_solve");
+}
+
+frax_status frax_ltdl_inverse(frax_model_t model, int64_t B, int64_t ld, const float* LD, float* Minv,
+                              void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_ltdl_inverse"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(LD, "frax_ltdl_inverse", "LD"));
+  FRAX_TRY(need(Minv, "frax_ltdl_inverse", "Minv"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.in_LD = LD; a.out0 = Minv; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpLtdlInverse, a, "frax_ltdl_inverse");
+}
+
 }  // extern "C"

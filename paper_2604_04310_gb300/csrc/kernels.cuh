@@ -5,6 +5,7 @@
 #pragma once
 #include "dyn.cuh"
 #include "seg.cuh"
+#include "solve.cuh"
 #include "launch.h"
 
 namespace frax {
@@ -65,6 +66,20 @@ __global__ void __launch_bounds__(kBlock) k_aba_vjp(const __grid_constant__ Mode
   else aba_vjp_one<T>(M, q, qd, tau, qdd, gbar, qbar, qdbar, taubar, col);
 }
 
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_ltdl_solve(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                        int64_t ld, const float* LD, const float* rhs, float* x) {
+  FRAX_TID();
+  ltdl_solve_vec<T>(M, LD, rhs, x, col);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_ltdl_inverse(const __grid_constant__ ModelImage<T::NBMAX> M,
+                                                          int64_t B, int64_t ld, const float* LD, float* Minv) {
+  FRAX_TID();
+  ltdl_inverse<T>(M, LD, Minv, col);
+}
+
 // Trees (segment-unrolled): register use capped so that 6 (FK, RNEA, CRBA)
 // or 4 (ABA, which keeps 8 floats per body in thread-local memory between
 // its sweeps) 128-thread blocks fit on an SM.
@@ -120,6 +135,12 @@ cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a)
     case kOpAba:
       if constexpr (T::kSeg) k_aba_seg<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.out0);
       else k_aba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.out0);
+      break;
+    case kOpLtdlSolve:
+      k_ltdl_solve<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.in_LD, a.qd, a.out0);
+      break;
+    case kOpLtdlInverse:
+      k_ltdl_inverse<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.in_LD, a.out0);
       break;
     case kOpRneaVjp:
       k_rnea_vjp<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1,

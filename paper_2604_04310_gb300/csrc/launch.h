@@ -8,7 +8,7 @@
 
 namespace frax {
 
-enum Op { kOpFk = 0, kOpJac, kOpRnea, kOpCrba, kOpAba, kOpRneaVjp, kOpAbaVjp, kOpCount };
+enum Op { kOpFk = 0, kOpJac, kOpRnea, kOpCrba, kOpAba, kOpRneaVjp, kOpAbaVjp, kOpLtdlSolve, kOpLtdlInverse, kOpCount };
 
 struct FramesArg {
   int n;
@@ -22,6 +22,7 @@ struct OpArgs {
   const float* qdd = nullptr;
   const float* tau = nullptr;
   const float* gbar = nullptr;
+  const float* in_LD = nullptr;
   float* out0 = nullptr;  // pose / tau / M / qdd / qbar
   float* out1 = nullptr;  // J / LD / qdbar
   float* out2 = nullptr;  // qddbar / taubar

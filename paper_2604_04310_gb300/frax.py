@@ -216,6 +216,29 @@ def frax_aba_vjp(model: Model, q, qd, tau, qdd, gbar, qbar=None, qdbar=None, tau
     return qbar, qdbar, taubar
 
 
+def frax_ltdl_solve(model: Model, LD, b, x=None):
+    """x = M^-1 b from the packed factor frax_crba returns (want_LD=True)."""
+    nv = model.nv
+    _soa(LD, nv * (nv + 1) // 2, "LD")
+    B, ld = LD.shape[1], _ld(LD)
+    _soa(b, nv, "b", ld, B)
+    _soa(x, nv, "x", ld, B)
+    x = _out(nv, LD, ld, B) if x is None else x
+    _check(lib().frax_ltdl_solve(model.handle, B, ld, _p(LD), _p(b), _p(x), _stream(LD)))
+    return x
+
+
+def frax_ltdl_inverse(model: Model, LD, Minv=None):
+    """M^-1 (nv*nv, B) from the packed factor."""
+    nv = model.nv
+    _soa(LD, nv * (nv + 1) // 2, "LD")
+    B, ld = LD.shape[1], _ld(LD)
+    _soa(Minv, nv * nv, "Minv", ld, B)
+    Minv = _out(nv * nv, LD, ld, B) if Minv is None else Minv
+    _check(lib().frax_ltdl_inverse(model.handle, B, ld, _p(LD), _p(Minv), _stream(LD)))
+    return Minv
+
+
 # ------------------------------------------------------- allocation-free batch
 
 class BatchRequest(ctypes.Structure):

@@ -235,3 +235,22 @@ def test_autograd_functions(fxm):
     gq, gqd, gt = torch.autograd.grad(a, (q, qd, tau), g)
     aq, aqd, at = fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], a.detach(), g)
     assert torch.equal(gq, aq) and torch.equal(gqd, aqd) and torch.equal(gt, at)
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_ltdl_solve_and_inverse(fxm, name):
+    """Solves with the factor frax_crba returns: x = M^-1 b, M^-1 itself, and
+    M^-1 (tau - c - g) equal to the articulated-body forward dynamics."""
+    m, h = MODELS[name], fxm[name]
+    B = 300
+    s, d = states(m, B, 41)
+    _, LD = fx.frax_crba(h, d["q"], want_M=False, want_LD=True)
+    Mref = rbd.crba(m, s.q)
+    x = fx.frax_ltdl_solve(h, LD, d["tau"])
+    assert normwise(host(x), np.linalg.solve(Mref, s.tau[..., None])[..., 0]) < TOL_ABA_TREE
+    Minv = fx.frax_ltdl_inverse(h, LD)
+    assert normwise(host(Minv), np.linalg.inv(Mref).reshape(B, -1)) < TOL_ABA_TREE
+    bias = fx.frax_rnea(h, d["q"], d["qd"], None)
+    qdd_solve = fx.frax_ltdl_solve(h, LD, d["tau"] - bias)
+    qdd_aba = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+    assert normwise(host(qdd_solve), host(qdd_aba)) < TOL_ABA_TREE
