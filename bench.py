@@ -49,10 +49,12 @@ FP32_LANES_PER_SM = 128
 # plus the stored-state RNEA adjoint (4913).
 FLOPS = {
     "chain7": {"fk_jac": 903, "fk": 819, "rnea": 2000, "bias": 2000, "crba_ltdl": 2305, "crba": 2172,
-               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 7302},
+               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 7302, "osc": 10718},
     "humanoid": {"fk_jac": 5304, "fk": 3792, "rnea": 9028, "bias": 9022, "crba_ltdl": 16691, "crba": 12921,
-                 "aba": 25231, "rnea_vjp": 22034, "aba_vjp": 43301},
+                 "aba": 25231, "rnea_vjp": 22034, "aba_vjp": 43301, "osc": 31265},
 }
+# operational-space control task bodies (the last end frame of each model)
+OSC_TASK = {"chain7": 6, "humanoid": 29}
 
 
 def bytes_per_instance(op, nq, nv, nb, nframes):
@@ -64,6 +66,7 @@ def bytes_per_instance(op, nq, nv, nb, nframes):
         "crba_ltdl": f * (nq + nv * nv + nv * (nv + 1) // 2),
         "aba": f * (nq + 3 * nv),
         "rnea_vjp": f * (2 * nq + 5 * nv), "aba_vjp": f * (2 * nq + 5 * nv),
+        "osc": f * (nq + 2 * nv + 6),
     }[op]
 
 
@@ -158,7 +161,7 @@ class Step:
     """The whole hot path over one resident batch; output buffers are
     allocated once (torch), the kernels write into them."""
 
-    def __init__(self, fx, model, robot, dev, device, ops):
+    def __init__(self, fx, model, robot, dev, device, ops, task=None):
         import torch
         self.fx, self.m, self.d, self.ops = fx, model, dev, ops
         B = dev["q"].shape[1]
@@ -181,6 +184,7 @@ class Step:
                                                   qdbar=o["rqd"], qddbar=o["rqdd"]),
             "aba_vjp": lambda: fx_.frax_aba_vjp(m, d["q"], d["qd"], d["tau"], o["qdd"], d["gbar"], qbar=o["aq"],
                                                 qdbar=o["aqd"], taubar=o["at"]),
+            "osc": lambda: fx_.frax_osc(m, task, d["q"], d["qd"], d["xdd"], tau=o["tau"]),
         }
         self.launches = [(n, table[n]) for n in ops]
         self.B = B
@@ -460,6 +464,7 @@ def e2e_pipeline(fx, model, robot, host, dev, step, device, steps, world, dist):
 
 
 def frax_arm(args, rank, world, local_rank):
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -530,6 +535,26 @@ def frax_arm(args, rank, world, local_rank):
                     "per_op": roofline_of(hper, FLOPS["humanoid"], hB, peak, hbm, hrobot)}
         del hstep, hdev
 
+    # third workload: operational-space control (tau for a task-space
+    # acceleration of the last end frame), chain at 2^20, humanoid at 2^18
+    osc = None
+    if not args.no_osc:
+        osc = {}
+        for oname, orobot, oB in (("chain7", gen.chain7(0), B), ("humanoid", gen.humanoid(0), args.humanoid_batch)):
+            omodel = fx.Model.from_robot(orobot)
+            _, odev = make_inputs(orobot, oB, 3003 + rank, device)
+            xdd = np.random.default_rng(3004 + rank).uniform(-3, 3, (6, oB)).astype(np.float32)
+            odev["xdd"] = torch.from_numpy(xdd).to(device)
+            ostep = Step(fx, omodel, orobot, odev, device, ["osc"], task=OSC_TASK[oname])
+            osteps = max(5, args.steps // 5)
+            oms, oper, ol, _, _ = time_step(ostep, osteps, max(3, args.warmup), flush, world, dist)
+            launches += ol
+            osc[oname] = {"task_body": OSC_TASK[oname], "batch": oB, "steps": osteps,
+                          "per_op": roofline_of(oper, FLOPS[oname], oB, peak, hbm, orobot)["osc"]}
+            del ostep, odev
+        osc["workload"] = ("operational-space control, tau = J^T Lambda (xdd - Jdot qd) + c + g for the last "
+                           "end frame: 7-DoF chain 2^20 and humanoid 2^18 instances, xdd uniform in [-3, 3]")
+
     serve = None
     if rank == 0 and not args.no_serve:
         serve = serve_stream(fx, args.serve_seconds)
@@ -547,7 +572,7 @@ def frax_arm(args, rank, world, local_rank):
                            "global_batch": B * world, "parallelism": f"replicas x{world}",
                            "l2": "256 MB buffer written between steps (L2 flush)"},
                 "clocks": clk, "gpu_launches": launches, "wall_s": wall, "per_op": per_op, "roofline": roofline,
-                "e2e": e2e, "humanoid": humanoid, "cpu_baseline": cpu, "serving": serve}
+                "e2e": e2e, "humanoid": humanoid, "osc": osc, "cpu_baseline": cpu, "serving": serve}
         print(json.dumps(line))
 
 
@@ -562,6 +587,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-humanoid", action="store_true")
+    ap.add_argument("--no-osc", action="store_true")
     ap.add_argument("--humanoid-batch", type=int, default=1 << 18)
     ap.add_argument("--count-flops", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -35,10 +35,11 @@ inline CF& operator-=(CF& a, CF b) { g.add++; a.v -= b.v; return a; }
 inline CF& operator*=(CF& a, CF b) { g.mul++; a.v *= b.v; return a; }
 inline CF fmaf(CF a, CF b, CF c) { g.fma++; return CF(std::fma(a.v, b.v, c.v)); }
 inline CF sqrtf(CF a) { g.sfu++; return CF(std::sqrt(a.v)); }
+inline CF rsqrtf(CF a) { g.sfu++; return CF(1.f / std::sqrt(a.v)); }
 inline void sincosf(CF x, CF* s, CF* c) { g.sfu++; s->v = std::sin(x.v); c->v = std::cos(x.v); }
 
 #define float CF
-#include "paper_2604_04310_gb300/csrc/seg.cuh"
+#include "paper_2604_04310_gb300/csrc/osc.cuh"
 #undef float
 
 using namespace frax;
@@ -79,6 +80,9 @@ void count(const Img& M, int nf, const int* frames) {
   if constexpr (T::kSeg) {
     rnea_vjp_seg_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp");
     aba_vjp_seg_one<T>(M, q.data(), qd.data(), tau.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp");
+    std::vector<CF> lam(36 + 8);
+    osc_seg<T>(M, frames[nf - 1], q.data(), qd.data(), qdd.data(), o6.data(), nullptr, col); rep("osc");
+    osc_seg<T>(M, frames[nf - 1], q.data(), qd.data(), qdd.data(), o6.data(), lam.data(), col); rep("osc_lambda");
   }
 }
 
@@ -100,6 +104,9 @@ void count_chain_vjp(const Img& M) {
   aba_vjp_chain_one<7>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp_chain");
   std::vector<CF> w(8);
   chain_minv<7>(M, q.data(), gb.data(), w.data(), col); rep("minv_factor");
+  std::vector<CF> lam(36 + 8);
+  osc_seg<T>(M, 6, q.data(), qd.data(), qdd.data(), o6.data(), nullptr, col); rep("osc");
+  osc_seg<T>(M, 6, q.data(), qd.data(), qdd.data(), o6.data(), lam.data(), col); rep("osc_lambda");
 }
 
 int main(int argc, char** argv) {

@@ -181,6 +181,25 @@ FRAX_API frax_status frax_ltdl_solve(frax_model_t model, int64_t B, int64_t ld, 
 FRAX_API frax_status frax_ltdl_inverse(frax_model_t model, int64_t B, int64_t ld, const float* LD, float* Minv,
                                        void* stream);
 
+/*
+ * frax_osc — operational-space control of one task body (the inverse-dynamics
+ * controller of Sec. V, Table II, built from M, J, c and g):
+ *   tau = J^T Lambda (xdd_des - Jdot qd) + c + g,   Lambda = (J M^-1 J^T)^-1
+ * with J the world-aligned Jacobian of the task body's origin (the rows of
+ * frax_jacobian), without a null-space term. One fused kernel: Lambda^-1
+ * from the articulated-body inertias along the path to the task body, a 6x6
+ * solve, and one RNEA pass that adds J^T f; M is never formed.
+ *   task_body  0..n_bodies-1; at least 6 dofs must move it, else FRAX_EINVAL
+ *              (the 6-D task inertia would be singular)
+ *   q [nq][ld], qd [nv][ld], xdd_des [6][ld] ([omega_dot; p_ddot] of the
+ *   task body's origin, world coordinates) in; tau [nv][ld] out;
+ *   Lambda [36][ld] out, row-major world-aligned, or NULL to skip it.
+ * Near a kinematic singularity Lambda grows without bound; no per-instance
+ * check is made.
+ */
+FRAX_API frax_status frax_osc(frax_model_t model, int task_body, int64_t B, int64_t ld, const float* q,
+                              const float* qd, const float* xdd_des, float* tau, float* Lambda, void* stream);
+
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of dynamics queries for many robots. The
  * paper has no serving layer; this is the batched evaluation of Sec. III-B

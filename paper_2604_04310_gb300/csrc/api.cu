@@ -227,4 +227,26 @@ frax_status frax_ltdl_inverse(frax_model_t model, int64_t B, int64_t ld, const f
   return dispatch(model, frax::kOpLtdlInverse, a, "frax_ltdl_inverse");
 }
 
+frax_status frax_osc(frax_model_t model, int task_body, int64_t B, int64_t ld, const float* q, const float* qd,
+                     const float* xdd_des, float* tau, float* Lambda, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_osc"));
+  const frax::HostModel& m = model->m;
+  if (task_body < 0 || task_body >= m.nb)
+    return fail(FRAX_EINVAL, "frax_osc: task_body out of range");
+  int path_dofs = m.free_root ? 5 : 0;
+  for (uint64_t x = m.anc[task_body]; x; x &= x - 1) ++path_dofs;
+  if (path_dofs < 6)
+    return fail(FRAX_EINVAL, "frax_osc: fewer than 6 dofs move the task body; its 6-D task inertia is singular");
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_osc", "q"));
+  FRAX_TRY(need(qd, "frax_osc", "qd"));
+  FRAX_TRY(need(xdd_des, "frax_osc", "xdd_des"));
+  FRAX_TRY(need(tau, "frax_osc", "tau"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.in_xdd = xdd_des; a.out0 = tau; a.out1 = Lambda;
+  a.frames.n = 1; a.frames.body[0] = task_body;
+  a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpOsc, a, "frax_osc");
+}
+
 }  // extern "C"

@@ -23,7 +23,7 @@ cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
                                                     a.out2);
     return cudaGetLastError();
   }
-  if (op == kOpRneaVjp) {
+  if (op == kOpRneaVjp || op == kOpOsc) {
     // the adjoints step the forward state back through the joints instead
     // of keeping it per body: far fewer live registers than the unrolled form
     ModelImage<8> img8;

@@ -6,6 +6,7 @@
 #include "dyn.cuh"
 #include "seg.cuh"
 #include "solve.cuh"
+#include "osc.cuh"
 #include "launch.h"
 
 namespace frax {
@@ -114,6 +115,14 @@ __global__ void __launch_bounds__(kBlock, 4) k_aba_seg(const __grid_constant__ M
 }
 
 template <class T>
+__global__ void __launch_bounds__(kBlock, 4) k_osc_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                        int64_t ld, int task, const float* q, const float* qd,
+                                                        const float* xdd, float* tau, float* Lam) {
+  FRAX_TID();
+  osc_seg<T>(M, task, q, qd, xdd, tau, Lam, col);
+}
+
+template <class T>
 cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a) {
   const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock)), block(kBlock);
   Frames fr{a.frames.n, {0}};
@@ -149,6 +158,13 @@ cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a)
     case kOpAbaVjp:
       k_aba_vjp<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.qdd, a.gbar, a.out0,
                                                  a.out1, a.out2);
+      break;
+    case kOpOsc:
+      if constexpr (T::kSeg)
+        k_osc_seg<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.frames.body[0], a.q, a.qd, a.in_xdd, a.out0,
+                                                   a.out1);
+      else
+        return cudaErrorInvalidValue;
       break;
     default:
       return cudaErrorInvalidValue;

@@ -8,7 +8,8 @@
 
 namespace frax {
 
-enum Op { kOpFk = 0, kOpJac, kOpRnea, kOpCrba, kOpAba, kOpRneaVjp, kOpAbaVjp, kOpLtdlSolve, kOpLtdlInverse, kOpCount };
+enum Op { kOpFk = 0, kOpJac, kOpRnea, kOpCrba, kOpAba, kOpRneaVjp, kOpAbaVjp, kOpLtdlSolve, kOpLtdlInverse,
+          kOpOsc, kOpCount };
 
 struct FramesArg {
   int n;
@@ -23,10 +24,11 @@ struct OpArgs {
   const float* tau = nullptr;
   const float* gbar = nullptr;
   const float* in_LD = nullptr;
+  const float* in_xdd = nullptr;  // task accelerations (kOpOsc)
   float* out0 = nullptr;  // pose / tau / M / qdd / qbar
-  float* out1 = nullptr;  // J / LD / qdbar
+  float* out1 = nullptr;  // J / LD / qdbar / Lambda
   float* out2 = nullptr;  // qddbar / taubar
-  FramesArg frames{0, {0}};
+  FramesArg frames{0, {0}};  // kOpOsc: body[0] is the task body
   cudaStream_t stream = nullptr;
 };
 

@@ -34,9 +34,12 @@ struct SegTopo {
 FD SV ez_velprod(const SV& v, float qd) { return qd * SV{mk(v.w.y, -v.w.x, 0.f), mk(v.v.y, -v.v.x, 0.f)}; }
 
 // ====================================================================== RNEA
-template <class T, class Img, class C>
+// With EXT, the spatial force fext (body coordinates) is added to the net
+// force of body ext_body, so tau gains J_ext^T fext.
+template <class T, class Img, class C, bool EXT = false>
 FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
-                 const float* __restrict__ qdd, float* __restrict__ tau, const C& col) {
+                 const float* __restrict__ qdd, float* __restrict__ tau, const C& col, int ext_body = -1,
+                 SV fext = SV{}) {
   constexpr int NB = T::NBMAX;
   SV bv[NB], ba[NB], Fa[NB], sf[NB];
   float sc[NB], ss[NB];
@@ -53,7 +56,10 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
         SV a0 = SV{mk(0, 0, 0), rotT(P.E, ag.v)};
         if (qdd) a0 = a0 + load6(qdd, 0, col);
         const RBI I = rbi_of(M.body[0]);
-        const SV f0 = rbi_mul(I, a0) + crf(v0, rbi_mul(I, v0));
+        SV f0 = rbi_mul(I, a0) + crf(v0, rbi_mul(I, v0));
+        if constexpr (EXT) {
+          if (ext_body == 0) f0 = f0 + fext;
+        }
         if (kind == kActLeaf) {
           store6(tau, 0, col, f0);
         } else {
@@ -88,6 +94,9 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
           a = a + ez_velprod(v, qdi);
           const RBI I = rbi_of(b);
           f[k] = rbi_mul(I, a) + crf(v, rbi_mul(I, v));
+          if constexpr (EXT) {
+            if (i == ext_body) f[k] = f[k] + fext;
+          }
         }
       }
       if (kind == kActOpen) {

@@ -240,14 +240,9 @@ FD void ai_rank1_sub(AI& I, const SV& u, float k) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) I.B[3 * r + c] = fmaf(-k * a[r], a[3 + c], I.B[3 * r + c]);
 }
-// X^T I X for the revolute joint transform: rotate all blocks by
-// E = R Rot_z(q), then shift by p: C' = C, B' = B + P C, A' = A - (Y P + (Y P)^T)
-// with P = [p]x and Y = B + P C / 2.
-FD void ai_out(const BodyImage& b, float c, float s, AI& I) {
-  sym_rotz(c, s, I.A); sym_rot(b.R, I.A);
-  sym_rotz(c, s, I.C); sym_rot(b.R, I.C);
-  gen_rotz(c, s, I.B); gen_rot(b.R, I.B);
-  V3 p = mk(b.p[0], b.p[1], b.p[2]);
+// Shift of a symmetric force-space tensor to a frame whose origin sits at
+// -p: C' = C, B' = B + P C, A' = A - (Y P + (Y P)^T), P = [p]x, Y = B + P C / 2.
+FD void ai_shift(const V3& p, AI& I) {
   float Cf[9] = {I.C[0], I.C[3], I.C[4], I.C[3], I.C[1], I.C[5], I.C[4], I.C[5], I.C[2]};
   float W[9];  // P C: column j = p x C[:, j]
 #pragma unroll
@@ -266,6 +261,23 @@ FD void ai_out(const BodyImage& b, float c, float s, AI& I) {
   }
   I.A[0] -= 2.f * Z[0]; I.A[1] -= 2.f * Z[4]; I.A[2] -= 2.f * Z[8];
   I.A[3] -= Z[1] + Z[3]; I.A[4] -= Z[2] + Z[6]; I.A[5] -= Z[5] + Z[7];
+}
+// X^T I X for the revolute joint transform (child' -> parent'): rotate all
+// blocks by E = R Rot_z(q), then shift by the joint origin p.
+FD void ai_out(const BodyImage& b, float c, float s, AI& I) {
+  sym_rotz(c, s, I.A); sym_rot(b.R, I.A);
+  sym_rotz(c, s, I.C); sym_rot(b.R, I.C);
+  gen_rotz(c, s, I.B); gen_rot(b.R, I.B);
+  ai_shift(mk(b.p[0], b.p[1], b.p[2]), I);
+}
+// The inverse congruence, parent' -> child': shift by -p, then rotate all
+// blocks by E^T.
+FD void ai_in(const BodyImage& b, float c, float s, AI& I) {
+  ai_shift(mk(-b.p[0], -b.p[1], -b.p[2]), I);
+  const float Rt[9] = {b.R[0], b.R[3], b.R[6], b.R[1], b.R[4], b.R[7], b.R[2], b.R[5], b.R[8]};
+  sym_rot(Rt, I.A); sym_rotz(c, -s, I.A);
+  sym_rot(Rt, I.C); sym_rotz(c, -s, I.C);
+  gen_rot(Rt, I.B); gen_rotz(c, -s, I.B);
 }
 
 }  // namespace frax

@@ -239,6 +239,18 @@ def frax_ltdl_inverse(model: Model, LD, Minv=None):
     return Minv
 
 
+def frax_osc(model: Model, task_body: int, q, qd, xdd_des, tau=None, Lam=None, want_lambda=False):
+    """Operational-space control of one task body: returns (tau (nv, B),
+    Lambda (36, B) row-major world-aligned, or None)."""
+    B, ld = _prep(model, q, qd=(qd, model.nv), xdd_des=(xdd_des, 6), tau=(tau, model.nv), Lam=(Lam, 36))
+    tau = _out(model.nv, q, ld, B) if tau is None else tau
+    if Lam is None and want_lambda:
+        Lam = _out(36, q, ld, B)
+    _check(lib().frax_osc(model.handle, int(task_body), B, ld, _p(q), _p(qd), _p(xdd_des), _p(tau), _p(Lam),
+                          _stream(q)))
+    return tau, Lam
+
+
 # ------------------------------------------------------- allocation-free batch
 
 class BatchRequest(ctypes.Structure):

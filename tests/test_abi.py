@@ -100,3 +100,21 @@ def test_batch_argument_checks_before_any_launch():
                            ctypes.c_void_p(16), null) == 1
     assert L.frax_jacobian(m.handle, 16, 16, ctypes.c_void_p(16), 9, frames.ctypes.data_as(_lib.c_i32), null,
                            ctypes.c_void_p(16), null) == 1
+
+
+def test_osc_argument_checks_before_any_launch():
+    """frax_osc rejects a task body out of range, and one moved by fewer than
+    six dofs (its 6-D task inertia is singular), before any launch."""
+    L = _lib.load()
+    null = ctypes.c_void_p(0)
+    p = ctypes.c_void_p(16)
+    ch = fx.Model.from_robot(gen.chain7(0))
+    assert L.frax_osc(ch.handle, 7, 16, 16, p, p, p, p, null, null) == 1
+    assert b"task_body" in L.frax_last_error()
+    assert L.frax_osc(ch.handle, 4, 16, 16, p, p, p, p, null, null) == 1  # 5 dofs above body 4
+    assert b"fewer than 6 dofs" in L.frax_last_error()
+    assert L.frax_osc(ch.handle, 6, 0, 0, null, null, null, null, null, null) == 0
+    assert L.frax_osc(ch.handle, 6, 16, 16, p, p, null, p, null, null) == 1
+    assert b"xdd_des is NULL" in L.frax_last_error()
+    hu = fx.Model.from_robot(gen.humanoid(0))
+    assert L.frax_osc(hu.handle, 0, 0, 0, null, null, null, null, null, null) == 0  # free root: 6 dofs
