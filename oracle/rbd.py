@@ -161,15 +161,30 @@ def jacobian(model, q, frames):
 
 # ------------------------------------------------------------------ dynamics
 
-def rnea(model, q, qd, qdd, gravity=True):
-    """Inverse dynamics tau = M qdd + c + g (Eq. 1, no external force) by the
-    recursive Newton-Euler algorithm: outward velocity/acceleration sweep,
-    body forces f_i = I_i a_i + v_i x* I_i v_i, inward force sweep,
-    tau_i = S_i^T f_i."""
+def external_body_forces(model, q, fext):
+    """Algorithm 1's external forces ^0F_ext,i, given as (B, n, 6) spatial
+    forces on the bodies in root-frame Pluecker coordinates [moment about the
+    root origin; force], expressed in each body's frame:
+    ^iF = (^iX_0)^* ^0F = [R_i^T (n - p_i x f); R_i^T f]."""
+    R, p = fk(model, q)
+    n_, f_ = fext[..., :3], fext[..., 3:]
+    Rt = np.swapaxes(R, -1, -2)
+    nb = np.einsum("bnij,bnj->bni", Rt, n_ - np.cross(p, f_))
+    fb = np.einsum("bnij,bnj->bni", Rt, f_)
+    return np.concatenate([nb, fb], -1)
+
+
+def rnea(model, q, qd, qdd, gravity=True, fext=None):
+    """Inverse dynamics tau = M qdd + c + g (Eq. 1) by the recursive
+    Newton-Euler algorithm: outward velocity/acceleration sweep, body forces
+    f_i = I_i a_i + v_i x* I_i v_i - F_ext,i (Algorithm 1 subtracts the
+    external force; fext as in external_body_forces, None for none), inward
+    force sweep, tau_i = S_i^T f_i."""
     lay = Layout(model)
-    dt = np.result_type(q, qd, qdd)
+    dt = np.result_type(q, qd, qdd) if fext is None else np.result_type(q, qd, qdd, fext)
     B = q.shape[0]
     X = joint_transforms(model, q)
+    fb = None if fext is None else external_body_forces(model, q, fext)
     a0 = base_acceleration(model, dt) if gravity else np.zeros(6, dt)
     v, a, f = [None] * lay.n, [None] * lay.n, [None] * lay.n
     for i in range(lay.n):
@@ -182,6 +197,8 @@ def rnea(model, q, qd, qdd, gravity=True):
         a[i] = matvec(X[i], ap) + matvec(S, qdd[:, lay.vslice(i)]) + matvec(crm(v[i]), vJ)
         I = body_inertia(model, i)
         f[i] = matvec(I, a[i]) + matvec(crf(v[i]), matvec(I, v[i]))
+        if fb is not None:
+            f[i] = f[i] - fb[:, i]
     tau = np.zeros((B, lay.nv), dt)
     for i in reversed(range(lay.n)):
         S = motion_subspace(model, i)
@@ -247,22 +264,25 @@ def pack_ltdl(L, D):
     return np.stack(out, -1)
 
 
-def aba(model, q, qd, tau):
-    """Forward dynamics as Eq. 2 itself (f = 0):
-    qdd = M(q)^-1 (tau - c(q, qd) - g(q)), with c + g = RNEA(q, qd, 0)."""
-    bias = rnea(model, q, qd, np.zeros_like(tau))
+def aba(model, q, qd, tau, fext=None):
+    """Forward dynamics as Eq. 2 itself:
+    qdd = M(q)^-1 (tau - c(q, qd) - g(q) + sum_i J_i^T F_ext,i), the bias
+    term being RNEA(q, qd, 0) with the same external forces."""
+    bias = rnea(model, q, qd, np.zeros_like(tau), fext=fext)
     M = crba(model, q)
     return np.linalg.solve(M, (tau - bias)[..., None])[..., 0]
 
 
-def aba_recursive(model, q, qd, tau, gravity=True):
+def aba_recursive(model, q, qd, tau, gravity=True, fext=None):
     """The articulated-body algorithm (Featherstone): velocity sweep,
-    articulated inertias I^A / bias forces p^A inward, accelerations outward.
-    A second formulation of ``aba`` used by the tests."""
+    articulated inertias I^A / bias forces p^A inward (p^A_i = v_i x* I_i v_i
+    - F_ext,i), accelerations outward. A second formulation of ``aba`` used
+    by the tests."""
     lay = Layout(model)
     dt = np.result_type(q, qd, tau)
     B = q.shape[0]
     X = joint_transforms(model, q)
+    fb = None if fext is None else external_body_forces(model, q, fext)
     a0 = base_acceleration(model, dt) if gravity else np.zeros(6, dt)
     v, c, IA, pA = [None] * lay.n, [None] * lay.n, [None] * lay.n, [None] * lay.n
     for i in range(lay.n):
@@ -275,6 +295,8 @@ def aba_recursive(model, q, qd, tau, gravity=True):
         I = body_inertia(model, i)
         IA[i] = np.broadcast_to(I, (B, 6, 6)).astype(dt)
         pA[i] = matvec(crf(v[i]), matvec(I, v[i]))
+        if fb is not None:
+            pA[i] = pA[i] - fb[:, i]
     Us, Dinv, u = [None] * lay.n, [None] * lay.n, [None] * lay.n
     for i in reversed(range(lay.n)):
         S = motion_subspace(model, i)
