@@ -49,9 +49,11 @@ FP32_LANES_PER_SM = 128
 # plus the stored-state RNEA adjoint (4913).
 FLOPS = {
     "chain7": {"fk_jac": 903, "fk": 819, "rnea": 2000, "bias": 2000, "crba_ltdl": 2305, "crba": 2172,
-               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 7302, "osc": 10718},
+               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 7302, "osc": 10718, "rnea_ext": 2710,
+               "aba_ext": 6012},
     "humanoid": {"fk_jac": 5304, "fk": 3792, "rnea": 9028, "bias": 9022, "crba_ltdl": 16691, "crba": 12921,
-                 "aba": 25231, "rnea_vjp": 22034, "aba_vjp": 43301, "osc": 31265},
+                 "aba": 25231, "rnea_vjp": 22034, "aba_vjp": 43301, "osc": 31265, "rnea_ext": 12236,
+                 "aba_ext": 28439},
 }
 # operational-space control task bodies (the last end frame of each model)
 OSC_TASK = {"chain7": 6, "humanoid": 29}
@@ -67,6 +69,7 @@ def bytes_per_instance(op, nq, nv, nb, nframes):
         "aba": f * (nq + 3 * nv),
         "rnea_vjp": f * (2 * nq + 5 * nv), "aba_vjp": f * (2 * nq + 5 * nv),
         "osc": f * (nq + 2 * nv + 6),
+        "rnea_ext": f * (nq + 3 * nv + 6 * nb), "aba_ext": f * (nq + 3 * nv + 6 * nb),
     }[op]
 
 
@@ -185,6 +188,8 @@ class Step:
             "aba_vjp": lambda: fx_.frax_aba_vjp(m, d["q"], d["qd"], d["tau"], o["qdd"], d["gbar"], qbar=o["aq"],
                                                 qdbar=o["aqd"], taubar=o["at"]),
             "osc": lambda: fx_.frax_osc(m, task, d["q"], d["qd"], d["xdd"], tau=o["tau"]),
+            "rnea_ext": lambda: fx_.frax_rnea_ext(m, d["q"], d["qd"], d["qdd"], d["fext"], tau=o["tau"]),
+            "aba_ext": lambda: fx_.frax_aba_ext(m, d["q"], d["qd"], d["tau"], d["fext"], qdd=o["qdd"]),
         }
         self.launches = [(n, table[n]) for n in ops]
         self.B = B
@@ -535,25 +540,28 @@ def frax_arm(args, rank, world, local_rank):
                     "per_op": roofline_of(hper, FLOPS["humanoid"], hB, peak, hbm, hrobot)}
         del hstep, hdev
 
-    # third workload: operational-space control (tau for a task-space
-    # acceleration of the last end frame), chain at 2^20, humanoid at 2^18
-    osc = None
-    if not args.no_osc:
-        osc = {}
+    # further rows on the same two robots: operational-space control of the
+    # last end frame, and RNEA / ABA with external forces on every body;
+    # chain at 2^20, humanoid at 2^18
+    nxt = None
+    if not args.no_next:
+        nxt = {"workload": "operational-space control tau = J^T Lambda (xdd - Jdot qd) + c + g for the last end "
+                           "frame (xdd uniform in [-3, 3]); RNEA and ABA with standard-normal external spatial "
+                           "forces on every body; 7-DoF chain 2^20, humanoid 2^18 instances"}
         for oname, orobot, oB in (("chain7", gen.chain7(0), B), ("humanoid", gen.humanoid(0), args.humanoid_batch)):
             omodel = fx.Model.from_robot(orobot)
             _, odev = make_inputs(orobot, oB, 3003 + rank, device)
-            xdd = np.random.default_rng(3004 + rank).uniform(-3, 3, (6, oB)).astype(np.float32)
-            odev["xdd"] = torch.from_numpy(xdd).to(device)
-            ostep = Step(fx, omodel, orobot, odev, device, ["osc"], task=OSC_TASK[oname])
+            rng = np.random.default_rng(3004 + rank)
+            odev["xdd"] = torch.from_numpy(rng.uniform(-3, 3, (6, oB)).astype(np.float32)).to(device)
+            odev["fext"] = torch.from_numpy(rng.standard_normal((6 * orobot.n_bodies, oB), np.float32)).to(device)
+            oops = ["osc", "rnea_ext", "aba_ext"]
+            ostep = Step(fx, omodel, orobot, odev, device, oops, task=OSC_TASK[oname])
             osteps = max(5, args.steps // 5)
             oms, oper, ol, _, _ = time_step(ostep, osteps, max(3, args.warmup), flush, world, dist)
             launches += ol
-            osc[oname] = {"task_body": OSC_TASK[oname], "batch": oB, "steps": osteps,
-                          "per_op": roofline_of(oper, FLOPS[oname], oB, peak, hbm, orobot)["osc"]}
+            nxt[oname] = {"osc_task_body": OSC_TASK[oname], "batch": oB, "steps": osteps,
+                          "per_op": roofline_of(oper, FLOPS[oname], oB, peak, hbm, orobot)}
             del ostep, odev
-        osc["workload"] = ("operational-space control, tau = J^T Lambda (xdd - Jdot qd) + c + g for the last "
-                           "end frame: 7-DoF chain 2^20 and humanoid 2^18 instances, xdd uniform in [-3, 3]")
 
     serve = None
     if rank == 0 and not args.no_serve:
@@ -572,7 +580,7 @@ def frax_arm(args, rank, world, local_rank):
                            "global_batch": B * world, "parallelism": f"replicas x{world}",
                            "l2": "256 MB buffer written between steps (L2 flush)"},
                 "clocks": clk, "gpu_launches": launches, "wall_s": wall, "per_op": per_op, "roofline": roofline,
-                "e2e": e2e, "humanoid": humanoid, "osc": osc, "cpu_baseline": cpu, "serving": serve}
+                "e2e": e2e, "humanoid": humanoid, "next_rows": nxt, "cpu_baseline": cpu, "serving": serve}
         print(json.dumps(line))
 
 
@@ -587,7 +595,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-humanoid", action="store_true")
-    ap.add_argument("--no-osc", action="store_true")
+    ap.add_argument("--no-next", action="store_true")
     ap.add_argument("--humanoid-batch", type=int, default=1 << 18)
     ap.add_argument("--count-flops", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -40,6 +40,7 @@ inline void sincosf(CF x, CF* s, CF* c) { g.sfu++; s->v = std::sin(x.v); c->v = 
 
 #define float CF
 #include "paper_2604_04310_gb300/csrc/osc.cuh"
+#include "paper_2604_04310_gb300/csrc/ext.cuh"
 #undef float
 
 using namespace frax;
@@ -76,6 +77,11 @@ void count(const Img& M, int nf, const int* frames) {
     crba_one<T>(M, q.data(), o3.data(), o4.data(), col); rep("crba_ltdl");
     crba_one<T>(M, q.data(), o3.data(), nullptr, col); rep("crba");
     aba_one<T>(M, q.data(), qd.data(), tau.data(), o6.data(), col); rep("aba");
+  }
+  {
+    std::vector<CF> fe(6 * nb + 8, CF(0.4f)), o8(nv + 8);
+    LocalVec<T> w;
+    ext_tau<T>(M, q.data(), fe.data(), col, OutToLocal<T>{&w}); rep("ext_tau");
   }
   if constexpr (T::kSeg) {
     rnea_vjp_seg_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp");

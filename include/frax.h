@@ -182,6 +182,25 @@ FRAX_API frax_status frax_ltdl_inverse(frax_model_t model, int64_t B, int64_t ld
                                        void* stream);
 
 /*
+ * frax_rnea_ext / frax_aba_ext — inverse and forward dynamics with external
+ * forces on the bodies (Eq. 1 and 2 with J^T f; Algorithm 1's ^0F_ext):
+ *   tau = M qdd + c + g - sum_i J_i^T F_ext,i
+ *   qdd = M^-1 (tau - c - g + sum_i J_i^T F_ext,i)
+ * fext [6*n_bodies][ld] in: entry (i, r) at 6*i + r, the spatial force that
+ * the environment applies to body i in root-frame Pluecker coordinates,
+ * [moment about the root (world) origin; force], as Algorithm 1 takes it and
+ * subtracts it. A point force f at world point c on body i is [c x f; f];
+ * rows of bodies without forces must be zero. Eq. 1's f is the force the
+ * robot applies, -F_ext.
+ *   frax_rnea_ext: q, qd, qdd (NULL: zero), fext in; tau [nv][ld] out.
+ *   frax_aba_ext:  q, qd, tau, fext in; qdd [nv][ld] out.
+ */
+FRAX_API frax_status frax_rnea_ext(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                                   const float* qdd, const float* fext, float* tau, void* stream);
+FRAX_API frax_status frax_aba_ext(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                                  const float* tau, const float* fext, float* qdd, void* stream);
+
+/*
  * frax_osc — operational-space control of one task body (the inverse-dynamics
  * controller of Sec. V, Table II, built from M, J, c and g):
  *   tau = J^T Lambda (xdd_des - Jdot qd) + c + g,   Lambda = (J M^-1 J^T)^-1

@@ -227,6 +227,35 @@ frax_status frax_ltdl_inverse(frax_model_t model, int64_t B, int64_t ld, const f
   return dispatch(model, frax::kOpLtdlInverse, a, "frax_ltdl_inverse");
 }
 
+frax_status frax_rnea_ext(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                          const float* qdd, const float* fext, float* tau, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_rnea_ext"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_rnea_ext", "q"));
+  FRAX_TRY(need(qd, "frax_rnea_ext", "qd"));
+  FRAX_TRY(need(fext, "frax_rnea_ext", "fext"));
+  FRAX_TRY(need(tau, "frax_rnea_ext", "tau"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.qdd = qdd; a.in_fext = fext; a.out0 = tau;
+  a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpRneaExt, a, "frax_rnea_ext");
+}
+
+frax_status frax_aba_ext(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                         const float* tau, const float* fext, float* qdd, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_aba_ext"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_aba_ext", "q"));
+  FRAX_TRY(need(qd, "frax_aba_ext", "qd"));
+  FRAX_TRY(need(tau, "frax_aba_ext", "tau"));
+  FRAX_TRY(need(fext, "frax_aba_ext", "fext"));
+  FRAX_TRY(need(qdd, "frax_aba_ext", "qdd"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.tau = tau; a.in_fext = fext; a.out0 = qdd;
+  a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpAbaExt, a, "frax_aba_ext");
+}
+
 frax_status frax_osc(frax_model_t model, int task_body, int64_t B, int64_t ld, const float* q, const float* qd,
                      const float* xdd_des, float* tau, float* Lambda, void* stream) {
   FRAX_TRY(check_batch(model, B, ld, "frax_osc"));

@@ -7,6 +7,7 @@
 #include "seg.cuh"
 #include "solve.cuh"
 #include "osc.cuh"
+#include "ext.cuh"
 #include "launch.h"
 
 namespace frax {
@@ -122,6 +123,33 @@ __global__ void __launch_bounds__(kBlock, 4) k_osc_seg(const __grid_constant__ M
   osc_seg<T>(M, task, q, qd, xdd, tau, Lam, col);
 }
 
+// External forces: the plain kernel's result, then tau_ext from one more
+// sweep (subtracted from RNEA's output, added to ABA's right-hand side).
+template <class T>
+__global__ void __launch_bounds__(kBlock, 6) k_rnea_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                         int64_t ld, const float* q, const float* qd,
+                                                         const float* qdd, const float* fext, float* tau) {
+  FRAX_TID();
+  if constexpr (T::kSeg) rnea_seg<T>(M, q, qd, qdd, tau, col);
+  else rnea_one<T>(M, q, qd, qdd, tau, col);
+  ext_tau<T>(M, q, fext, col, SubFromGlobal<T>{tau, ColT<false>{ld, b}});
+}
+template <class T>
+__global__ void __launch_bounds__(kBlock, 4) k_aba_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                        int64_t ld, const float* q, const float* qd,
+                                                        const float* tau, const float* fext, float* qdd) {
+  FRAX_TID();
+  LocalVec<T> w;
+  ext_tau<T>(M, q, fext, col, OutToLocal<T>{&w});
+  const RhsPlusLocal<T, Col> rhs{tau, col, &w};
+  if constexpr (T::kSeg) {
+    P3Local<T::NBMAX> P;
+    aba_seg_core<T, ModelImage<T::NBMAX>, true>(M, q, qd, rhs, OutToGlobal<T, Col>{qdd, col}, col, P);
+  } else {
+    aba_core<T, ModelImage<T::NBMAX>, true>(M, q, qd, rhs, OutToGlobal<T, Col>{qdd, col}, col);
+  }
+}
+
 template <class T>
 cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a) {
   const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock)), block(kBlock);
@@ -158,6 +186,12 @@ cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a)
     case kOpAbaVjp:
       k_aba_vjp<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.qdd, a.gbar, a.out0,
                                                  a.out1, a.out2);
+      break;
+    case kOpRneaExt:
+      k_rnea_ext<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.in_fext, a.out0);
+      break;
+    case kOpAbaExt:
+      k_aba_ext<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.in_fext, a.out0);
       break;
     case kOpOsc:
       if constexpr (T::kSeg)

@@ -9,7 +9,7 @@
 namespace frax {
 
 enum Op { kOpFk = 0, kOpJac, kOpRnea, kOpCrba, kOpAba, kOpRneaVjp, kOpAbaVjp, kOpLtdlSolve, kOpLtdlInverse,
-          kOpOsc, kOpCount };
+          kOpOsc, kOpRneaExt, kOpAbaExt, kOpCount };
 
 struct FramesArg {
   int n;
@@ -25,6 +25,7 @@ struct OpArgs {
   const float* gbar = nullptr;
   const float* in_LD = nullptr;
   const float* in_xdd = nullptr;  // task accelerations (kOpOsc)
+  const float* in_fext = nullptr;  // external forces (kOpRneaExt, kOpAbaExt)
   float* out0 = nullptr;  // pose / tau / M / qdd / qbar
   float* out1 = nullptr;  // J / LD / qdbar / Lambda
   float* out2 = nullptr;  // qddbar / taubar

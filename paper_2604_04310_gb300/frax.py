@@ -189,6 +189,26 @@ def frax_aba(model: Model, q, qd, tau, qdd=None):
     return qdd
 
 
+def frax_rnea_ext(model: Model, q, qd, qdd, fext, tau=None):
+    """tau = M qdd + c + g - sum_i J_i^T F_ext,i; fext (6*n_bodies, B) holds
+    each body's external spatial force in root-frame Pluecker coordinates
+    [moment about the root origin; force]; qdd=None means zero."""
+    B, ld = _prep(model, q, qd=(qd, model.nv), qdd=(qdd, model.nv), fext=(fext, 6 * model.n_bodies),
+                  tau=(tau, model.nv))
+    tau = _out(model.nv, q, ld, B) if tau is None else tau
+    _check(lib().frax_rnea_ext(model.handle, B, ld, _p(q), _p(qd), _p(qdd), _p(fext), _p(tau), _stream(q)))
+    return tau
+
+
+def frax_aba_ext(model: Model, q, qd, tau, fext, qdd=None):
+    """qdd = M^-1 (tau - c - g + sum_i J_i^T F_ext,i), fext as frax_rnea_ext."""
+    B, ld = _prep(model, q, qd=(qd, model.nv), tau=(tau, model.nv), fext=(fext, 6 * model.n_bodies),
+                  qdd=(qdd, model.nv))
+    qdd = _out(model.nv, q, ld, B) if qdd is None else qdd
+    _check(lib().frax_aba_ext(model.handle, B, ld, _p(q), _p(qd), _p(tau), _p(fext), _p(qdd), _stream(q)))
+    return qdd
+
+
 def frax_rnea_vjp(model: Model, q, qd, qdd, gbar, qbar=None, qdbar=None, qddbar=None, want_qddbar=True):
     """(dtau/dq)^T gbar [ambient, nq], (dtau/dqd)^T gbar, M gbar."""
     nv = model.nv

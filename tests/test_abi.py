@@ -118,3 +118,15 @@ def test_osc_argument_checks_before_any_launch():
     assert b"xdd_des is NULL" in L.frax_last_error()
     hu = fx.Model.from_robot(gen.humanoid(0))
     assert L.frax_osc(hu.handle, 0, 0, 0, null, null, null, null, null, null) == 0  # free root: 6 dofs
+
+
+def test_external_force_argument_checks():
+    L = _lib.load()
+    null = ctypes.c_void_p(0)
+    p = ctypes.c_void_p(16)
+    ch = fx.Model.from_robot(gen.chain7(0))
+    assert L.frax_rnea_ext(ch.handle, 0, 0, null, null, null, null, null, null) == 0
+    assert L.frax_rnea_ext(ch.handle, 16, 16, p, p, null, null, p, null) == 1
+    assert b"fext is NULL" in L.frax_last_error()
+    assert L.frax_aba_ext(ch.handle, 16, 16, p, p, p, p, null, null) == 1
+    assert b"qdd is NULL" in L.frax_last_error()
