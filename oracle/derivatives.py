@@ -18,7 +18,7 @@ and satisfies quat_bar . dquat = dw_bar . dw for every dquat = Q dw / 2.
 
 import numpy as np
 
-from .rbd import Layout, FREE, aba, crba, rnea
+from .rbd import Layout, FREE, aba, crba, fk, rnea
 from .spatial import matvec, quat_exp, quat_multiply, quat_to_rotation
 
 H_STEP = 1e-30
@@ -110,3 +110,34 @@ def mass_matrix_rate(model, q, qd):
     d = np.zeros(q.shape[:1] + (Layout(model).nv,), dtype=np.complex128)
     d[:] = 1j * H_STEP * qd
     return np.imag(crba(model, retract(model, q, d))) / H_STEP
+
+
+# ------------------------------------------------ forward mode (JVPs)
+# One complex evaluation along the tangent direction: the directional
+# derivative, what jax.jvp returns (Sec. IV-A uses it on the dynamics).
+
+def rnea_jvp(model, q, qd, qdd, dq, dqd, dqdd):
+    """d tau along (dq [tangent], dqd, dqdd): (B, nv)."""
+    h = H_STEP
+    t = rnea(model, retract(model, q, 1j * h * dq.astype(np.complex128)), qd + 1j * h * dqd,
+             qdd + 1j * h * dqdd)
+    return np.imag(t) / h
+
+
+def aba_jvp(model, q, qd, tau, dq, dqd, dtau):
+    """d qdd along (dq [tangent], dqd, dtau) of Eq. 2: (B, nv)."""
+    h = H_STEP
+    a = aba(model, retract(model, q, 1j * h * dq.astype(np.complex128)), qd + 1j * h * dqd, tau + 1j * h * dtau)
+    return np.imag(a) / h
+
+
+def fk_jvp(model, q, dq, frames):
+    """Motion of each frame body along dq: [omega; d p] (B, nf, 6) in world
+    coordinates, omega = vee(dR R^T)."""
+    h = H_STEP
+    Rc, pc = fk(model, retract(model, q, 1j * h * dq.astype(np.complex128)))
+    R, p = fk(model, q)
+    f = list(frames)
+    W = (np.imag(Rc[:, f]) / h) @ np.swapaxes(R[:, f], -1, -2)
+    w = np.stack([W[..., 2, 1], W[..., 0, 2], W[..., 1, 0]], -1)
+    return np.concatenate([w, np.imag(pc[:, f]) / h], -1)
