@@ -46,14 +46,16 @@ FP32_LANES_PER_SM = 128
 # keeps the count of the direct formulation that stores instead, so the
 # roofline is against the algorithm's work, not the kernel's extra work. The
 # chain ABA adjoint = its M^-1 solve through the mass-matrix factor (2389)
-# plus the stored-state RNEA adjoint (4913).
+# plus the stored-state RNEA adjoint (4913). The JVPs' counts leave out the
+# 280-flop step back through a joint that the kernels make instead of storing
+# (6 per chain sweep, 24 per humanoid sweep).
 FLOPS = {
     "chain7": {"fk_jac": 903, "fk": 819, "rnea": 2000, "bias": 2000, "crba_ltdl": 2305, "crba": 2172,
                "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 7302, "osc": 10718, "rnea_ext": 2710,
-               "aba_ext": 6012},
+               "aba_ext": 6012, "fk_jvp": 856, "rnea_jvp": 4816, "aba_jvp": 7212},
     "humanoid": {"fk_jac": 5304, "fk": 3792, "rnea": 9028, "bias": 9022, "crba_ltdl": 16691, "crba": 12921,
                  "aba": 25231, "rnea_vjp": 22034, "aba_vjp": 43301, "osc": 31265, "rnea_ext": 12236,
-                 "aba_ext": 28439},
+                 "aba_ext": 28439, "fk_jvp": 3635, "rnea_jvp": 20429, "aba_jvp": 41814},
 }
 # operational-space control task bodies (the last end frame of each model)
 OSC_TASK = {"chain7": 6, "humanoid": 29}
@@ -70,6 +72,7 @@ def bytes_per_instance(op, nq, nv, nb, nframes):
         "rnea_vjp": f * (2 * nq + 5 * nv), "aba_vjp": f * (2 * nq + 5 * nv),
         "osc": f * (nq + 2 * nv + 6),
         "rnea_ext": f * (nq + 3 * nv + 6 * nb), "aba_ext": f * (nq + 3 * nv + 6 * nb),
+        "fk_jvp": f * (nq + nv + 6 * nframes), "rnea_jvp": f * (nq + 6 * nv), "aba_jvp": f * (nq + 6 * nv),
     }[op]
 
 
@@ -176,6 +179,8 @@ class Step:
             "LD": e(nv * (nv + 1) // 2), "qdd": e(nv), "rq": e(model.nq), "rqd": e(nv), "rqdd": e(nv),
             "aq": e(model.nq), "aqd": e(nv), "at": e(nv),
         }
+        if "fk_jvp" in ops:
+            self.out["dpose"] = e(6 * len(self.frames))
         fx_, m, d, o = fx, model, dev, self.out
         table = {
             "fk_jac": lambda: fx_.frax_jacobian(m, d["q"], self.frames, pose=o["pose"], J=o["J"]),
@@ -189,6 +194,11 @@ class Step:
                                                 qdbar=o["aqd"], taubar=o["at"]),
             "osc": lambda: fx_.frax_osc(m, task, d["q"], d["qd"], d["xdd"], tau=o["tau"]),
             "rnea_ext": lambda: fx_.frax_rnea_ext(m, d["q"], d["qd"], d["qdd"], d["fext"], tau=o["tau"]),
+            "fk_jvp": lambda: fx_.frax_fk_jvp(m, d["q"], d["dq"], self.frames, dpose=o["dpose"]),
+            "rnea_jvp": lambda: fx_.frax_rnea_jvp(m, d["q"], d["qd"], d["qdd"], d["dq"], d["dqd"], d["dx"],
+                                                  dtau=o["at"]),
+            "aba_jvp": lambda: fx_.frax_aba_jvp(m, d["q"], d["qd"], d["tau"], d["qdd"], d["dq"], d["dqd"], d["dx"],
+                                                dqdd=o["aqd"]),
             "aba_ext": lambda: fx_.frax_aba_ext(m, d["q"], d["qd"], d["tau"], d["fext"], qdd=o["qdd"]),
         }
         self.launches = [(n, table[n]) for n in ops]
@@ -547,14 +557,18 @@ def frax_arm(args, rank, world, local_rank):
     if not args.no_next:
         nxt = {"workload": "operational-space control tau = J^T Lambda (xdd - Jdot qd) + c + g for the last end "
                            "frame (xdd uniform in [-3, 3]); RNEA and ABA with standard-normal external spatial "
-                           "forces on every body; 7-DoF chain 2^20, humanoid 2^18 instances"}
+                           "forces on every body; JVPs of FK (end frames), RNEA and ABA along standard-normal "
+                           "directions (the ABA JVP at the input qdd as saved forward result); 7-DoF chain 2^20, "
+                           "humanoid 2^18 instances"}
         for oname, orobot, oB in (("chain7", gen.chain7(0), B), ("humanoid", gen.humanoid(0), args.humanoid_batch)):
             omodel = fx.Model.from_robot(orobot)
             _, odev = make_inputs(orobot, oB, 3003 + rank, device)
             rng = np.random.default_rng(3004 + rank)
             odev["xdd"] = torch.from_numpy(rng.uniform(-3, 3, (6, oB)).astype(np.float32)).to(device)
             odev["fext"] = torch.from_numpy(rng.standard_normal((6 * orobot.n_bodies, oB), np.float32)).to(device)
-            oops = ["osc", "rnea_ext", "aba_ext"]
+            for k in ("dq", "dqd", "dx"):
+                odev[k] = torch.from_numpy(rng.standard_normal((orobot.nv, oB), np.float32)).to(device)
+            oops = ["osc", "rnea_ext", "aba_ext", "fk_jvp", "rnea_jvp", "aba_jvp"]
             ostep = Step(fx, omodel, orobot, odev, device, oops, task=OSC_TASK[oname])
             osteps = max(5, args.steps // 5)
             oms, oper, ol, _, _ = time_step(ostep, osteps, max(3, args.warmup), flush, world, dist)

@@ -41,9 +41,25 @@ inline void sincosf(CF x, CF* s, CF* c) { g.sfu++; s->v = std::sin(x.v); c->v = 
 #define float CF
 #include "paper_2604_04310_gb300/csrc/osc.cuh"
 #include "paper_2604_04310_gb300/csrc/ext.cuh"
+#include "paper_2604_04310_gb300/csrc/jvp.cuh"
 #undef float
 
 using namespace frax;
+
+// One JVP step back through a joint, and how many a sweep makes (bodies after
+// the first of each revolute segment): the direct formulation that stores the
+// forward state does not make them.
+template <class Img>
+void count_stepback(const Img& M) {
+  SV v{mk(0.1f, 0.2f, 0.3f), mk(0.4f, 0.5f, 0.6f)}, a = v, dv = v, da = v;
+  g = Counts{};
+  jvp_step_back(M.body[M.nb - 1], CF(0.8f), CF(0.6f), CF(0.1f), CF(0.2f), CF(0.3f), CF(0.4f), CF(0.5f), v, a, dv, da);
+  int n = 0;
+  for (int s = (M.free_root ? 1 : 0); s < M.n_seg; ++s) n += M.seg_len[s] - 1;
+  printf("  \"jvp_stepback\": {\"flops\": %lld, \"count\": %d},\n", 2 * g.fma + g.add + g.mul, n);
+  g = Counts{};
+}
+
 
 template <class T, class Img>
 void count(const Img& M, int nf, const int* frames) {
@@ -84,6 +100,13 @@ void count(const Img& M, int nf, const int* frames) {
     ext_tau<T>(M, q.data(), fe.data(), col, OutToLocal<T>{&w}); rep("ext_tau");
   }
   if constexpr (T::kSeg) {
+    std::vector<CF> dq(nv, CF(0.3f)), dqd(nv, CF(0.2f)), dx(nv, CF(0.1f)), o9(nv + 8), o10(6 * nf + 8);
+    rnea_jvp_seg<T>(M, q.data(), qd.data(), qdd.data(), dq.data(), dqd.data(), dx.data(),
+                    JvpToGlobal<T, Col>{o6.data(), o9.data(), col}, col); rep("rnea_jvp");
+    aba_jvp_seg_one<T>(M, q.data(), qd.data(), qdd.data(), dq.data(), dqd.data(), dx.data(), o9.data(), col);
+    rep("aba_jvp");
+    fk_jvp_seg<T>(M, q.data(), dq.data(), fr, o10.data(), col); rep("fk_jvp");
+    count_stepback(M);
     rnea_vjp_seg_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp");
     aba_vjp_seg_one<T>(M, q.data(), qd.data(), tau.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp");
     std::vector<CF> lam(36 + 8);
@@ -109,7 +132,14 @@ void count_chain_vjp(const Img& M) {
   rnea_vjp_seg_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("rnea_vjp_seg");
   aba_vjp_chain_one<7>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp_chain");
   std::vector<CF> w(8);
-  chain_minv<7>(M, q.data(), gb.data(), w.data(), col); rep("minv_factor");
+  chain_minv<7>(M, q.data(), RhsFromGlobal<ChainTopo<7>, Col>{gb.data(), col}, w.data(), col); rep("minv_factor");
+  std::vector<CF> dq(nv, CF(0.3f)), dqd(nv, CF(0.2f)), dx(nv, CF(0.1f)), o9(nv + 8), o10(6 + 8);
+  rnea_jvp_seg<T>(M, q.data(), qd.data(), qdd.data(), dq.data(), dqd.data(), dx.data(),
+                  JvpToGlobal<T, Col>{o6.data(), o9.data(), col}, col); rep("rnea_jvp");
+  aba_jvp_chain_one<7>(M, q.data(), qd.data(), qdd.data(), dq.data(), dqd.data(), dx.data(), o9.data(), col);
+  rep("aba_jvp");
+  fk_jvp_seg<T>(M, q.data(), dq.data(), Frames{1, {6}}, o10.data(), col); rep("fk_jvp");
+  count_stepback(M);
   std::vector<CF> lam(36 + 8);
   osc_seg<T>(M, 6, q.data(), qd.data(), qdd.data(), o6.data(), nullptr, col); rep("osc");
   osc_seg<T>(M, 6, q.data(), qd.data(), qdd.data(), o6.data(), lam.data(), col); rep("osc_lambda");

@@ -163,6 +163,33 @@ FRAX_API frax_status frax_aba_vjp(frax_model_t model, int64_t B, int64_t ld, con
                          float* qbar, float* qdbar, float* taubar, void* stream);
 
 /*
+ * Forward-mode derivatives (JVPs): the directional derivatives jax.jvp
+ * returns on FK and on Eq. 1 and 2 (Sec. IV-A), as tangent recursions run
+ * beside the value recursions. Directions are tangent vectors (nv rows): a
+ * revolute entry is the angle's rate, a free-flyer root's six entries
+ * [dw; dv] perturb its pose as T * Exp([dw; dv]) (body frame).
+ *
+ * frax_fk_jvp — the motion of each frame body along dq, [omega; p_dot] in
+ *   world coordinates (J dq without forming J).
+ *   q [nq][ld], dq [nv][ld] in; n_frames 1..8, frame_body HOST int32;
+ *   dpose [n_frames*6][ld] out.
+ * frax_rnea_jvp — tau = RNEA(q, qd, qdd) and its derivative along
+ *   (dq, dqd, dqdd). qdd or dqdd NULL: zero. tau may be NULL.
+ * frax_aba_jvp — the derivative of qdd = ABA(q, qd, tau) along
+ *   (dq, dqd, dtau), evaluated at the saved forward result qdd (tau itself
+ *   is not read): M dqdd = dtau - dRNEA(q, qd, qdd)[dq, dqd, 0]. dtau NULL:
+ *   zero. dqdd [nv][ld] out.
+ */
+FRAX_API frax_status frax_fk_jvp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* dq,
+                                 int n_frames, const int32_t* frame_body, float* dpose, void* stream);
+FRAX_API frax_status frax_rnea_jvp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                                   const float* qdd, const float* dq, const float* dqd, const float* dqdd,
+                                   float* tau, float* dtau, void* stream);
+FRAX_API frax_status frax_aba_jvp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                                  const float* tau, const float* qdd, const float* dq, const float* dqd,
+                                  const float* dtau, float* dqdd, void* stream);
+
+/*
  * frax_ltdl_solve — x = M^-1 b from the packed factor M = L^T D L that
  * frax_crba writes (the Cholesky-based solve the paper's Sec. VI footnote
  * recommends over inverting M): L^T y = b, then L x = D^-1 y, walking only

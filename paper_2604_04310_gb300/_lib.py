@@ -34,6 +34,9 @@ SIGNATURES = {
     "frax_ltdl_inverse": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
     "frax_rnea_ext": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_aba_ext": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_fk_jvp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_int, c_vp, c_vp, c_vp]),
+    "frax_rnea_jvp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_aba_jvp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_osc": (c_int, [c_vp, c_int, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_server_create": (c_int, [c_i64, ctypes.c_double, ctypes.POINTER(c_vp)]),
     "frax_server_add_model": (c_int, [c_vp, c_vp, ctypes.POINTER(c_int)]),

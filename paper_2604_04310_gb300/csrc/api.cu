@@ -256,6 +256,61 @@ frax_status frax_aba_ext(frax_model_t model, int64_t B, int64_t ld, const float*
   return dispatch(model, frax::kOpAbaExt, a, "frax_aba_ext");
 }
 
+frax_status frax_fk_jvp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* dq, int n_frames,
+                        const int32_t* frame_body, float* dpose, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_fk_jvp"));
+  if (n_frames < 1 || n_frames > FRAX_MAX_FRAMES)
+    return fail(FRAX_EINVAL, "frax_fk_jvp: n_frames must be in [1, 8]");
+  FRAX_TRY(need(frame_body, "frax_fk_jvp", "frame_body"));
+  frax::OpArgs a;
+  a.frames.n = n_frames;
+  for (int f = 0; f < n_frames; ++f) {
+    if (frame_body[f] < 0 || frame_body[f] >= model->m.nb)
+      return fail(FRAX_EINVAL, "frax_fk_jvp: frame body index out of range");
+    a.frames.body[f] = frame_body[f];
+  }
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_fk_jvp", "q"));
+  FRAX_TRY(need(dq, "frax_fk_jvp", "dq"));
+  FRAX_TRY(need(dpose, "frax_fk_jvp", "dpose"));
+  a.B = B; a.ld = ld; a.q = q; a.in_dq = dq; a.out0 = dpose; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpFkJvp, a, "frax_fk_jvp");
+}
+
+frax_status frax_rnea_jvp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                          const float* qdd, const float* dq, const float* dqd, const float* dqdd, float* tau,
+                          float* dtau, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_rnea_jvp"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_rnea_jvp", "q"));
+  FRAX_TRY(need(qd, "frax_rnea_jvp", "qd"));
+  FRAX_TRY(need(dq, "frax_rnea_jvp", "dq"));
+  FRAX_TRY(need(dqd, "frax_rnea_jvp", "dqd"));
+  FRAX_TRY(need(dtau, "frax_rnea_jvp", "dtau"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.qdd = qdd; a.in_dq = dq; a.in_dqd = dqd; a.in_dx = dqdd;
+  a.out0 = tau; a.out1 = dtau; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpRneaJvp, a, "frax_rnea_jvp");
+}
+
+frax_status frax_aba_jvp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                         const float* tau, const float* qdd, const float* dq, const float* dqd, const float* dtau,
+                         float* dqdd, void* stream) {
+  (void)tau;  // evaluated at the saved forward result qdd = ABA(q, qd, tau)
+  FRAX_TRY(check_batch(model, B, ld, "frax_aba_jvp"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_aba_jvp", "q"));
+  FRAX_TRY(need(qd, "frax_aba_jvp", "qd"));
+  FRAX_TRY(need(qdd, "frax_aba_jvp", "qdd"));
+  FRAX_TRY(need(dq, "frax_aba_jvp", "dq"));
+  FRAX_TRY(need(dqd, "frax_aba_jvp", "dqd"));
+  FRAX_TRY(need(dqdd, "frax_aba_jvp", "dqdd"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.qdd = qdd; a.in_dq = dq; a.in_dqd = dqd; a.in_dx = dtau;
+  a.out0 = dqdd; a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpAbaJvp, a, "frax_aba_jvp");
+}
+
 frax_status frax_osc(frax_model_t model, int task_body, int64_t B, int64_t ld, const float* q, const float* qd,
                      const float* xdd_des, float* tau, float* Lambda, void* stream) {
   FRAX_TRY(check_batch(model, B, ld, "frax_osc"));

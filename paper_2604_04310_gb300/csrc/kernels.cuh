@@ -8,6 +8,7 @@
 #include "solve.cuh"
 #include "osc.cuh"
 #include "ext.cuh"
+#include "jvp.cuh"
 #include "launch.h"
 
 namespace frax {
@@ -150,6 +151,31 @@ __global__ void __launch_bounds__(kBlock, 4) k_aba_ext(const __grid_constant__ M
   }
 }
 
+// Forward-mode derivatives (segment code; chains run it on the 8-slot image).
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_rnea_jvp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                      int64_t ld, const float* q, const float* qd,
+                                                      const float* qdd, const float* dq, const float* dqd,
+                                                      const float* dqdd, float* tau, float* dtau) {
+  FRAX_TID();
+  rnea_jvp_seg<T>(M, q, qd, qdd, dq, dqd, dqdd, JvpToGlobal<T, Col>{tau, dtau, col}, col);
+}
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_aba_jvp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                     int64_t ld, const float* q, const float* qd,
+                                                     const float* qdd, const float* dq, const float* dqd,
+                                                     const float* dtau, float* dqdd) {
+  FRAX_TID();
+  aba_jvp_seg_one<T>(M, q, qd, qdd, dq, dqd, dtau, dqdd, col);
+}
+template <class T>
+__global__ void __launch_bounds__(kBlock, 6) k_fk_jvp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+                                                       int64_t ld, const float* q, const float* dq,
+                                                       const __grid_constant__ Frames fr, float* out) {
+  FRAX_TID();
+  fk_jvp_seg<T>(M, q, dq, fr, out, col);
+}
+
 template <class T>
 cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a) {
   const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock)), block(kBlock);
@@ -192,6 +218,24 @@ cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a)
       break;
     case kOpAbaExt:
       k_aba_ext<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.in_fext, a.out0);
+      break;
+    case kOpFkJvp:
+      if constexpr (T::kSeg) k_fk_jvp<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.in_dq, fr, a.out0);
+      else return cudaErrorInvalidValue;
+      break;
+    case kOpRneaJvp:
+      if constexpr (T::kSeg)
+        k_rnea_jvp<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.in_dq, a.in_dqd, a.in_dx,
+                                                    a.out0, a.out1);
+      else
+        return cudaErrorInvalidValue;
+      break;
+    case kOpAbaJvp:
+      if constexpr (T::kSeg)
+        k_aba_jvp<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.in_dq, a.in_dqd, a.in_dx,
+                                                   a.out0);
+      else
+        return cudaErrorInvalidValue;
       break;
     case kOpOsc:
       if constexpr (T::kSeg)

@@ -9,7 +9,7 @@
 namespace frax {
 
 enum Op { kOpFk = 0, kOpJac, kOpRnea, kOpCrba, kOpAba, kOpRneaVjp, kOpAbaVjp, kOpLtdlSolve, kOpLtdlInverse,
-          kOpOsc, kOpRneaExt, kOpAbaExt, kOpCount };
+          kOpOsc, kOpRneaExt, kOpAbaExt, kOpFkJvp, kOpRneaJvp, kOpAbaJvp, kOpCount };
 
 struct FramesArg {
   int n;
@@ -26,6 +26,9 @@ struct OpArgs {
   const float* in_LD = nullptr;
   const float* in_xdd = nullptr;  // task accelerations (kOpOsc)
   const float* in_fext = nullptr;  // external forces (kOpRneaExt, kOpAbaExt)
+  const float* in_dq = nullptr;    // JVP directions: dq, dqd, and dqdd or dtau
+  const float* in_dqd = nullptr;
+  const float* in_dx = nullptr;
   float* out0 = nullptr;  // pose / tau / M / qdd / qbar
   float* out1 = nullptr;  // J / LD / qdbar / Lambda
   float* out2 = nullptr;  // qddbar / taubar

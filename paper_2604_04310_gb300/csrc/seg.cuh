@@ -763,9 +763,9 @@ FD void aba_vjp_seg_one(const Img& M, const float* q, const float* qd, const flo
 // lower triangle (registers), factored in place as M = L^T D L, then
 // L^T u = gbar (back substitution), L w = D^-1 u (forward substitution).
 // The rest is the segment RNEA adjoint seeded with w.
-template <int N, class Img, class C>
-FD void chain_minv(const Img& M, const float* __restrict__ q, const float* __restrict__ g, float* w,
-                   const C& col) {
+// g(k): right-hand side entry k (a global column or a thread-local vector).
+template <int N, class Img, class G, class C>
+FD void chain_minv(const Img& M, const float* __restrict__ q, const G& g, float* w, const C& col) {
   using T = ChainTopo<N>;
   constexpr int NT = N * (N + 1) / 2;
   float H[NT];
@@ -802,7 +802,7 @@ FD void chain_minv(const Img& M, const float* __restrict__ q, const float* __res
   float u[N];
 #pragma unroll
   for (int k = N - 1; k >= 0; --k) {
-    float x = col.in(g, k);
+    float x = g(k);
 #pragma unroll
     for (int i = k + 1; i < N; ++i) x = fmaf(-H[MSink::tri(i, k)], u[i], x);
     u[k] = x;
@@ -822,7 +822,7 @@ FD void aba_vjp_chain_one(const Img& M, const float* q, const float* qd, const f
                           float* qbar, float* qdbar, float* taubar, const C& col) {
   using S = SegTopo<N + 1, false>;
   LocalVec<S> w;
-  chain_minv<N>(M, q, gbar, w.x, col);
+  chain_minv<N>(M, q, RhsFromGlobal<ChainTopo<N>, C>{gbar, col}, w.x, col);
   if (taubar) {
 #pragma unroll
     for (int k = 0; k < N; ++k) col.out(taubar, k, w.x[k]);

@@ -209,6 +209,44 @@ def frax_aba_ext(model: Model, q, qd, tau, fext, qdd=None):
     return qdd
 
 
+def frax_fk_jvp(model: Model, q, dq, frames, dpose=None):
+    """Motion [omega; p_dot] (world) of each frame along the tangent dq:
+    (n_frames*6, B)."""
+    frames = np.ascontiguousarray(frames, dtype=np.int32).reshape(-1)
+    nf = int(frames.shape[0])
+    B, ld = _prep(model, q, dq=(dq, model.nv), dpose=(dpose, 6 * nf))
+    dpose = _out(6 * nf, q, ld, B) if dpose is None else dpose
+    _check(lib().frax_fk_jvp(model.handle, B, ld, _p(q), _p(dq), nf, frames.ctypes.data_as(_lib.c_i32), _p(dpose),
+                             _stream(q)))
+    return dpose
+
+
+def frax_rnea_jvp(model: Model, q, qd, qdd, dq, dqd, dqdd=None, tau=None, dtau=None, want_tau=False):
+    """(tau or None, dtau): RNEA and its derivative along the tangent
+    direction (dq, dqd, dqdd); qdd/dqdd None mean zero."""
+    nv = model.nv
+    B, ld = _prep(model, q, qd=(qd, nv), qdd=(qdd, nv), dq=(dq, nv), dqd=(dqd, nv), dqdd=(dqdd, nv),
+                  tau=(tau, nv), dtau=(dtau, nv))
+    dtau = _out(nv, q, ld, B) if dtau is None else dtau
+    if tau is None and want_tau:
+        tau = _out(nv, q, ld, B)
+    _check(lib().frax_rnea_jvp(model.handle, B, ld, _p(q), _p(qd), _p(qdd), _p(dq), _p(dqd), _p(dqdd), _p(tau),
+                               _p(dtau), _stream(q)))
+    return tau, dtau
+
+
+def frax_aba_jvp(model: Model, q, qd, tau, qdd, dq, dqd, dtau=None, dqdd=None):
+    """Derivative of qdd = ABA(q, qd, tau) along (dq, dqd, dtau), at the
+    saved forward result qdd; dtau None means zero."""
+    nv = model.nv
+    B, ld = _prep(model, q, qd=(qd, nv), tau=(tau, nv), qdd=(qdd, nv), dq=(dq, nv), dqd=(dqd, nv),
+                  dtau=(dtau, nv), dqdd=(dqdd, nv))
+    dqdd = _out(nv, q, ld, B) if dqdd is None else dqdd
+    _check(lib().frax_aba_jvp(model.handle, B, ld, _p(q), _p(qd), _p(tau), _p(qdd), _p(dq), _p(dqd), _p(dtau),
+                              _p(dqdd), _stream(q)))
+    return dqdd
+
+
 def frax_rnea_vjp(model: Model, q, qd, qdd, gbar, qbar=None, qdbar=None, qddbar=None, want_qddbar=True):
     """(dtau/dq)^T gbar [ambient, nq], (dtau/dqd)^T gbar, M gbar."""
     nv = model.nv

@@ -130,3 +130,19 @@ def test_external_force_argument_checks():
     assert b"fext is NULL" in L.frax_last_error()
     assert L.frax_aba_ext(ch.handle, 16, 16, p, p, p, p, null, null) == 1
     assert b"qdd is NULL" in L.frax_last_error()
+
+
+def test_jvp_argument_checks():
+    L = _lib.load()
+    null = ctypes.c_void_p(0)
+    p = ctypes.c_void_p(16)
+    ch = fx.Model.from_robot(gen.chain7(0))
+    frames = np.array([6], np.int32)
+    assert L.frax_fk_jvp(ch.handle, 16, 16, p, null, 1, frames.ctypes.data_as(_lib.c_i32), p, null) == 1
+    assert b"dq is NULL" in L.frax_last_error()
+    assert L.frax_fk_jvp(ch.handle, 16, 16, p, p, 0, frames.ctypes.data_as(_lib.c_i32), p, null) == 1
+    assert L.frax_rnea_jvp(ch.handle, 0, 0, null, null, null, null, null, null, null, null, null) == 0
+    assert L.frax_rnea_jvp(ch.handle, 16, 16, p, p, null, p, p, null, null, null, null) == 1
+    assert b"dtau is NULL" in L.frax_last_error()
+    assert L.frax_aba_jvp(ch.handle, 16, 16, p, p, null, null, p, p, null, p, null) == 1
+    assert b"qdd is NULL" in L.frax_last_error()
