@@ -195,6 +195,8 @@ class Step:
             "osc": lambda: fx_.frax_osc(m, task, d["q"], d["qd"], d["xdd"], tau=o["tau"]),
             "rnea_ext": lambda: fx_.frax_rnea_ext(m, d["q"], d["qd"], d["qdd"], d["fext"], tau=o["tau"]),
             "fk_jvp": lambda: fx_.frax_fk_jvp(m, d["q"], d["dq"], self.frames, dpose=o["dpose"]),
+            "fk": lambda: fx_.frax_fk(m, d["q"], pose=o["pose"]),
+            "fk_scan": lambda: fx_.frax_fk_scan(m, d["q"], pose=o["pose"]),
             "rnea_jvp": lambda: fx_.frax_rnea_jvp(m, d["q"], d["qd"], d["qdd"], d["dq"], d["dqd"], d["dx"],
                                                   dtau=o["at"]),
             "aba_jvp": lambda: fx_.frax_aba_jvp(m, d["q"], d["qd"], d["tau"], d["qdd"], d["dq"], d["dqd"], d["dx"],
@@ -576,6 +578,21 @@ def frax_arm(args, rank, world, local_rank):
             nxt[oname] = {"osc_task_body": OSC_TASK[oname], "batch": oB, "steps": osteps,
                           "per_op": roofline_of(oper, FLOPS[oname], oB, peak, hbm, orobot)}
             del ostep, odev
+
+    # serial-chain FK: the thread-per-instance loop vs the warp-level SE(3)
+    # prefix scan, on a 64-body chain at a small and a large batch
+    if nxt is not None:
+        srobot = gen.serial_chain(5, 64)
+        smodel = fx.Model.from_robot(srobot)
+        nxt["fk_scan"] = {"workload": "64-body serial chain (seed 5): frax_fk (sequential loop per thread) vs "
+                                      "frax_fk_scan (prefix product over SE(3), one warp per instance)"}
+        for sB in (256, 1 << 16):
+            _, sdev = make_inputs(srobot, sB, 3005 + rank, device)
+            sstep = Step(fx, smodel, srobot, sdev, device, ["fk", "fk_scan"])
+            _, sper, sl, _, _ = time_step(sstep, 50, 5, flush, world, dist)
+            launches += sl
+            nxt["fk_scan"][f"B{sB}"] = {"fk_us": sper["fk"] * 1e3, "fk_scan_us": sper["fk_scan"] * 1e3}
+            del sstep, sdev
 
     serve = None
     if rank == 0 and not args.no_serve:

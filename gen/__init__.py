@@ -10,10 +10,10 @@ Sec. IV); their parameters are random because the real robots' URDFs are not
 available.
 """
 
-from .models import RobotModel, chain7, humanoid, random_tree, serving_pool
+from .models import RobotModel, chain7, humanoid, random_tree, serial_chain, serving_pool
 from .states import States, draw_states, draw_gbar, to_soa, from_soa
 
 __all__ = [
-    "RobotModel", "chain7", "humanoid", "random_tree", "serving_pool",
+    "RobotModel", "chain7", "humanoid", "random_tree", "serial_chain", "serving_pool",
     "States", "draw_states", "draw_gbar", "to_soa", "from_soa",
 ]

@@ -150,6 +150,21 @@ def random_tree(seed: int, n: int | None = None) -> RobotModel:
     return RobotModel(f"tree{seed}_{n}", parent, jt, axis, placement, inertia, end_frames=leaves)
 
 
+def serial_chain(seed: int, n: int, free_root: bool = False) -> RobotModel:
+    """Serial chain of n bodies (parent of i is i - 1): n revolute joints, or
+    a free-flyer root followed by n - 1 revolute joints."""
+    rng = np.random.default_rng(seed)
+    axis, placement, inertia = _draw_links(rng, n, (0.3, 4.0))
+    parent = np.arange(-1, n - 1, dtype=np.int32)
+    jt = np.zeros(n, dtype=np.int32)
+    if free_root:
+        jt[0] = FREE
+        placement[0, :9] = np.eye(3).reshape(-1)
+        placement[0, 9:] = 0.0
+    return RobotModel(f"serial{n}{'f' if free_root else ''}_{seed}", parent, jt, axis, placement, inertia,
+                      end_frames=(n - 1,))
+
+
 def serving_pool(n_random: int = 32):
     """The models a serving stream draws from: chain, humanoid and random trees
     (seeds 100..100+n_random-1, 3-64 bodies)."""

@@ -85,9 +85,9 @@ FRAX_API frax_status frax_model_create(int n_bodies, const int32_t* parent, cons
 FRAX_API frax_status frax_model_destroy(frax_model_t model);
 /* nq, nv, n_bodies of the model (any pointer may be NULL). */
 FRAX_API frax_status frax_model_dims(frax_model_t model, int* nq, int* nv, int* n_bodies);
-/* Kernel family the model dispatches to: 0 = serial chain (thread per
- * instance, topology compiled in), 1 = general tree (thread per instance),
- * 2 = the 30-body floating-base humanoid shape (branch-parallel warp). */
+/* Kernel family the model dispatches to: 0 = 7-body serial chain (thread
+ * per instance, topology compiled in), 1 = general tree (thread per
+ * instance, segment sweeps). */
 FRAX_API frax_status frax_model_kind(frax_model_t model, int* kind);
 
 /*
@@ -97,6 +97,17 @@ FRAX_API frax_status frax_model_kind(frax_model_t model, int* kind);
  */
 FRAX_API frax_status frax_fk(frax_model_t model, int64_t B, int64_t ld, const float* q, float* pose,
                     void* stream);
+
+/*
+ * frax_fk_scan — frax_fk for serial chains (parent[i] = i - 1) as a parallel
+ * prefix product over SE(3), one warp per instance (the associative scan
+ * that replaces the FK loop for serial chains, Sec. III-A): depth 7 instead
+ * of n_bodies sequential compositions. For small batches of long chains;
+ * frax_fk does less work per instance and is faster for large batches.
+ * FRAX_EINVAL for a model that is not a serial chain. Same layout as frax_fk.
+ */
+FRAX_API frax_status frax_fk_scan(frax_model_t model, int64_t B, int64_t ld, const float* q, float* pose,
+                                  void* stream);
 
 /*
  * frax_jacobian — geometric Jacobians of body frames (Sec. IV, "Jacobians"),

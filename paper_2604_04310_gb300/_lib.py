@@ -34,6 +34,7 @@ SIGNATURES = {
     "frax_ltdl_inverse": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
     "frax_rnea_ext": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_aba_ext": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_fk_scan": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
     "frax_fk_jvp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_int, c_vp, c_vp, c_vp]),
     "frax_rnea_jvp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_aba_jvp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),

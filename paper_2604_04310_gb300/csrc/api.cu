@@ -256,6 +256,23 @@ frax_status frax_aba_ext(frax_model_t model, int64_t B, int64_t ld, const float*
   return dispatch(model, frax::kOpAbaExt, a, "frax_aba_ext");
 }
 
+frax_status frax_fk_scan(frax_model_t model, int64_t B, int64_t ld, const float* q, float* pose, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_fk_scan"));
+  const frax::HostModel& m = model->m;
+  for (int i = 1; i < m.nb; ++i)
+    if (m.parent[i] != i - 1) return fail(FRAX_EINVAL, "frax_fk_scan: the model is not a serial chain");
+  if (B > (int64_t(1) << 32)) return fail(FRAX_EINVAL, "frax_fk_scan: B too large");
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_fk_scan", "q"));
+  FRAX_TRY(need(pose, "frax_fk_scan", "pose"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.out0 = pose; a.stream = static_cast<cudaStream_t>(stream);
+  const cudaError_t e = frax::launch_fk_scan(m, a);
+  if (e != cudaSuccess)
+    return fail(FRAX_ECUDA, std::string("frax_fk_scan: kernel launch failed: ") + cudaGetErrorString(e));
+  return ok();
+}
+
 frax_status frax_fk_jvp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* dq, int n_frames,
                         const int32_t* frame_body, float* dpose, void* stream) {
   FRAX_TRY(check_batch(model, B, ld, "frax_fk_jvp"));

@@ -40,6 +40,8 @@ struct OpArgs {
 cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a);
 cudaError_t launch_tree32(const HostModel& m, Op op, const OpArgs& a);
 cudaError_t launch_tree64(const HostModel& m, Op op, const OpArgs& a);
+// serial chains, one warp per instance (prefix product over SE(3))
+cudaError_t launch_fk_scan(const HostModel& m, const OpArgs& a);
 
 constexpr int kBlock = 128;
 

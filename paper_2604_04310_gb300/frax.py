@@ -148,6 +148,14 @@ def frax_fk(model: Model, q, pose=None):
     return pose
 
 
+def frax_fk_scan(model: Model, q, pose=None):
+    """frax_fk for serial chains by a warp-level prefix product over SE(3)."""
+    B, ld = _prep(model, q, pose=(pose, 12 * model.n_bodies))
+    pose = _out(12 * model.n_bodies, q, ld, B) if pose is None else pose
+    _check(lib().frax_fk_scan(model.handle, B, ld, _p(q), _p(pose), _stream(q)))
+    return pose
+
+
 def frax_jacobian(model: Model, q, frames, pose=None, J=None, want_pose=False):
     """Frame Jacobians (n_frames*6*nv, B); returns (pose or None, J)."""
     frames = np.ascontiguousarray(frames, dtype=np.int32).reshape(-1)

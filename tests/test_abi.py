@@ -146,3 +146,13 @@ def test_jvp_argument_checks():
     assert b"dtau is NULL" in L.frax_last_error()
     assert L.frax_aba_jvp(ch.handle, 16, 16, p, p, null, null, p, p, null, p, null) == 1
     assert b"qdd is NULL" in L.frax_last_error()
+
+
+def test_fk_scan_requires_a_serial_chain():
+    L = _lib.load()
+    p = ctypes.c_void_p(16)
+    tree = fx.Model.from_robot(gen.random_tree(101))
+    assert L.frax_fk_scan(tree.handle, 4, 4, p, p, ctypes.c_void_p(0)) == 1
+    assert b"serial chain" in L.frax_last_error()
+    ch = fx.Model.from_robot(gen.serial_chain(1, 64, free_root=True))
+    assert L.frax_fk_scan(ch.handle, 0, 0, ctypes.c_void_p(0), ctypes.c_void_p(0), ctypes.c_void_p(0)) == 0
