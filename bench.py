@@ -45,17 +45,19 @@ FP32_LANES_PER_SM = 128
 # velocities; the tree factor comes from articulated inertias) the table
 # keeps the count of the direct formulation that stores instead, so the
 # roofline is against the algorithm's work, not the kernel's extra work. The
-# chain ABA adjoint = its M^-1 solve through the mass-matrix factor (2389)
-# plus the stored-state RNEA adjoint (4913). The JVPs' counts leave out the
-# 280-flop step back through a joint that the kernels make instead of storing
-# (6 per chain sweep, 24 per humanoid sweep).
+# chain ABA adjoint = its M^-1 solve through the mass-matrix factor (1670)
+# plus the stored-state RNEA adjoint (4272); the "direct_*" lines of
+# --count-flops give the stored-state counts. The JVPs' counts leave out the
+# 208-flop step back through a joint that the kernels make instead of storing
+# (6 per chain sweep, 24 per humanoid sweep). With external forces: the
+# plain kernel's count plus the force sweep's (554 chain, 2585 humanoid).
 FLOPS = {
-    "chain7": {"fk_jac": 903, "fk": 819, "rnea": 2000, "bias": 2000, "crba_ltdl": 2305, "crba": 2172,
-               "aba": 5302, "rnea_vjp": 4913, "aba_vjp": 7302, "osc": 10718, "rnea_ext": 2710,
-               "aba_ext": 6012, "fk_jvp": 856, "rnea_jvp": 4816, "aba_jvp": 7212},
-    "humanoid": {"fk_jac": 5304, "fk": 3792, "rnea": 9028, "bias": 9022, "crba_ltdl": 16691, "crba": 12921,
-                 "aba": 25231, "rnea_vjp": 22034, "aba_vjp": 43301, "osc": 31265, "rnea_ext": 12236,
-                 "aba_ext": 28439, "fk_jvp": 3635, "rnea_jvp": 20429, "aba_jvp": 41814},
+    "chain7": {"fk_jac": 748, "fk": 664, "rnea": 1683, "bias": 1683, "crba_ltdl": 1586, "crba": 1453,
+               "aba": 4073, "rnea_vjp": 4272, "aba_vjp": 5942, "osc": 8213, "rnea_ext": 2237,
+               "aba_ext": 4627, "fk_jvp": 593, "rnea_jvp": 4175, "aba_jvp": 5852},
+    "humanoid": {"fk_jac": 4685, "fk": 3173, "rnea": 7761, "bias": 7755, "crba_ltdl": 13474, "crba": 9704,
+                 "aba": 20316, "rnea_vjp": 19471, "aba_vjp": 36255, "osc": 24669, "rnea_ext": 10346,
+                 "aba_ext": 22901, "fk_jvp": 2584, "rnea_jvp": 17866, "aba_jvp": 34797},
 }
 # operational-space control task bodies (the last end frame of each model)
 OSC_TASK = {"chain7": 6, "humanoid": 29}

@@ -53,7 +53,7 @@ template <class Img>
 void count_stepback(const Img& M) {
   SV v{mk(0.1f, 0.2f, 0.3f), mk(0.4f, 0.5f, 0.6f)}, a = v, dv = v, da = v;
   g = Counts{};
-  jvp_step_back(M.body[M.nb - 1], CF(0.8f), CF(0.6f), CF(0.1f), CF(0.2f), CF(0.3f), CF(0.4f), CF(0.5f), v, a, dv, da);
+  jvp_step_back(M.body[M.nb - 1], CF(0.8f), CF(0.6f), CF(0.1f), CF(0.2f), CF(0.3f), CF(0.4f), CF(0.5f), v, a, dv, da, DhOn{});
   int n = 0;
   for (int s = (M.free_root ? 1 : 0); s < M.n_seg; ++s) n += M.seg_len[s] - 1;
   printf("  \"jvp_stepback\": {\"flops\": %lld, \"count\": %d},\n", 2 * g.fma + g.add + g.mul, n);
@@ -115,6 +115,29 @@ void count(const Img& M, int nf, const int* frames) {
   }
 }
 
+// The direct formulations that keep per-body state instead of recomputing it
+// (dyn.cuh, one thread per instance, no segments): the algorithm's own work,
+// the basis of the roofline where a kernel trades flops for registers.
+template <class T, class Img>
+void count_direct(const Img& M) {
+  int nq = M.nq, nv = M.nv;
+  std::vector<CF> q(nq, CF(0.3f)), qd(nv, CF(0.2f)), qdd(nv, CF(0.1f)), tau(nv, CF(0.5f)), gb(nv, CF(0.7f));
+  if (M.free_root) { q[3] = q[4] = q[5] = CF(0.f); q[6] = CF(1.f); }
+  std::vector<CF> o3(nv * nv + 64), o4(nv * (nv + 1) / 2 + 64), o5(nq + 8), o6(nv + 8), o7(nv + 8);
+  Col col{1, 0};
+  auto rep = [&](const char* name) {
+    printf("  \"%s\": {\"flops\": %lld},\n", name, 2 * g.fma + g.add + g.mul);
+    g = Counts{};
+  };
+  g = Counts{};
+  crba_one<T>(M, q.data(), o3.data(), o4.data(), col); rep("direct_crba_ltdl");
+  aba_one<T>(M, q.data(), qd.data(), tau.data(), o6.data(), col); rep("direct_aba");
+  rnea_vjp_one<T>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col);
+  rep("direct_rnea_vjp");
+  aba_vjp_one<T>(M, q.data(), qd.data(), tau.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col);
+  rep("direct_aba_vjp");
+}
+
 // The chain's adjoints run on the segment code (SegTopo<8, false>).
 template <class Img>
 void count_chain_vjp(const Img& M) {
@@ -167,11 +190,14 @@ int main(int argc, char** argv) {
   printf("{\n");
   if (hm.kind == kKindChain) {
     static ModelImage<7> img; hm.pack(&img); count<ChainTopo<7>>(img, nf, frames.data());
+    count_direct<ChainTopo<7>>(img);
     static ModelImage<8> img8; hm.pack(&img8); count_chain_vjp(img8);
   } else if (hm.free_root) {
     static ModelImage<64> img; hm.pack(&img); count<SegTopo<64, true>>(img, nf, frames.data());
+    count_direct<TreeTopo<64, true, true>>(img);
   } else {
     static ModelImage<64> img; hm.pack(&img); count<SegTopo<64, false>>(img, nf, frames.data());
+    count_direct<TreeTopo<64, false, true>>(img);
   }
   printf("  \"nb\": %d, \"nv\": %d\n}\n", hm.nb, hm.nv);
   return 0;

@@ -19,6 +19,7 @@ namespace frax {
 template <int N>
 struct ChainTopo {
   static constexpr int NBMAX = N;
+  static constexpr bool kDhRt = false;  // every body after the first is Rot_x
   static constexpr int NVMAX = N;
   static constexpr bool kFree = false;
   static constexpr bool kStatic = true;
@@ -31,9 +32,12 @@ struct ChainTopo {
   FD static int dparent(const Img&, int k) { return k - 1; }
 };
 
-template <int NBM, bool FREE>
+template <int NBM, bool FREE, bool DHRT = false>
 struct TreeTopo {
   static constexpr int NBMAX = NBM;
+  // the Rot_x form of a body's R is taken from b.dh at run time when set (the
+  // flop counter's direct formulations); the kernels keep the general form
+  static constexpr bool kDhRt = DHRT;
   static constexpr int NVMAX = NBM + (FREE ? 5 : 0);
   static constexpr bool kFree = FREE;
   static constexpr bool kStatic = false;
@@ -68,6 +72,14 @@ struct ColT {
   FD void out(float* __restrict__ p, int k, float v) const { p[k * ld + b] = v; }
 };
 using Col = ColT<true>;
+
+// Whether body i's R takes the Rot_x form here: always after the first body
+// of a chain (known once the loops are unrolled), from the image when the
+// topology asks for it, else never.
+template <class T, class Img>
+FD bool dh_of(const Img& M, int i) {
+  return T::kStatic ? i > 0 : (T::kDhRt && M.body[i].dh);
+}
 
 template <class GT>
 FD SV gravity_acc(const GT* g) { return SV{mk(0, 0, 0), mk(-g[0], -g[1], -g[2])}; }
@@ -121,14 +133,14 @@ FD void fk_one(const Img& M, const float* __restrict__ q, float* __restrict__ po
       pw[0] = P.r;
     } else {
       float s, c;
-      sincosf(col.in(q, iq_of<T>(i)), &s, &c);
+      sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &s, &c);
       float A[9];
       if (k < 0) {
 #pragma unroll
         for (int t = 0; t < 9; ++t) A[t] = b.R[t];
         pw[i] = mk(b.p[0], b.p[1], b.p[2]);
       } else {
-        mat_mul(Rw[k], b.R, A);
+        mat_mul_b(Rw[k], b, A, dh_of<T>(M, i));
         pw[i] = pw[k] + rot(Rw[k], mk(b.p[0], b.p[1], b.p[2]));
       }
 #pragma unroll
@@ -218,11 +230,11 @@ FD void rnea_one(const Img& M, const float* __restrict__ q, const float* __restr
       if (qdd) a[0] = a[0] + load6(qdd, 0, col);
     } else {
       const int k = T::parent(M, i);
-      sincosf(col.in(q, iq_of<T>(i)), &sq[i], &cq[i]);
+      sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
       const float qdi = col.in(qd, iv_of<T>(i));
       const float qddi = qdd ? col.in(qdd, iv_of<T>(i)) : 0.f;
-      SV vi = k < 0 ? szero() : mot_in(b, cq[i], sq[i], v[k]);
-      SV ai = mot_in(b, cq[i], sq[i], k < 0 ? ag : a[k]);
+      SV vi = k < 0 ? szero() : mot_in(b, cq[i], sq[i], v[k], dh_of<T>(M, i));
+      SV ai = mot_in(b, cq[i], sq[i], k < 0 ? ag : a[k], dh_of<T>(M, i));
       vi.w.z += qdi;
       ai.w.z += qddi;
       ai = ai + qdi * SV{mk(vi.w.y, -vi.w.x, 0.f), mk(vi.v.y, -vi.v.x, 0.f)};  // v x e qd
@@ -239,7 +251,7 @@ FD void rnea_one(const Img& M, const float* __restrict__ q, const float* __restr
     } else {
       col.out(tau, iv_of<T>(i), f[i].w.z);
       const int k = T::parent(M, i);
-      if (k >= 0) f[k] = f[k] + frc_out(M.body[i], cq[i], sq[i], f[i]);
+      if (k >= 0) f[k] = f[k] + frc_out(M.body[i], cq[i], sq[i], f[i], dh_of<T>(M, i));
     }
   }
 }
@@ -268,13 +280,13 @@ FD void crba_one(const Img& M, const float* __restrict__ q, float* __restrict__ 
   for (int i = 0; i < T::NBMAX; ++i) {
     if (i >= nb) break;
     Ic[i] = rbi_of(M.body[i]);
-    if (!(T::kFree && i == 0)) sincosf(col.in(q, iq_of<T>(i)), &sq[i], &cq[i]);
+    if (!(T::kFree && i == 0)) sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
   }
 #pragma unroll(T::kStatic ? T::NBMAX : 1)
   for (int i = T::NBMAX - 1; i >= 1; --i) {
     if (i >= nb) continue;
     const int k = T::parent(M, i);
-    if (k >= 0) Ic[k] = rbi_add(Ic[k], rbi_out(M.body[i], cq[i], sq[i], Ic[i]));
+    if (k >= 0) Ic[k] = rbi_add(Ic[k], rbi_out(M.body[i], cq[i], sq[i], Ic[i], dh_of<T>(M, i)));
   }
   auto put = [&](int r, int c, float val) {  // r >= c
     if (Mout) {
@@ -314,7 +326,7 @@ FD void crba_one(const Img& M, const float* __restrict__ q, float* __restrict__ 
     for (int step = 0; step < T::NBMAX; ++step) {
       const int k = T::parent(M, j);
       if (k < 0) break;
-      F = frc_out(M.body[j], cq[j], sq[j], F);
+      F = frc_out(M.body[j], cq[j], sq[j], F, dh_of<T>(M, j));
       j = k;
       done |= 1ull << j;
       if (T::kFree && j == 0) {
@@ -448,10 +460,10 @@ FD void aba_core(const Img& M, const float* __restrict__ q, const float* __restr
       cb[0] = szero();
     } else {
       const int k = T::parent(M, i);
-      sincosf(col.in(q, iq_of<T>(i)), &sq[i], &cq[i]);
+      sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
       if (VEL) {
         const float qdi = col.in(qd, iv_of<T>(i));
-        SV vi = k < 0 ? szero() : mot_in(b, cq[i], sq[i], v[k]);
+        SV vi = k < 0 ? szero() : mot_in(b, cq[i], sq[i], v[k], dh_of<T>(M, i));
         vi.w.z += qdi;
         v[i] = vi;
         cb[i] = qdi * SV{mk(vi.w.y, -vi.w.x, 0.f), mk(vi.v.y, -vi.v.x, 0.f)};
@@ -477,9 +489,9 @@ FD void aba_core(const Img& M, const float* __restrict__ q, const float* __restr
       AI Ia = IA[i];
       ai_rank1_sub(Ia, Ui, di);
       const SV pa = pA[i] + ai_mul(Ia, cb[i]) + (ui * di) * Ui;
-      ai_out(M.body[i], cq[i], sq[i], Ia);
+      ai_out(M.body[i], cq[i], sq[i], Ia, dh_of<T>(M, i));
       ai_add(IA[k], Ia);
-      pA[k] = pA[k] + frc_out(M.body[i], cq[i], sq[i], pa);
+      pA[k] = pA[k] + frc_out(M.body[i], cq[i], sq[i], pa, dh_of<T>(M, i));
     }
   }
 #pragma unroll(T::kStatic ? T::NBMAX : 1)
@@ -492,7 +504,7 @@ FD void aba_core(const Img& M, const float* __restrict__ q, const float* __restr
       out_at.root(a[0] - ap);
     } else {
       const int k = T::parent(M, i);
-      SV ap = mot_in(M.body[i], cq[i], sq[i], k < 0 ? ag : a[k]) + cb[i];
+      SV ap = mot_in(M.body[i], cq[i], sq[i], k < 0 ? ag : a[k], dh_of<T>(M, i)) + cb[i];
       const float qddi = (u[i] - dot(U[i], ap)) * Dinv[i];
       ap.w.z += qddi;
       a[i] = ap;
@@ -553,16 +565,16 @@ FD void rnea_vjp_core(const Img& M, const float* __restrict__ q, const float* __
       Fb[0] = gb_at.root();
     } else {
       const int k = T::parent(M, i);
-      sincosf(col.in(q, iq_of<T>(i)), &sq[i], &cq[i]);
+      sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
       const float qdi = col.in(qd, iv_of<T>(i));
-      SV vi = k < 0 ? szero() : mot_in(b, cq[i], sq[i], v[k]);
-      xa[i] = mot_in(b, cq[i], sq[i], k < 0 ? ag : a_prev[k]);
+      SV vi = k < 0 ? szero() : mot_in(b, cq[i], sq[i], v[k], dh_of<T>(M, i));
+      xa[i] = mot_in(b, cq[i], sq[i], k < 0 ? ag : a_prev[k], dh_of<T>(M, i));
       vi.w.z += qdi;
       v[i] = vi;
       ai = xa[i];
       ai.w.z += col.in(qdd, iv_of<T>(i));
       ai = ai + qdi * SV{mk(vi.w.y, -vi.w.x, 0.f), mk(vi.v.y, -vi.v.x, 0.f)};
-      SV fb = k < 0 ? szero() : mot_in(b, cq[i], sq[i], Fb[k]);
+      SV fb = k < 0 ? szero() : mot_in(b, cq[i], sq[i], Fb[k], dh_of<T>(M, i));
       fb.w.z += gb_at(i);
       Fb[i] = fb;
     }
@@ -590,9 +602,9 @@ FD void rnea_vjp_core(const Img& M, const float* __restrict__ q, const float* __
       sink(i, qb, qdb, qddb);
       const int k = T::parent(M, i);
       if (k >= 0) {
-        F[k] = F[k] + frc_out(b, cq[i], sq[i], F[i]);
-        ab[k] = ab[k] + frc_out(b, cq[i], sq[i], abi);
-        vb[k] = vb[k] + frc_out(b, cq[i], sq[i], vbi);
+        F[k] = F[k] + frc_out(b, cq[i], sq[i], F[i], dh_of<T>(M, i));
+        ab[k] = ab[k] + frc_out(b, cq[i], sq[i], abi, dh_of<T>(M, i));
+        vb[k] = vb[k] + frc_out(b, cq[i], sq[i], vbi, dh_of<T>(M, i));
       }
     }
   }

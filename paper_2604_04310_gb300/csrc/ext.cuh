@@ -71,12 +71,12 @@ FD void ext_tau(const Img& M, const float* __restrict__ q, const float* __restri
           const BodyImage& b = M.body[i];
           o = o + rot(E, mk(b.p[0], b.p[1], b.p[2]));
           float ER[9];
-          mat_mul(E, b.R, ER);
+          mat_mul_b(E, b, ER, k > 0);
           z[k] = mk(ER[2], ER[5], ER[8]);
           p[k] = o;
           if (kind == kActOpen && k == len - 1) {
             float sn, cs;
-            sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
+            sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn, &cs);
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
               const float x = ER[3 * r], y = ER[3 * r + 1];
@@ -87,7 +87,7 @@ FD void ext_tau(const Img& M, const float* __restrict__ q, const float* __restri
             bp[i] = o;
           } else if (k < len - 1) {
             float sn, cs;
-            sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
+            sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn, &cs);
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
               const float x = ER[3 * r], y = ER[3 * r + 1];

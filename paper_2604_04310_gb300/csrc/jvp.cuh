@@ -18,8 +18,9 @@ namespace frax {
 
 // One step back through joint b: from the child's v, a, dv, da to the
 // parent's, all recomputed rather than stored (X v_p = v - e_z qd, ...).
+template <class DH>
 FD void jvp_step_back(const BodyImage& b, float cs, float sn, float qdi, float qddi, float dqi, float dqdi,
-                      float dqddi, SV& v, SV& a, SV& dv, SV& da) {
+                      float dqddi, SV& v, SV& a, SV& dv, SV& da, DH dh) {
   SV Xv = v;
   Xv.w.z -= qdi;
   SV Xa = a - ez_velprod(v, qdi);
@@ -28,10 +29,10 @@ FD void jvp_step_back(const BodyImage& b, float cs, float sn, float qdi, float q
   Xdv.w.z -= dqdi;
   SV Xda = da - ez_velprod(dv, qdi) - ez_velprod(v, dqdi) + dqi * ez_crm(Xa);
   Xda.w.z -= dqddi;
-  v = mot_out(b, cs, sn, Xv);
-  a = mot_out(b, cs, sn, Xa);
-  dv = mot_out(b, cs, sn, Xdv);
-  da = mot_out(b, cs, sn, Xda);
+  v = mot_out(b, cs, sn, Xv, dh);
+  a = mot_out(b, cs, sn, Xa, dh);
+  dv = mot_out(b, cs, sn, Xdv, dh);
+  da = mot_out(b, cs, sn, Xda, dh);
 }
 
 template <class T, class Img, class C, class Sink>
@@ -82,22 +83,24 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
       for (int k = 0; k < len; ++k) {
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
-        float sn, cs;
-        sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
-        sc[i] = cs;
-        ss[i] = sn;
-        const int iv = iv_of<T>(i);
-        const float qdi = col.in(qd, iv), dqi = col.in(dq, iv), dqdi = col.in(dqd, iv);
-        const SV Xv = mot_in(b, cs, sn, v);
-        const SV Xa = mot_in(b, cs, sn, a);
-        dv = mot_in(b, cs, sn, dv) - dqi * ez_crm(Xv);
-        dv.w.z += dqdi;
-        v = Xv;
-        v.w.z += qdi;
-        da = mot_in(b, cs, sn, da) - dqi * ez_crm(Xa) + ez_velprod(dv, qdi) + ez_velprod(v, dqdi);
-        da.w.z += in0(dqdd, iv);
-        a = Xa + ez_velprod(v, qdi);
-        a.w.z += in0(qdd, iv);
+        with_dh(b.dh, [&](auto dh) {
+          float sn, cs;
+          sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+          sc[i] = cs;
+          ss[i] = sn;
+          const int iv = iv_of<T>(i);
+          const float qdi = col.in(qd, iv), dqi = col.in(dq, iv), dqdi = col.in(dqd, iv);
+          const SV Xv = mot_in(b, cs, sn, v, dh);
+          const SV Xa = mot_in(b, cs, sn, a, dh);
+          dv = mot_in(b, cs, sn, dv, dh) - dqi * ez_crm(Xv);
+          dv.w.z += dqdi;
+          v = Xv;
+          v.w.z += qdi;
+          da = mot_in(b, cs, sn, da, dh) - dqi * ez_crm(Xa) + ez_velprod(dv, qdi) + ez_velprod(v, dqdi);
+          da.w.z += in0(dqdd, iv);
+          a = Xa + ez_velprod(v, qdi);
+          a.w.z += in0(qdd, iv);
+        });
       }
       if (kind == kActOpen) {
         bv[last] = v;
@@ -120,17 +123,19 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
     for (int k = len - 1; k >= 0; --k) {
       const int i = M.order[st + k];
       const BodyImage& b = M.body[i];
-      const RBI I = rbi_of(b);
-      const float cs = sc[i], sn = ss[i];
-      const int iv = iv_of<T>(i);
-      const float qdi = col.in(qd, iv), dqi = col.in(dq, iv), dqdi = col.in(dqd, iv);
-      const SV Iv = rbi_mul(I, v);
-      const SV F = rbi_mul(I, a) + crf(v, Iv) + Fc;
-      const SV dF = rbi_mul(I, da) + crf(dv, Iv) + crf(v, rbi_mul(I, dv)) + dFc;
-      sink(i, F.w.z, dF.w.z);
-      Fc = frc_out(b, cs, sn, F);
-      dFc = frc_out(b, cs, sn, dF + dqi * ez_crf(F));
-      if (k > 0) jvp_step_back(b, cs, sn, qdi, in0(qdd, iv), dqi, dqdi, in0(dqdd, iv), v, a, dv, da);
+      with_dh(b.dh, [&](auto dh) {
+        const RBI I = rbi_of(b);
+        const float cs = sc[i], sn = ss[i];
+        const int iv = iv_of<T>(i);
+        const float qdi = col.in(qd, iv), dqi = col.in(dq, iv), dqdi = col.in(dqd, iv);
+        const SV Iv = rbi_mul(I, v);
+        const SV F = rbi_mul(I, a) + crf(v, Iv) + Fc;
+        const SV dF = rbi_mul(I, da) + crf(dv, Iv) + crf(v, rbi_mul(I, dv)) + dFc;
+        sink(i, F.w.z, dF.w.z);
+        Fc = frc_out(b, cs, sn, F, dh);
+        dFc = frc_out(b, cs, sn, dF + dqi * ez_crf(F), dh);
+        if (k > 0) jvp_step_back(b, cs, sn, qdi, in0(qdd, iv), dqi, dqdi, in0(dqdd, iv), v, a, dv, da, dh);
+      });
     }
     const int p = M.seg_parent[s];
     if (p >= 0) {
@@ -229,11 +234,13 @@ FD void fk_jvp_seg(const Img& M, const float* __restrict__ q, const float* __res
       const int i = M.order[st + k];
       const BodyImage& b = M.body[i];
       float sn, cs;
-      sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
-      v = mot_in(b, cs, sn, v);
-      v.w.z += col.in(dq, iv_of<T>(i));
+      sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
       float ER[9];
-      mat_mul(E, b.R, ER);
+      with_dh(b.dh, [&](auto dh) {
+        v = mot_in(b, cs, sn, v, dh);
+        mat_mul_b(E, b, ER, dh);
+      });
+      v.w.z += col.in(dq, iv_of<T>(i));
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         const float x = ER[3 * r], y = ER[3 * r + 1];

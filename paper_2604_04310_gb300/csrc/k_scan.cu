@@ -60,11 +60,11 @@ __device__ __forceinline__ SE3 joint_tf(const ModelImage<64>& M, int i, const fl
   }
   const BodyImage& b = M.body[i];
   float sn, cs;
-  sincosf(col.in(q, FREE ? i + 6 : i), &sn, &cs);
+  sincosf(col.in(q, FREE ? i + 6 : i) + b.th0, &sn, &cs);
   SE3 t;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    const float x = b.R[3 * r], y = b.R[3 * r + 1];
+    const float x = b.R[3 * r], y = b.R[3 * r + 1];  // R Rot_z(q + th0)
     t.R[3 * r] = fmaf(cs, x, sn * y);
     t.R[3 * r + 1] = fmaf(-sn, x, cs * y);
     t.R[3 * r + 2] = b.R[3 * r + 2];

@@ -56,6 +56,20 @@ M3 frame_with_z(const double a[3]) {
   return Q;
 }
 
+M3 rot_z(double t) {
+  M3 R = identity();
+  R(0, 0) = std::cos(t); R(0, 1) = -std::sin(t);
+  R(1, 0) = std::sin(t); R(1, 1) = std::cos(t);
+  return R;
+}
+
+M3 rot_x(double t) {
+  M3 R = identity();
+  R(1, 1) = std::cos(t); R(1, 2) = -std::sin(t);
+  R(2, 1) = std::sin(t); R(2, 2) = std::cos(t);
+  return R;
+}
+
 bool finite_all(const double* p, int n) {
   for (int k = 0; k < n; ++k)
     if (!std::isfinite(p[k])) return false;
@@ -129,6 +143,33 @@ std::string build_model(int n, const int32_t* parent, const int32_t* joint_type,
     double au[3] = {a[0] / na, a[1] / na, a[2] / na};
     Q[i] = frame_with_z(au);
   }
+  // Denavit-Hartenberg turn of the internal frames: a revolute body k whose
+  // only child c is revolute turns its frame about z by phi_k so that its x
+  // lies on the common normal of the two axes. With the child's axis in k's
+  // frame u = Rot_z(g1) Rot_x(b) e_z = (sin b sin g1, -sin b cos g1, cos b),
+  // phi_k = g1; c's constant rotation becomes Rot_x(b) Rot_z(th0).
+  std::vector<int> nchild(n, 0), only_child(n, -1);
+  for (int i = 0; i < n; ++i)
+    if (parent[i] >= 0) {
+      nchild[parent[i]]++;
+      only_child[parent[i]] = i;
+    }
+  std::vector<int> dh_child(n, -1);
+  for (int k = 0; k < n; ++k) {
+    const int c = only_child[k];
+    if (nchild[k] != 1 || joint_type[k] == 1 || joint_type[c] == 1) continue;
+    dh_child[k] = c;
+    M3 RTc{};
+    for (int t = 0; t < 9; ++t) RTc.a[t] = placement[12 * c + t];
+    const M3 Rc = mul(mul(transpose(Q[k]), RTc), Q[c]);
+    const double ux = Rc(0, 2), uy = Rc(1, 2);
+    const double phi = std::hypot(ux, uy) > 1e-12 ? std::atan2(ux, -uy) : 0.0;
+    Q[k] = mul(Q[k], rot_z(phi));
+  }
+  std::vector<char> is_dh(n, 0);
+  for (int k = 0; k < n; ++k)
+    if (dh_child[k] >= 0) is_dh[dh_child[k]] = 1;
+
   m.bodies.resize(n);
   for (int i = 0; i < n; ++i) {
     M3 RT{};
@@ -161,11 +202,32 @@ std::string build_model(int n, const int32_t* parent, const int32_t* joint_type,
     BodyImage& b = m.bodies[i];
     int k = parent[i];
     M3 Qp = k >= 0 ? Q[k] : identity();
-    M3 Rint = joint_type[i] == 1 ? RT : mul(mul(transpose(Qp), RT), Q[i]);
+    M3 Rint = joint_type[i] == 1 ? RT : mul(mul(transpose(Qp), RT), Q[i]);  // before any dh rewrite
     double pint[3];
     for (int r = 0; r < 3; ++r) {
       pint[r] = joint_type[i] == 1 ? pT[r]
                                    : Qp(0, r) * pT[0] + Qp(1, r) * pT[1] + Qp(2, r) * pT[2];
+    }
+    b.dh = 0;
+    b.ca = 1.f;
+    b.sa = 0.f;
+    b.th0 = 0.f;
+    if (is_dh[i]) {
+      // Rint = Rot_x(alpha) Rot_z(th0) =
+      //   [[ct, -st, 0], [ca st, ca ct, -sa], [sa st, sa ct, ca]]
+      const double alpha = std::atan2(-Rint(1, 2), Rint(2, 2));
+      const double th0 = std::atan2(-Rint(0, 1), Rint(0, 0));
+      const M3 Rdh = mul(rot_x(alpha), rot_z(th0));
+      double res = 0;
+      for (int t = 0; t < 9; ++t) res = std::fmax(res, std::fabs(Rdh.a[t] - Rint.a[t]));
+      // the turn above makes the child's axis (0, -sin a, cos a), so this
+      // form is exact; chain kernels rely on it for every body after the first
+      if (!(res < 1e-9)) return fmt("body %d: internal Denavit-Hartenberg frame failed", i);
+      b.dh = 1;
+      b.ca = static_cast<float>(std::cos(alpha));
+      b.sa = static_cast<float>(std::sin(alpha));
+      b.th0 = static_cast<float>(th0);
+      Rint = rot_x(alpha);
     }
     for (int t = 0; t < 9; ++t) b.R[t] = static_cast<float>(Rint.a[t]);
     for (int t = 0; t < 3; ++t) b.p[t] = static_cast<float>(pint[t]);
@@ -253,6 +315,10 @@ std::string build_model(int n, const int32_t* parent, const int32_t* joint_type,
   bool chain = !m.free_root;
   for (int i = 0; i < n; ++i) chain = chain && parent[i] == i - 1;
   m.kind = (chain && n == 7) ? kKindChain : kKindTree;
+  // kernels that unroll a segment take the Rot_x form for every body after
+  // the segment's first: each such body is the only child of a revolute body
+  for (int i = 0; i < n; ++i)
+    if (m.pos_of[i] > 0 && !m.bodies[i].dh) return fmt("body %d: segment body without a Rot_x frame", i);
   *out = std::move(m);
   return "";
 }

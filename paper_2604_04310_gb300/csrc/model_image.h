@@ -11,8 +11,16 @@ constexpr int kMaxDofs = kMaxBodies + 5;
 
 // One body in its *internal* frame: the user's body frame rotated by a
 // constant Q_i chosen so that the revolute joint axis becomes local z.
-// Then ^parent'R_i' = R * Rot_z(q_i), the motion subspace is e_z, and
+// Then ^parent'R_i' = R * Rot_z(q_i + th0), the motion subspace is e_z, and
 // tau_i is the z component of the body's joint moment.
+//
+// The rotation of an internal frame about its own z is free. A body with a
+// single (revolute) child turns its x onto the common normal of its axis and
+// the child's (the Denavit-Hartenberg choice); the child's R is then a
+// rotation about x alone, R = Rot_x(alpha), and the rest of the relative
+// rotation, Rot_z(th0), joins the joint angle. Kernels transform through
+// such a body with the sparse form (dh != 0): a third of the flops of a
+// general R.
 struct BodyImage {
   float R[9];  // constant rotation child' -> parent' (row-major); for a free
                // root: the placement rotation
@@ -22,6 +30,9 @@ struct BodyImage {
   float h[3];  // first moment m*c in internal coordinates
   float I[6];  // rotational inertia about the body origin, internal coords:
                // xx, yy, zz, xy, xz, yz
+  float ca, sa;  // cos, sin of alpha when R = Rot_x(alpha)
+  float th0;     // joint angle offset (0 unless dh)
+  int32_t dh;    // R is Rot_x(alpha)
 };
 
 // Segments: maximal runs of bodies in which every body but the last has

@@ -144,7 +144,7 @@ FD AI osc_inertias(const Img& M, const float* __restrict__ q, uint64_t path, PL&
       const int i = M.order[st + k];
       const BodyImage& b = M.body[i];
       float sn, cs;
-      sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
+      sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
       const SV U = ai_col_z(IA);
       const float dinv = 1.f / U.w.z;
       if ((path >> i) & 1ull) {
@@ -153,7 +153,7 @@ FD AI osc_inertias(const Img& M, const float* __restrict__ q, uint64_t path, PL&
         P.at(i, 6) = dinv;
       }
       ai_rank1_sub(IA, U, dinv);
-      ai_out(b, cs, sn, IA);
+      with_dh(b.dh, [&](auto dh) { ai_out(b, cs, sn, IA, dh); });
       if (k > 0) {
         AI Ip = ai_of(rbi_of(M.body[M.order[st + k - 1]]));
         ai_add(Ip, IA);
@@ -208,35 +208,37 @@ FD OscPath osc_path(const Img& M, const float* __restrict__ q, const float* __re
     const int j = low_bit(rest);
     const BodyImage& b = M.body[j];
     float sn, cs;
-    sincosf(col.in(q, iq_of<T>(j)), &sn, &cs);
+    sincosf(col.in(q, iq_of<T>(j)) + b.th0, &sn, &cs);
     const float qdj = col.in(qd, iv_of<T>(j));
-    // W = X Omega_p X^T
-    ai_in(b, cs, sn, o.Om);
-    // Omega = P W P^T + e_z e_z^T / D, P = 1 - e_z u^T, u = U / D
-    const float dinv = P.at(j, 6);
-    const SV u{dinv * mk(P.at(j, 0), P.at(j, 1), P.at(j, 2)), dinv * mk(P.at(j, 3), P.at(j, 4), P.at(j, 5))};
-    const SV y = ai_mul(o.Om, SV{u.v, u.w});  // W u as [linear; angular]
-    const float uWu = dot(u.w, y.v) + dot(u.v, y.w);
-    o.Om.B[2] -= y.w.x;
-    o.Om.B[5] -= y.w.y;
-    o.Om.B[8] -= y.w.z;
-    o.Om.C[4] -= y.v.x;
-    o.Om.C[5] -= y.v.y;
-    o.Om.C[2] += fmaf(-2.f, y.v.z, uWu + dinv);
-    // velocity and velocity-product acceleration
-    o.v = mot_in(b, cs, sn, o.v);
-    o.v.w.z += qdj;
-    o.a = mot_in(b, cs, sn, o.a) + ez_velprod(o.v, qdj);
-    // E <- E R Rot_z(q)
-    float ER[9];
-    mat_mul(o.E, b.R, ER);
+    with_dh(b.dh, [&](auto dh) {
+      // W = X Omega_p X^T
+      ai_in(b, cs, sn, o.Om, dh);
+      // Omega = P W P^T + e_z e_z^T / D, P = 1 - e_z u^T, u = U / D
+      const float dinv = P.at(j, 6);
+      const SV u{dinv * mk(P.at(j, 0), P.at(j, 1), P.at(j, 2)), dinv * mk(P.at(j, 3), P.at(j, 4), P.at(j, 5))};
+      const SV y = ai_mul(o.Om, SV{u.v, u.w});  // W u as [linear; angular]
+      const float uWu = dot(u.w, y.v) + dot(u.v, y.w);
+      o.Om.B[2] -= y.w.x;
+      o.Om.B[5] -= y.w.y;
+      o.Om.B[8] -= y.w.z;
+      o.Om.C[4] -= y.v.x;
+      o.Om.C[5] -= y.v.y;
+      o.Om.C[2] += fmaf(-2.f, y.v.z, uWu + dinv);
+      // velocity and velocity-product acceleration
+      o.v = mot_in(b, cs, sn, o.v, dh);
+      o.v.w.z += qdj;
+      o.a = mot_in(b, cs, sn, o.a, dh) + ez_velprod(o.v, qdj);
+      // E <- E R Rot_z(q)
+      float ER[9];
+      mat_mul_b(o.E, b, ER, dh);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const float x = ER[3 * r], z = ER[3 * r + 1];
-      o.E[3 * r] = fmaf(cs, x, sn * z);
-      o.E[3 * r + 1] = fmaf(-sn, x, cs * z);
-      o.E[3 * r + 2] = ER[3 * r + 2];
-    }
+      for (int r = 0; r < 3; ++r) {
+        const float x = ER[3 * r], z = ER[3 * r + 1];
+        o.E[3 * r] = fmaf(cs, x, sn * z);
+        o.E[3 * r + 1] = fmaf(-sn, x, cs * z);
+        o.E[3 * r + 2] = ER[3 * r + 2];
+      }
+    });
   }
   return o;
 }

@@ -84,12 +84,12 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
         if (k < len) {
           const int i = M.order[st + k];
           const BodyImage& b = M.body[i];
-          sincosf(col.in(q, iq_of<T>(i)), &sn[k], &cc[k]);
+          sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn[k], &cc[k]);
           const float qdi = col.in(qd, iv_of<T>(i));
           const float qddi = qdd ? col.in(qdd, iv_of<T>(i)) : 0.f;
-          v = mot_in(b, cc[k], sn[k], v);
+          v = mot_in(b, cc[k], sn[k], v, k > 0);
           v.w.z += qdi;
-          a = mot_in(b, cc[k], sn[k], a);
+          a = mot_in(b, cc[k], sn[k], a, k > 0);
           a.w.z += qddi;
           a = a + ez_velprod(v, qdi);
           const RBI I = rbi_of(b);
@@ -131,7 +131,7 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
         const int i = M.order[st + k];
         F = F + f[k];
         col.out(tau, iv_of<T>(i), F.w.z);
-        F = frc_out(M.body[i], cc[k], sn[k], F);
+        F = frc_out(M.body[i], cc[k], sn[k], F, k > 0);
       }
     }
     const int p = M.seg_parent[s];
@@ -201,10 +201,13 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
 #pragma unroll 1
         for (int k = 0; k < len; ++k) {
           const int i = M.order[st + k];
-          float sn, cs;
-          sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
-          vv = mot_in(M.body[i], cs, sn, vv);
-          vv.w.z += col.in(qd, iv_of<T>(i));
+          const BodyImage& b = M.body[i];
+          with_dh(b.dh, [&](auto dh) {
+            float sn, cs;
+            sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+            vv = mot_in(b, cs, sn, vv, dh);
+            vv.w.z += col.in(qd, iv_of<T>(i));
+          });
         }
       }
       vtip = vv;
@@ -223,13 +226,13 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
     const bool closing = kind == kActClose;
 #pragma unroll 1
     for (int k = len - 1; k >= 0; --k) {
-      {
+      with_dh(M.body[M.order[st + k]].dh, [&](auto dh) {
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
         const RBI Ib = rbi_of(b);
         const SV vk = vtip;  // velocity of body i, stepped back from the segment's tip
         float sk, ck;
-        sincosf(col.in(q, iq_of<T>(i)), &sk, &ck);
+        sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sk, &ck);
         AI IA = ai_of(Ib);
         SV pAt = szero();
         SV cb = szero();
@@ -261,14 +264,14 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         Ia = IA;
         ai_rank1_sub(Ia, U, dinv);
         pa = pAt + ai_mul(Ia, cb) + (u * dinv) * U;
-        ai_out(b, ck, sk, Ia);
-        pa = frc_out(b, ck, sk, pa);
+        ai_out(b, ck, sk, Ia, dh);
+        pa = frc_out(b, ck, sk, pa, dh);
         if (VEL && k > 0) {
           SV vp = vk;
           vp.w.z -= col.in(qd, iv_of<T>(i));
-          vtip = mot_out(b, ck, sk, vp);
+          vtip = mot_out(b, ck, sk, vp, dh);
         }
-      }
+      });
     }
     const int p = M.seg_parent[s];
     if (p >= 0) {
@@ -285,24 +288,24 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
     SV vv = (!VEL || p < 0) ? szero() : bv[p];
 #pragma unroll 1
     for (int k = 0; k < len; ++k) {
-      {
+      with_dh(M.body[M.order[st + k]].dh, [&](auto dh) {
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
         float sn, cs;
-        sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
+        sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
         SV cb = szero();
         if (VEL) {
           const float qdi = col.in(qd, iv_of<T>(i));
-          vv = mot_in(b, cs, sn, vv);
+          vv = mot_in(b, cs, sn, vv, dh);
           vv.w.z += qdi;
           cb = ez_velprod(vv, qdi);
         }
-        a = mot_in(b, cs, sn, a) + cb;
+        a = mot_in(b, cs, sn, a, dh) + cb;
         const SV U{mk(P.at(i, 0), P.at(i, 1), P.at(i, 2)), mk(P.at(i, 3), P.at(i, 4), P.at(i, 5))};
         const float x = (P.at(i, 7) - dot(U, a)) * P.at(i, 6);
         a.w.z += x;
         out_at(i, x);
-      }
+      });
     }
     bA[M.order[st + len - 1]] = a;
   }
@@ -446,7 +449,7 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
 #pragma unroll 1
       for (int k = 0; k < len; ++k) {
         const int i = M.order[st + k];
-        sincosf(col.in(q, iq_of<T>(i)), &ss[i], &sc[i]);
+        sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &ss[i], &sc[i]);
       }
       if (kind == kActOpen) {
         ICa[last] = rzero;
@@ -569,9 +572,9 @@ FD void fk_seg(const Img& M, const float* __restrict__ q, float* __restrict__ po
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
         float sn, cs;
-        sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
+        sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
         float A[9];
-        mat_mul(R, b.R, A);
+        with_dh(b.dh, [&](auto dh) { mat_mul_b(R, b, A, dh); });
         p = p + rot(R, mk(b.p[0], b.p[1], b.p[2]));
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -627,7 +630,10 @@ FD void fk_seg(const Img& M, const float* __restrict__ q, float* __restrict__ po
 // a_parent = X^-1 (a - e qdd - v x e qd), Fb_parent = X^-1 (Fb - e gbar)),
 // and the body force is recomputed; only segment tips and the accumulated
 // adjoints handed to branch bodies are kept per body.
-template <class T, class Img, class Seed, class Sink, class C>
+// With SPARSE false every joint takes the general form: one copy of each
+// loop body (the chain ABA adjoint, whose kernel also holds the factor solve,
+// runs faster so).
+template <class T, class Img, class Seed, class Sink, class C, bool SPARSE = true>
 FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
                      const float* __restrict__ qdd, const Seed& gb_at, const Sink& sink, const C& col) {
   constexpr int NB = T::NBMAX;
@@ -670,18 +676,20 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
       for (int k = 0; k < len; ++k) {
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
-        float sn, cs;
-        sincosf(col.in(q, iq_of<T>(i)), &sn, &cs);
-        sc[i] = cs;
-        ss[i] = sn;
-        const float qdi = col.in(qd, iv_of<T>(i));
-        v = mot_in(b, cs, sn, v);
-        v.w.z += qdi;
-        a = mot_in(b, cs, sn, a);
-        a.w.z += col.in(qdd, iv_of<T>(i));
-        a = a + ez_velprod(v, qdi);
-        Fb = mot_in(b, cs, sn, Fb);
-        Fb.w.z += gb_at(i);
+        with_dh(SPARSE && b.dh, [&](auto dh) {
+          float sn, cs;
+          sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+          sc[i] = cs;
+          ss[i] = sn;
+          const float qdi = col.in(qd, iv_of<T>(i));
+          v = mot_in(b, cs, sn, v, dh);
+          v.w.z += qdi;
+          a = mot_in(b, cs, sn, a, dh);
+          a.w.z += col.in(qdd, iv_of<T>(i));
+          a = a + ez_velprod(v, qdi);
+          Fb = mot_in(b, cs, sn, Fb, dh);
+          Fb.w.z += gb_at(i);
+        });
       }
       if (kind == kActOpen) {
         bv[last] = v;
@@ -703,28 +711,30 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
     for (int k = len - 1; k >= 0; --k) {
       const int i = M.order[st + k];
       const BodyImage& b = M.body[i];
-      const RBI I = rbi_of(b);
-      const float cs = sc[i], sn = ss[i];
-      const float qdi = col.in(qd, iv_of<T>(i));
-      SV xa = a - ez_velprod(v, qdi);
-      xa.w.z -= col.in(qdd, iv_of<T>(i));
-      const SV F = body_force(I, v, a) + Fc;
-      const SV ab = rbi_mul(I, Fb) + abc;
-      const SV vb = vbc - crf(Fb, rbi_mul(I, v)) - rbi_mul(I, crm(v, Fb)) + qdi * ez_crf(ab);
-      sink(i, dot(Fb, ez_crf(F)) - dot(ab, ez_crm(xa)) - dot(vb, ez_crm(v)), vb.w.z - dot(ab, ez_crm(v)),
-           ab.w.z);
-      Fc = frc_out(b, cs, sn, F);
-      abc = frc_out(b, cs, sn, ab);
-      vbc = frc_out(b, cs, sn, vb);
-      if (k > 0) {
-        SV vp = v;
-        vp.w.z -= qdi;
-        v = mot_out(b, cs, sn, vp);
-        a = mot_out(b, cs, sn, xa);
-        SV Fp = Fb;
-        Fp.w.z -= gb_at(i);
-        Fb = mot_out(b, cs, sn, Fp);
-      }
+      with_dh(SPARSE && b.dh, [&](auto dh) {
+        const RBI I = rbi_of(b);
+        const float cs = sc[i], sn = ss[i];
+        const float qdi = col.in(qd, iv_of<T>(i));
+        SV xa = a - ez_velprod(v, qdi);
+        xa.w.z -= col.in(qdd, iv_of<T>(i));
+        const SV F = body_force(I, v, a) + Fc;
+        const SV ab = rbi_mul(I, Fb) + abc;
+        const SV vb = vbc - crf(Fb, rbi_mul(I, v)) - rbi_mul(I, crm(v, Fb)) + qdi * ez_crf(ab);
+        sink(i, dot(Fb, ez_crf(F)) - dot(ab, ez_crm(xa)) - dot(vb, ez_crm(v)), vb.w.z - dot(ab, ez_crm(v)),
+             ab.w.z);
+        Fc = frc_out(b, cs, sn, F, dh);
+        abc = frc_out(b, cs, sn, ab, dh);
+        vbc = frc_out(b, cs, sn, vb, dh);
+        if (k > 0) {
+          SV vp = v;
+          vp.w.z -= qdi;
+          v = mot_out(b, cs, sn, vp, dh);
+          a = mot_out(b, cs, sn, xa, dh);
+          SV Fp = Fb;
+          Fp.w.z -= gb_at(i);
+          Fb = mot_out(b, cs, sn, Fp, dh);
+        }
+      });
     }
     const int p = M.seg_parent[s];
     if (p >= 0) {
@@ -774,17 +784,17 @@ FD void chain_minv(const Img& M, const float* __restrict__ q, const G& g, float*
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     Ic[i] = rbi_of(M.body[i]);
-    sincosf(col.in(q, i), &sq[i], &cq[i]);
+    sincosf(col.in(q, i) + M.body[i].th0, &sq[i], &cq[i]);
   }
 #pragma unroll
-  for (int i = N - 1; i >= 1; --i) Ic[i - 1] = rbi_add(Ic[i - 1], rbi_out(M.body[i], cq[i], sq[i], Ic[i]));
+  for (int i = N - 1; i >= 1; --i) Ic[i - 1] = rbi_add(Ic[i - 1], rbi_out(M.body[i], cq[i], sq[i], Ic[i], true));
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     SV F{mk(Ic[i].xz, Ic[i].yz, Ic[i].zz), mk(-Ic[i].h.y, Ic[i].h.x, 0.f)};
     H[MSink::tri(i, i)] = F.w.z;
 #pragma unroll
     for (int j = i; j >= 1; --j) {
-      F = frc_out(M.body[j], cq[j], sq[j], F);
+      F = frc_out(M.body[j], cq[j], sq[j], F, true);
       H[MSink::tri(i, j - 1)] = F.w.z;
     }
   }
@@ -827,7 +837,8 @@ FD void aba_vjp_chain_one(const Img& M, const float* q, const float* qd, const f
 #pragma unroll
     for (int k = 0; k < N; ++k) col.out(taubar, k, w.x[k]);
   }
-  rnea_vjp_seg<S>(M, q, qd, qdd, w, vjp_sink<S>(M, q, qbar, qdbar, nullptr, -1.f, col), col);
+  const auto sink = vjp_sink<S>(M, q, qbar, qdbar, nullptr, -1.f, col);
+  rnea_vjp_seg<S, Img, LocalVec<S>, decltype(sink), C, false>(M, q, qd, qdd, w, sink, col);
 }
 
 }  // namespace frax

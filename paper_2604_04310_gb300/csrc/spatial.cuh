@@ -76,24 +76,67 @@ FD void mat_mul(const AT* A, const BT* B, float* C) {
       C[3 * r + c] = fmaf(A[3 * r], B[c], fmaf(A[3 * r + 1], B[3 + c], A[3 * r + 2] * B[6 + c]));
 }
 
+// --- a body's constant rotation R -------------------------------------------
+// Compile-time forms of the dh flag below. A loop over bodies whose forms are
+// only known at run time writes its body as a generic lambda and runs it
+// through with_dh: one specialised copy per form behind one uniform branch,
+// instead of a branch in every transform.
+struct DhOn {
+  FD constexpr operator bool() const { return true; }
+};
+struct DhOff {
+  FD constexpr operator bool() const { return false; }
+};
+template <class F>
+FD void with_dh(bool dh, const F& f) {
+  if (dh) f(DhOn{});
+  else f(DhOff{});
+}
+// With dh (the caller knows R = Rot_x(alpha), see BodyImage) the sparse form,
+// else the general one; callers pass a value the compiler can fold (a loop
+// index after unrolling), so each call site keeps one form.
+FD V3 rot_b(const BodyImage& b, V3 a, bool dh = false) {  // R a
+  if (dh) return mk(a.x, fmaf(b.ca, a.y, -b.sa * a.z), fmaf(b.sa, a.y, b.ca * a.z));
+  return rot(b.R, a);
+}
+FD V3 rotT_b(const BodyImage& b, V3 a, bool dh = false) {  // R^T a
+  if (dh) return mk(a.x, fmaf(b.ca, a.y, b.sa * a.z), fmaf(-b.sa, a.y, b.ca * a.z));
+  return rotT(b.R, a);
+}
+// C = E R (E row-major)
+FD void mat_mul_b(const float* E, const BodyImage& b, float* C, bool dh = false) {
+  if (dh) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float y = E[3 * r + 1], z = E[3 * r + 2];
+      C[3 * r] = E[3 * r];
+      C[3 * r + 1] = fmaf(b.ca, y, b.sa * z);
+      C[3 * r + 2] = fmaf(-b.sa, y, b.ca * z);
+    }
+    return;
+  }
+  mat_mul(E, b.R, C);
+}
+
 // --- joint transforms (internal frames) -------------------------------------
-// A revolute body i sits at ^parent'T_i' = (R Rot_z(q), p) with R, p constant.
+// A revolute body i sits at ^parent'T_i' = (R Rot_z(q + th0), p) with R, p
+// constant; (c, s) below are cos and sin of q + th0.
 // Motion vectors: parent' -> child' coordinates.
-FD SV mot_in(const BodyImage& b, float c, float s, const SV& m) {
+FD SV mot_in(const BodyImage& b, float c, float s, const SV& m, bool dh = false) {
   V3 p = mk(b.p[0], b.p[1], b.p[2]);
-  return SV{rotzT(c, s, rotT(b.R, m.w)), rotzT(c, s, rotT(b.R, m.v - cross(p, m.w)))};
+  return SV{rotzT(c, s, rotT_b(b, m.w, dh)), rotzT(c, s, rotT_b(b, m.v - cross(p, m.w), dh))};
 }
 // Force vectors: child' -> parent' coordinates (the transpose of mot_in).
-FD SV frc_out(const BodyImage& b, float c, float s, const SV& f) {
+FD SV frc_out(const BodyImage& b, float c, float s, const SV& f, bool dh = false) {
   V3 p = mk(b.p[0], b.p[1], b.p[2]);
-  V3 fl = rot(b.R, rotz(c, s, f.v));
-  return SV{rot(b.R, rotz(c, s, f.w)) + cross(p, fl), fl};
+  V3 fl = rot_b(b, rotz(c, s, f.v), dh);
+  return SV{rot_b(b, rotz(c, s, f.w), dh) + cross(p, fl), fl};
 }
 // Motion vectors child' -> parent' (inverse of mot_in); used by adjoints.
-FD SV mot_out(const BodyImage& b, float c, float s, const SV& m) {
+FD SV mot_out(const BodyImage& b, float c, float s, const SV& m, bool dh = false) {
   V3 p = mk(b.p[0], b.p[1], b.p[2]);
-  V3 w = rot(b.R, rotz(c, s, m.w));
-  return SV{w, rot(b.R, rotz(c, s, m.v)) + cross(p, w)};
+  V3 w = rot_b(b, rotz(c, s, m.w), dh);
+  return SV{w, rot_b(b, rotz(c, s, m.v), dh) + cross(p, w)};
 }
 
 // e x m and e x* f for e = [z; 0] (the revolute motion subspace)
@@ -174,13 +217,60 @@ FD void gen_rotz(float c, float s, float* M) {
   M[6] = fmaf(c, d0, -s * d1); M[7] = fmaf(s, d0, c * d1); M[8] = d2;
 }
 
+// symmetric S -> Rot_x S Rot_x^T
+FD void sym_rotx(float c, float s, float* S) {
+  float yy = S[1], zz = S[2], xy = S[3], xz = S[4], yz = S[5];
+  float cc = c * c, ss = s * s, cs = c * s;
+  S[1] = fmaf(cc, yy, fmaf(-2.f * cs, yz, ss * zz));
+  S[2] = fmaf(ss, yy, fmaf(2.f * cs, yz, cc * zz));
+  S[5] = fmaf(cs, yy - zz, (cc - ss) * yz);
+  S[3] = fmaf(c, xy, -s * xz);
+  S[4] = fmaf(s, xy, c * xz);
+}
+// general M -> Rot_x M Rot_x^T
+FD void gen_rotx(float c, float s, float* M) {
+  // rows: A = Rot_x M
+  float a0 = M[0], a1 = M[1], a2 = M[2];
+  float b0 = fmaf(c, M[3], -s * M[6]), b1 = fmaf(c, M[4], -s * M[7]), b2 = fmaf(c, M[5], -s * M[8]);
+  float d0 = fmaf(s, M[3], c * M[6]), d1 = fmaf(s, M[4], c * M[7]), d2 = fmaf(s, M[5], c * M[8]);
+  // columns: A Rot_x^T
+  M[0] = a0; M[1] = fmaf(c, a1, -s * a2); M[2] = fmaf(s, a1, c * a2);
+  M[3] = b0; M[4] = fmaf(c, b1, -s * b2); M[5] = fmaf(s, b1, c * b2);
+  M[6] = d0; M[7] = fmaf(c, d1, -s * d2); M[8] = fmaf(s, d1, c * d2);
+}
+// S -> R S R^T and R^T S R, M -> R M R^T and R^T M R with a body's R
+FD void sym_rot_b(const BodyImage& b, float* S, bool dh = false) {
+  if (dh) sym_rotx(b.ca, b.sa, S);
+  else sym_rot(b.R, S);
+}
+FD void sym_rotT_b(const BodyImage& b, float* S, bool dh = false) {
+  if (dh) {
+    sym_rotx(b.ca, -b.sa, S);
+  } else {
+    const float Rt[9] = {b.R[0], b.R[3], b.R[6], b.R[1], b.R[4], b.R[7], b.R[2], b.R[5], b.R[8]};
+    sym_rot(Rt, S);
+  }
+}
+FD void gen_rot_b(const BodyImage& b, float* M, bool dh = false) {
+  if (dh) gen_rotx(b.ca, b.sa, M);
+  else gen_rot(b.R, M);
+}
+FD void gen_rotT_b(const BodyImage& b, float* M, bool dh = false) {
+  if (dh) {
+    gen_rotx(b.ca, -b.sa, M);
+  } else {
+    const float Rt[9] = {b.R[0], b.R[3], b.R[6], b.R[1], b.R[4], b.R[7], b.R[2], b.R[5], b.R[8]};
+    gen_rot(Rt, M);
+  }
+}
+
 // Composite inertia of body i (child' coords) carried to parent' coords:
 // X^T I X for ^child X_parent = the revolute joint transform.
-FD RBI rbi_out(const BodyImage& b, float c, float s, const RBI& I) {
+FD RBI rbi_out(const BodyImage& b, float c, float s, const RBI& I, bool dh = false) {
   float S[6] = {I.xx, I.yy, I.zz, I.xy, I.xz, I.yz};
   sym_rotz(c, s, S);
-  sym_rot(b.R, S);
-  V3 hr = rot(b.R, rotz(c, s, I.h));
+  sym_rot_b(b, S, dh);
+  V3 hr = rot_b(b, rotz(c, s, I.h), dh);
   V3 p = mk(b.p[0], b.p[1], b.p[2]);
   V3 hn = hr + I.m * p;
   float sh = dot(p, hn + hr);
@@ -264,20 +354,19 @@ FD void ai_shift(const V3& p, AI& I) {
 }
 // X^T I X for the revolute joint transform (child' -> parent'): rotate all
 // blocks by E = R Rot_z(q), then shift by the joint origin p.
-FD void ai_out(const BodyImage& b, float c, float s, AI& I) {
-  sym_rotz(c, s, I.A); sym_rot(b.R, I.A);
-  sym_rotz(c, s, I.C); sym_rot(b.R, I.C);
-  gen_rotz(c, s, I.B); gen_rot(b.R, I.B);
+FD void ai_out(const BodyImage& b, float c, float s, AI& I, bool dh = false) {
+  sym_rotz(c, s, I.A); sym_rot_b(b, I.A, dh);
+  sym_rotz(c, s, I.C); sym_rot_b(b, I.C, dh);
+  gen_rotz(c, s, I.B); gen_rot_b(b, I.B, dh);
   ai_shift(mk(b.p[0], b.p[1], b.p[2]), I);
 }
 // The inverse congruence, parent' -> child': shift by -p, then rotate all
 // blocks by E^T.
-FD void ai_in(const BodyImage& b, float c, float s, AI& I) {
+FD void ai_in(const BodyImage& b, float c, float s, AI& I, bool dh = false) {
   ai_shift(mk(-b.p[0], -b.p[1], -b.p[2]), I);
-  const float Rt[9] = {b.R[0], b.R[3], b.R[6], b.R[1], b.R[4], b.R[7], b.R[2], b.R[5], b.R[8]};
-  sym_rot(Rt, I.A); sym_rotz(c, -s, I.A);
-  sym_rot(Rt, I.C); sym_rotz(c, -s, I.C);
-  gen_rot(Rt, I.B); gen_rotz(c, -s, I.B);
+  sym_rotT_b(b, I.A, dh); sym_rotz(c, -s, I.A);
+  sym_rotT_b(b, I.C, dh); sym_rotz(c, -s, I.C);
+  gen_rotT_b(b, I.B, dh); gen_rotz(c, -s, I.B);
 }
 
 }  // namespace frax
