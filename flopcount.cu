@@ -156,6 +156,9 @@ void count_chain_vjp(const Img& M) {
   aba_vjp_chain_one<7>(M, q.data(), qd.data(), qdd.data(), gb.data(), o5.data(), o6.data(), o7.data(), col); rep("aba_vjp_chain");
   std::vector<CF> w(8);
   chain_minv<7>(M, q.data(), RhsFromGlobal<ChainTopo<7>, Col>{gb.data(), col}, w.data(), col); rep("minv_factor");
+  rnea_one<ChainTopo<7>>(M, q.data(), qd.data(), nullptr, o6.data(), col);
+  chain_minv<7>(M, q.data(), RhsFromGlobal<ChainTopo<7>, Col>{gb.data(), col}, w.data(), col);
+  rep("aba_factor");
   std::vector<CF> dq(nv, CF(0.3f)), dqd(nv, CF(0.2f)), dx(nv, CF(0.1f)), o9(nv + 8), o10(6 + 8);
   rnea_jvp_seg<T>(M, q.data(), qd.data(), qdd.data(), dq.data(), dqd.data(), dx.data(),
                   JvpToGlobal<T, Col>{o6.data(), o9.data(), col}, col); rep("rnea_jvp");

@@ -144,7 +144,9 @@ FRAX_API frax_status frax_crba(frax_model_t model, int64_t B, int64_t ld, const 
 
 /*
  * frax_aba — forward dynamics, Eq. 2 with f = 0: qdd = M^-1 (tau - c - g),
- * by the articulated-body algorithm (O(n); named future work in Sec. VI).
+ * by the articulated-body algorithm (O(n); named future work in Sec. VI);
+ * for 7-body chains through the mass-matrix factor instead (the Cholesky-
+ * style solve of the Sec. VI footnote), cheaper at that size.
  *   q [nq][ld], qd [nv][ld], tau [nv][ld] in; qdd [nv][ld] out.
  */
 FRAX_API frax_status frax_aba(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
