@@ -69,7 +69,37 @@ __global__ void __launch_bounds__(kBlock, 6) k_aba_ext_chain7(const __grid_const
   for (int k = 0; k < 7; ++k) col.out(qdd, k, x[k]);
 }
 
+// The ABA adjoint in two launches when taubar is asked for (it is w itself):
+// w = M^-1 gbar through the factor into taubar, then the RNEA adjoint seeded
+// with it. Each kernel stays small enough for the instruction cache.
+__global__ void __launch_bounds__(kBlock, 8) k_minv_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+                                                          int64_t ld, const float* q, const float* g, float* w) {
+  FRAX_TID();
+  float x[7];
+  chain_minv<7>(M, q, RhsFromGlobal<ChainTopo<7>, Col>{g, col}, x, col);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) col.out(w, k, x[k]);
+}
+__global__ void __launch_bounds__(kBlock) k_aba_vjp_tail_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+                                                                 int64_t ld, const float* q, const float* qd,
+                                                                 const float* qdd, const float* w, float* qbar,
+                                                                 float* qdbar) {
+  FRAX_TID();
+  using S = SegTopo<8, false>;
+  rnea_vjp_seg<S>(M, q, qd, qdd, RhsFromGlobal<S, Col>{w, col}, vjp_sink<S>(M, q, qbar, qdbar, nullptr, -1.f, col),
+                  col);
+}
+
 cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
+  if (op == kOpAbaVjp && a.out2) {
+    ModelImage<8> img8;
+    m.pack(&img8);
+    const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
+    k_minv_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.gbar, a.out2);
+    k_aba_vjp_tail_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.out2, a.out0,
+                                                         a.out1);
+    return cudaGetLastError();
+  }
   if (op == kOpAbaExt) {
     ModelImage<8> img8;
     m.pack(&img8);
