@@ -69,7 +69,15 @@ struct ColT {
     return p[k * ld + b];
 #endif
   }
-  FD void out(float* __restrict__ p, int k, float v) const { p[k * ld + b] = v; }
+  // outputs are written once and not read again by the kernel that writes
+  // them (except through ColT<false>): streaming stores (evict-first in L2)
+  FD void out(float* __restrict__ p, int k, float v) const {
+#ifdef __CUDA_ARCH__
+    __stcs(p + k * ld + b, v);
+#else
+    p[k * ld + b] = v;
+#endif
+  }
 };
 using Col = ColT<true>;
 
@@ -367,14 +375,15 @@ FD void crba_one(const Img& M, const float* __restrict__ q, float* __restrict__ 
 #pragma unroll
     for (int t = 0; t < NT; ++t) col.out(LD, t, H[t]);
   } else {
+    const ColT<false> own{col.ld, col.b};  // LD is rewritten in place: read through L2
     for (int k = nv - 1; k >= 0; --k) {
-      const float rk = 1.f / col.in(LD, MSink::tri(k, k));
+      const float rk = 1.f / own.in(LD, MSink::tri(k, k));
       int i = T::dparent(M, k);
       while (i >= 0) {
-        const float a = col.in(LD, MSink::tri(k, i)) * rk;
+        const float a = own.in(LD, MSink::tri(k, i)) * rk;
         int j = i;
         while (j >= 0) {
-          col.out(LD, MSink::tri(i, j), fmaf(-a, col.in(LD, MSink::tri(k, j)), col.in(LD, MSink::tri(i, j))));
+          col.out(LD, MSink::tri(i, j), fmaf(-a, own.in(LD, MSink::tri(k, j)), own.in(LD, MSink::tri(i, j))));
           j = T::dparent(M, j);
         }
         col.out(LD, MSink::tri(k, i), a);
