@@ -61,6 +61,14 @@ FLOPS = {
                  "aba": 20316, "rnea_vjp": 19471, "aba_vjp": 36255, "osc": 24669, "rnea_ext": 10346,
                  "aba_ext": 22901, "fk_jvp": 2584, "rnea_jvp": 17866, "aba_jvp": 34797},
 }
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# chain step's kernels, from one `ncu --set full` capture of this bench's
+# workload; an entry is removed when its kernel changes. aba_vjp = the factor
+# solve plus the adjoint sweep.
+NCU_TRAFFIC = {
+    "fk_jac": 29.40e6 + 493.34e6, "rnea": 88.13e6 + 8.78e6, "crba_ltdl": 29.42e6 + 267.21e6,
+    "aba": 88.19e6 + 11.31e6, "rnea_vjp": 117.54e6 + 51.05e6, "aba_vjp": 58.76e6 + 2.52e6 + 117.50e6 + 30.95e6,
+}
 # operational-space control task bodies (the last end frame of each model)
 OSC_TASK = {"chain7": 6, "humanoid": 29}
 
@@ -525,7 +533,7 @@ def frax_arm(args, rank, world, local_rank):
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": hbm, "unit": "GB/s",
                     "frac": d["frac_hbm_peak"], "peak_basis": f"{hbm_src} HBM copy bandwidth"}
-    roofline["traffic"] = None
+    roofline["traffic"] = NCU_TRAFFIC.get(dom)
 
     # end to end through the public API with pinned host buffers: every step
     # copies its inputs in (H2D stream) and every output back (D2H stream,
