@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kBlock) k_rnea_vjp(const __grid_constant__ Mod
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_aba_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_aba_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                      int64_t ld, const float* q, const float* qd,
                                                      const float* tau, const float* qdd, const float* gbar,
                                                      float* qbar, float* qdbar, float* taubar) {
@@ -83,32 +83,34 @@ __global__ void __launch_bounds__(kBlock) k_ltdl_inverse(const __grid_constant__
   ltdl_inverse<T>(M, LD, Minv, col);
 }
 
-// Trees (segment-unrolled): register use capped so that 6 (FK, RNEA, CRBA)
-// or 4 (ABA, which keeps 8 floats per body in thread-local memory between
-// its sweeps) 128-thread blocks fit on an SM.
+// Trees (segment-unrolled): register caps (128-thread blocks per SM) chosen
+// by measurement on the humanoid: 8 for FK, RNEA and ABA (which keeps 8
+// floats per body in thread-local memory between its sweeps), 4 for CRBA;
+// more resident warps hide those memory latencies better than the registers
+// they cost.
 template <class T>
-__global__ void __launch_bounds__(kBlock, 6) k_fk_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_fk_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                        int64_t ld, const float* q, float* pose,
                                                        const __grid_constant__ Frames fr, float* J) {
   FRAX_TID();
   fk_seg<T>(M, q, pose, fr, J, col);
 }
 template <class T>
-__global__ void __launch_bounds__(kBlock, 6) k_rnea_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
+__global__ void __launch_bounds__(kBlock, 8) k_rnea_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
                                                          int64_t B, int64_t ld, const float* q, const float* qd,
                                                          const float* qdd, float* tau) {
   FRAX_TID();
   rnea_seg<T>(M, q, qd, qdd, tau, col);
 }
 template <class T>
-__global__ void __launch_bounds__(kBlock, 6) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
+__global__ void __launch_bounds__(kBlock, 4) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
                                                          int64_t B, int64_t ld, const float* q, float* Mout,
                                                          float* LD) {
   FRAX_TID();
   crba_seg<T>(M, q, Mout, LD, col);
 }
 template <class T>
-__global__ void __launch_bounds__(kBlock, 4) k_aba_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_aba_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                         int64_t ld, const float* q, const float* qd,
                                                         const float* tau, float* qdd) {
   FRAX_TID();
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_aba_seg(const __grid_constant__ M
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock, 4) k_osc_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 5) k_osc_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                         int64_t ld, int task, const float* q, const float* qd,
                                                         const float* xdd, float* tau, float* Lam) {
   FRAX_TID();
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_osc_seg(const __grid_constant__ M
 // External forces: the plain kernel's result, then tau_ext from one more
 // sweep (subtracted from RNEA's output, added to ABA's right-hand side).
 template <class T>
-__global__ void __launch_bounds__(kBlock, 6) k_rnea_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_rnea_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                          int64_t ld, const float* q, const float* qd,
                                                          const float* qdd, const float* fext, float* tau) {
   FRAX_TID();
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_rnea_ext(const __grid_constant__ 
   ext_tau<T>(M, q, fext, col, SubFromGlobal<T>{tau, ColT<false>{ld, b}});
 }
 template <class T>
-__global__ void __launch_bounds__(kBlock, 4) k_aba_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_aba_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                         int64_t ld, const float* q, const float* qd,
                                                         const float* tau, const float* fext, float* qdd) {
   FRAX_TID();
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kBlock) k_rnea_jvp(const __grid_constant__ Mod
   rnea_jvp_seg<T>(M, q, qd, qdd, dq, dqd, dqdd, JvpToGlobal<T, Col>{tau, dtau, col}, col);
 }
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_aba_jvp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_aba_jvp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                      int64_t ld, const float* q, const float* qd,
                                                      const float* qdd, const float* dq, const float* dqd,
                                                      const float* dtau, float* dqdd) {
