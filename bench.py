@@ -175,6 +175,27 @@ def make_inputs(robot, B, seed, device):
     return host, dev
 
 
+def kernels_per_call(robot, op):
+    """Kernel launches one public call makes: the chain's ABA adjoint runs as
+    the factor solve plus the adjoint sweep; a tree's FK+J and CRBA add the
+    fill of their structural zeros (rows for non-ancestor pairs) when the
+    model has any."""
+    chain7 = robot.n_bodies == 7 and all(int(p) == i - 1 for i, p in enumerate(robot.parent)) \
+        and not robot.has_free_root
+    if chain7:
+        return 2 if op == "aba_vjp" else 1
+    anc = []
+    for i, p in enumerate(robot.parent):
+        anc.append((anc[int(p)] if p >= 0 else 0) | (1 << i))
+    bodies = range(robot.n_bodies)
+    unrelated = any(not (anc[a] >> b) & 1 and not (anc[b] >> a) & 1 for a in bodies for b in bodies)
+    if op == "fk_jac":
+        return 1 + any(not (anc[f] >> b) & 1 for f in robot.end_frames for b in bodies)
+    if op == "crba_ltdl":
+        return 1 + unrelated
+    return 1
+
+
 class Step:
     """The whole hot path over one resident batch; output buffers are
     allocated once (torch), the kernels write into them."""
@@ -216,6 +237,7 @@ class Step:
             "aba_ext": lambda: fx_.frax_aba_ext(m, d["q"], d["qd"], d["tau"], d["fext"], qdd=o["qdd"]),
         }
         self.launches = [(n, table[n]) for n in ops]
+        self.kernels = sum(kernels_per_call(robot, n) for n in ops)
         self.B = B
 
     def run(self, events=None):
@@ -225,7 +247,7 @@ class Step:
             fn()
             if events is not None:
                 events[name][1].record()
-        return len(self.launches)
+        return self.kernels
 
 
 def time_step(step, steps, warmup, flush, world, dist, clocks=None):

@@ -55,6 +55,16 @@ frax_status dispatch(frax_model_t model, frax::Op op, const frax::OpArgs& a, con
   return ok();
 }
 
+// Structural zeros of a tree's outputs, written by one row fill after the
+// per-instance kernel (which skips them). ZeroRows is large (14 KB): one
+// per thread, reused.
+frax_status fill_zeros(frax::ZeroRows& z, float* base0, float* base1, const frax::OpArgs& a, const char* fn) {
+  const cudaError_t e = frax::launch_zero_rows(z, base0, base1, a.ld, a.B, a.stream);
+  if (e != cudaSuccess) return fail(FRAX_ECUDA, std::string(fn) + ": zero fill launch failed: " + cudaGetErrorString(e));
+  return ok();
+}
+thread_local frax::ZeroRows g_zero_rows;
+
 #define FRAX_TRY(expr)                    \
   do {                                    \
     frax_status s_ = (expr);              \
@@ -131,7 +141,17 @@ frax_status frax_jacobian(frax_model_t model, int64_t B, int64_t ld, const float
   FRAX_TRY(need(q, "frax_jacobian", "q"));
   FRAX_TRY(need(J, "frax_jacobian", "J"));
   a.B = B; a.ld = ld; a.q = q; a.out0 = pose; a.out1 = J; a.stream = static_cast<cudaStream_t>(stream);
-  return dispatch(model, frax::kOpJac, a, "frax_jacobian");
+  FRAX_TRY(dispatch(model, frax::kOpJac, a, "frax_jacobian"));
+  const frax::HostModel& m = model->m;
+  if (m.kind == frax::kKindChain) return ok();
+  frax::ZeroRows& z = g_zero_rows;
+  z.n0 = z.n = 0;
+  for (int f = 0; f < n_frames; ++f)
+    for (int c = 0; c < m.nv; ++c)
+      if (!((m.anc[frame_body[f]] >> m.dof_body[c]) & 1ull))
+        for (int r = 0; r < 6; ++r) z.row[z.n++] = static_cast<uint16_t>((f * 6 + r) * m.nv + c);
+  z.n0 = z.n;
+  return fill_zeros(z, J, nullptr, a, "frax_jacobian");
 }
 
 frax_status frax_rnea(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
@@ -155,7 +175,17 @@ frax_status frax_crba(frax_model_t model, int64_t B, int64_t ld, const float* q,
   if (!M && !LD) return fail(FRAX_EINVAL, "frax_crba: M and LD are both NULL");
   frax::OpArgs a;
   a.B = B; a.ld = ld; a.q = q; a.out0 = M; a.out1 = LD; a.stream = static_cast<cudaStream_t>(stream);
-  return dispatch(model, frax::kOpCrba, a, "frax_crba");
+  FRAX_TRY(dispatch(model, frax::kOpCrba, a, "frax_crba"));
+  const frax::HostModel& m = model->m;
+  if (m.kind == frax::kKindChain) return ok();
+  frax::ZeroRows& z = g_zero_rows;
+  z.n0 = z.n = 0;
+  if (M)
+    for (uint16_t r : m.zero_M) z.row[z.n++] = r;
+  z.n0 = z.n;
+  if (LD)
+    for (uint16_t r : m.zero_LD) z.row[z.n++] = r;
+  return fill_zeros(z, M, LD, a, "frax_crba");
 }
 
 frax_status frax_aba(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,

@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(kBlock) k_ltdl_inverse(const __grid_constant__
   ltdl_inverse<T>(M, LD, Minv, col);
 }
 
-// Trees (segment-unrolled): register caps (128-thread blocks per SM) chosen
+// Trees (segment-unrolled). FK+J and CRBA leave the structural zeros of J, M
+// and the factor to the row fill of zeros.cu. Register caps (128-thread blocks per SM) chosen
 // by measurement on the humanoid: 8 for FK, RNEA and ABA (which keeps 8
 // floats per body in thread-local memory between its sweeps), 4 for CRBA;
 // more resident warps hide those memory latencies better than the registers
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_fk_seg(const __grid_constant__ Mo
                                                        int64_t ld, const float* q, float* pose,
                                                        const __grid_constant__ Frames fr, float* J) {
   FRAX_TID();
-  fk_seg<T>(M, q, pose, fr, J, col);
+  fk_seg<T, ModelImage<T::NBMAX>, Col, false>(M, q, pose, fr, J, col);
 }
 template <class T>
 __global__ void __launch_bounds__(kBlock, 8) k_rnea_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_crba_seg(const __grid_constant__ 
                                                          int64_t B, int64_t ld, const float* q, float* Mout,
                                                          float* LD) {
   FRAX_TID();
-  crba_seg<T>(M, q, Mout, LD, col);
+  crba_seg<T, ModelImage<T::NBMAX>, Col, false>(M, q, Mout, LD, col);
 }
 template <class T>
 __global__ void __launch_bounds__(kBlock, 8) k_aba_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,

@@ -36,6 +36,17 @@ struct OpArgs {
   cudaStream_t stream = nullptr;
 };
 
+// Rows (entries of an SoA output) to be zeroed: rows [0, n0) of the first
+// array, [n0, n) of the second. Sized for M and the packed factor of the
+// largest model (69 x 69 + 69 x 70 / 2 entries).
+constexpr int kMaxZeroRows = kMaxDofs * kMaxDofs + kMaxDofs * (kMaxDofs + 1) / 2;
+struct ZeroRows {
+  int32_t n0 = 0, n = 0;
+  uint16_t row[kMaxZeroRows];
+};
+cudaError_t launch_zero_rows(const ZeroRows& z, float* base0, float* base1, int64_t ld, int64_t B,
+                             cudaStream_t stream);
+
 // Each returns the launch status (cudaGetLastError after the launch).
 cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a);
 cudaError_t launch_tree32(const HostModel& m, Op op, const OpArgs& a);

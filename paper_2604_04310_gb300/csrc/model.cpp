@@ -315,6 +315,19 @@ std::string build_model(int n, const int32_t* parent, const int32_t* joint_type,
   bool chain = !m.free_root;
   for (int i = 0; i < n; ++i) chain = chain && parent[i] == i - 1;
   m.kind = (chain && n == 7) ? kKindChain : kKindTree;
+  // structural zeros: dofs whose bodies are not in an ancestor relation
+  m.dof_body.assign(m.nv, 0);
+  for (int i = 0; i < n; ++i)
+    for (int d = 0; d < (joint_type[i] == 1 ? 6 : 1); ++d) m.dof_body[m.iv[i] + d] = i;
+  auto related = [&](int a, int b) {
+    const int ba = m.dof_body[a], bb = m.dof_body[b];
+    return ((m.anc[ba] >> bb) & 1ull) || ((m.anc[bb] >> ba) & 1ull);
+  };
+  for (int r = 0; r < m.nv; ++r)
+    for (int c = 0; c < m.nv; ++c) {
+      if (!related(r, c)) m.zero_M.push_back(static_cast<uint16_t>(r * m.nv + c));
+      if (c < r && !related(r, c)) m.zero_LD.push_back(static_cast<uint16_t>(r * (r + 1) / 2 + c));
+    }
   // kernels that unroll a segment take the Rot_x form for every body after
   // the segment's first: each such body is the only child of a revolute body
   for (int i = 0; i < n; ++i)

@@ -23,6 +23,9 @@ struct HostModel {
   std::vector<int> depth;        // per body, root = 0
   std::vector<int> order, seg_start, seg_len, seg_parent, act;  // segment schedule
   std::vector<int> seg_of, pos_of;
+  std::vector<int> dof_body;        // per dof: its body
+  std::vector<uint16_t> zero_M;     // structural zeros of M (entry r * nv + c)
+  std::vector<uint16_t> zero_LD;    // and of the packed factor (r (r + 1) / 2 + c)
   double gravity[3] = {0, 0, 0};
   std::vector<BodyImage> bodies;  // FP32 internal-frame image
 

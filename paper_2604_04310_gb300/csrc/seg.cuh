@@ -330,7 +330,9 @@ FD void aba_seg(const Img& M, const float* __restrict__ q, const float* __restri
 // forces carried to the root through the joint transforms) and zeros at the
 // dofs of non-ancestors. Not inlined: called once per body, it keeps the
 // kernel's code small.
-template <class T, class Img, class C>
+// With ZEROS false the structural zeros (non-ancestor pairs) are left to the
+// caller (a separate fill of those rows, the same for every instance).
+template <class T, class Img, class C, bool ZEROS>
 FRAX_NOINLINE void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mout,
                                            float* __restrict__ LD, const float* sc, const float* ss, C col) {
   const int nv = T::kFree ? M.nb + 5 : M.nb;
@@ -358,6 +360,7 @@ FRAX_NOINLINE void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __res
       put(iv_of<T>(j), FM.w.z, FL.w.z);
     }
   }
+  if (!ZEROS) return;
   const uint64_t anc = M.anc[i];
   for (int jj = 0; jj < i; ++jj) {
     if ((anc >> jj) & 1ull) continue;
@@ -369,7 +372,7 @@ FRAX_NOINLINE void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __res
   }
 }
 
-template <class T, class Img, class C>
+template <class T, class Img, class C, bool ZEROS = true>
 FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ Mout, float* __restrict__ LD,
                  const C& col) {
   constexpr int NB = T::NBMAX;
@@ -482,7 +485,7 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
           ai_rank1_sub(Ia, U, dinv);
           ai_out(b, sc[i], ss[i], Ia);
         }
-        crba_emit_row<T>(M, i, FM, FL, Mout, LD, sc, ss, col);
+        crba_emit_row<T, Img, C, ZEROS>(M, i, FM, FL, Mout, LD, sc, ss, col);
         const RBI up = rbi_out(b, sc[i], ss[i], Cc);
         if (k > 0) {
           const RBI Ip = rbi_of(M.body[M.order[st + k - 1]]);
@@ -510,7 +513,7 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
 // registers; the joint axes and origins of the bodies of open ancestor
 // segments are kept per body so a frame's Jacobian is written as soon as its
 // segment is done. Column j of frame k: [z_j; z_j x (p_k - p_j)], 0 off Anc(k).
-template <class T, class Img, class C>
+template <class T, class Img, class C, bool ZEROS = true>
 FD void fk_seg(const Img& M, const float* __restrict__ q, float* __restrict__ pose, const Frames& fr,
                float* __restrict__ J, const C& col) {
   constexpr int NB = T::NBMAX;
@@ -534,6 +537,7 @@ FD void fk_seg(const Img& M, const float* __restrict__ q, float* __restrict__ po
     col.out(pose, 12 * i + 11, p.z);
   };
   auto jcol = [&](int base, int cj, bool on, V3 z, V3 lin) {
+    if (!ZEROS && !on) return;  // a structural zero, written by the caller
     col.out(J, base + 0 * nv + cj, on ? z.x : 0.f);
     col.out(J, base + 1 * nv + cj, on ? z.y : 0.f);
     col.out(J, base + 2 * nv + cj, on ? z.z : 0.f);

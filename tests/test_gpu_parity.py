@@ -254,3 +254,26 @@ def test_ltdl_solve_and_inverse(fxm, name):
     qdd_solve = fx.frax_ltdl_solve(h, LD, d["tau"] - bias)
     qdd_aba = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
     assert normwise(host(qdd_solve), host(qdd_aba)) < TOL_ABA_TREE
+
+
+@pytest.mark.parametrize("name", ["humanoid", "tree_big"])
+def test_structural_zeros_are_written(fxm, name):
+    """Outputs pre-filled with NaN: every entry of J, M and the factor is
+    written, the structural zeros (non-ancestor pairs, the same for every
+    instance) by the row fill, the rest by the per-instance kernels."""
+    m, h = MODELS[name], fxm[name]
+    B = 300
+    s, d = states(m, B, 27)
+    frames = list(m.end_frames)[:8]
+    nan = lambda rows: torch.full((rows, B), float("nan"), device="cuda")
+    J = nan(len(frames) * 6 * m.nv)
+    fx.frax_jacobian(h, d["q"], frames, J=J)
+    assert normwise(host(J), rbd.jacobian(m, s.q, frames).reshape(B, -1)) < TOL
+    M, LD = nan(m.nv * m.nv), nan(m.nv * (m.nv + 1) // 2)
+    fx.frax_crba(h, d["q"], M=M, LD=LD)
+    Mref = rbd.crba(m, s.q)
+    assert normwise(host(M), Mref.reshape(B, -1)) < TOL
+    assert normwise(host(LD), rbd.pack_ltdl(*rbd.ltdl(Mref))) < TOL
+    LD2 = nan(m.nv * (m.nv + 1) // 2)
+    fx.frax_crba(h, d["q"], LD=LD2, want_M=False)
+    assert torch.equal(LD2, LD)
