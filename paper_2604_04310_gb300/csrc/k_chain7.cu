@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_aba_ext_chain7(const __grid_const
 // The ABA adjoint in two launches when taubar is asked for (it is w itself):
 // w = M^-1 gbar through the factor into taubar, then the RNEA adjoint seeded
 // with it. Each kernel stays small enough for the instruction cache.
-__global__ void __launch_bounds__(kBlock, 8) k_minv_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 10) k_minv_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
                                                           int64_t ld, const float* q, const float* g, float* w) {
   FRAX_TID();
   float x[7];

@@ -350,8 +350,10 @@ FRAX_NOINLINE void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __res
     const int k = M.parent[j];
     if (k < 0) break;
     const BodyImage& b = M.body[j];
-    if (wM) FM = frc_out(b, sc[j], ss[j], FM);
-    if (wL) FL = frc_out(b, sc[j], ss[j], FL);
+    with_dh(b.dh, [&](auto dh) {
+      if (wM) FM = frc_out(b, sc[j], ss[j], FM, dh);
+      if (wL) FL = frc_out(b, sc[j], ss[j], FL, dh);
+    });
     j = k;
     if (T::kFree && j == 0) {
       put(0, FM.w.x, FL.w.x); put(1, FM.w.y, FL.w.y); put(2, FM.w.z, FL.w.z);
