@@ -73,11 +73,23 @@ NCU_TRAFFIC = {
 OSC_TASK = {"chain7": 6, "humanoid": 29}
 
 
-def bytes_per_instance(op, nq, nv, nb, nframes):
-    """Minimum HBM traffic: inputs read once, outputs written once (FP32)."""
+def jacobian_nonzeros(robot):
+    """Structurally non-zero Jacobian entries of the end frames: 6 per dof
+    whose body is an ancestor of (or is) the frame body."""
+    anc = []
+    for i, p in enumerate(robot.parent):
+        anc.append((anc[int(p)] if p >= 0 else 0) | (1 << i))
+    dof_body = [i for i, t in enumerate(robot.joint_type) for _ in range(6 if t == 1 else 1)]
+    return sum(6 for f in robot.end_frames for b in dof_body if (anc[f] >> b) & 1)
+
+
+def bytes_per_instance(op, nq, nv, nb, nframes, j_nonzero=None):
+    """Minimum HBM traffic: inputs read once, outputs written once (FP32).
+    For the Jacobians only the structurally non-zero entries count when
+    j_nonzero is given (the dense zero-filled write is reported beside)."""
     f = 4
     return {
-        "fk_jac": f * (nq + 12 * nb + nframes * 6 * nv),
+        "fk_jac": f * (nq + 12 * nb + (nframes * 6 * nv if j_nonzero is None else j_nonzero)),
         "rnea": f * (nq + 3 * nv), "bias": f * (nq + 2 * nv),
         "crba_ltdl": f * (nq + nv * nv + nv * (nv + 1) // 2),
         "aba": f * (nq + 3 * nv),
@@ -291,12 +303,15 @@ def roofline_of(per_op_ms, flops, B, peak, hbm_gbs, robot):
     out = {}
     for n, ms in per_op_ms.items():
         t = ms / 1e3
-        by = bytes_per_instance(n, robot.nq, robot.nv, robot.n_bodies, len(robot.end_frames))
+        by = bytes_per_instance(n, robot.nq, robot.nv, robot.n_bodies, len(robot.end_frames),
+                                jacobian_nonzeros(robot))
+        dense = bytes_per_instance(n, robot.nq, robot.nv, robot.n_bodies, len(robot.end_frames))
         tf = flops[n] * B / t / 1e12
         gbs = by * B / t / 1e9
         t_alu = flops[n] * B / (peak * 1e12)
         t_hbm = by * B / (hbm_gbs * 1e9)
         out[n] = {"ms": ms, "evals_per_s": B / t, "flops_per_instance": flops[n], "bytes_per_instance": by,
+                  "bytes_dense_per_instance": dense,
                   "tflops": tf, "gbs": gbs, "frac_fp32_peak": tf / peak, "frac_hbm_peak": gbs / hbm_gbs,
                   "bound": "alu" if t_alu >= t_hbm else "hbm", "roofline_frac": max(t_alu, t_hbm) / t}
     return out

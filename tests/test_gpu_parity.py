@@ -277,3 +277,39 @@ def test_structural_zeros_are_written(fxm, name):
     LD2 = nan(m.nv * (m.nv + 1) // 2)
     fx.frax_crba(h, d["q"], LD=LD2, want_M=False)
     assert torch.equal(LD2, LD)
+
+
+@pytest.mark.parametrize("name,B", [("chain7", 65536), ("humanoid", 16384)])
+def test_autograd_full_batch_vs_central_differences(fxm, name, B):
+    """The differentiation workload: RNEA and forward dynamics through the
+    autograd functions on the whole batch (velocities recomputed inside the
+    adjoint kernels, nothing stored per body), 12 sampled instances checked
+    against FP64 central differences (step 1e-6) of the oracle."""
+    m, h = MODELS[name], fxm[name]
+    s, d = states(m, B, 1003)
+    q, qd, qdd, tau = (d[k].clone().requires_grad_(True) for k in ("q", "qd", "qdd", "tau"))
+    g = gen.draw_gbar(m.nv, B, 1004).astype(np.float32).astype(np.float64)
+    gd = dev(g)
+    rq, rqd, _ = torch.autograd.grad(fx.rnea(h, q, qd, qdd), (q, qd, qdd), gd)
+    aq, aqd, at = torch.autograd.grad(fx.aba(h, q, qd, tau), (q, qd, tau), gd)
+    idx = np.sort(np.random.default_rng(1005).choice(B, 12, replace=False))
+    ss, gs = s.take(idx), g[idx]
+    sel = torch.from_numpy(idx).cuda()
+    pick = lambda t: host(t.index_select(1, sel))
+    hstep = 1e-6
+
+    def vjp_fd(fun, n):
+        out = np.zeros((len(idx), n))
+        for k in range(n):
+            e = np.zeros((len(idx), n))
+            e[:, k] = hstep
+            out[:, k] = np.einsum("bi,bi->b", gs, (fun(e) - fun(-e)) / (2 * hstep))
+        return out
+
+    assert normwise(pick(rq), dv.to_ambient(m, ss.q, vjp_fd(
+        lambda e: rbd.rnea(m, dv.retract(m, ss.q, e), ss.qd, ss.qdd), m.nv))) < TOL_GRAD
+    assert normwise(pick(rqd), vjp_fd(lambda e: rbd.rnea(m, ss.q, ss.qd + e, ss.qdd), m.nv)) < TOL_GRAD
+    assert normwise(pick(aq), dv.to_ambient(m, ss.q, vjp_fd(
+        lambda e: rbd.aba(m, dv.retract(m, ss.q, e), ss.qd, ss.tau), m.nv))) < TOL_GRAD
+    assert normwise(pick(aqd), vjp_fd(lambda e: rbd.aba(m, ss.q, ss.qd + e, ss.tau), m.nv)) < TOL_GRAD
+    assert normwise(pick(at), vjp_fd(lambda e: rbd.aba(m, ss.q, ss.qd, ss.tau + e), m.nv)) < TOL_GRAD
