@@ -296,6 +296,18 @@ def time_step(step, steps, warmup, flush, world, dist, clocks=None):
     return step_ms, per_op_ms, launches, wall, clk
 
 
+def whole_job(step_ms, steps, evals_per_step, world, dist, device):
+    """Replicas: every rank times its own batch; the job's step time is the
+    slowest rank's (max over ranks) and the value counts every rank's
+    evaluations. Returns (ms per step, evaluations per second)."""
+    import torch
+    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / steps
+    return ms_per_step, world * evals_per_step / (ms_per_step / 1e3)
+
+
 def roofline_of(per_op_ms, flops, B, peak, hbm_gbs, robot):
     """Per kernel: achieved FP32 rate and HBM rate from the algorithmic work,
     and the roofline fraction t_roof / t_measured with
@@ -553,12 +565,7 @@ def frax_arm(args, rank, world, local_rank):
     step = Step(fx, model, robot, dev, device, OPS)
     clocks = ClockSampler(phys)
     step_ms, per_op_ms, launches, wall, clk = time_step(step, args.steps, args.warmup, flush, world, dist, clocks)
-    t = torch.tensor([step_ms], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / args.steps
-    evals_per_step = len(OPS) * B
-    value = world * evals_per_step / (ms_per_step / 1e3)
+    ms_per_step, value = whole_job(step_ms, args.steps, len(OPS) * B, world, dist, device)
     hbm, hbm_src = measured_hbm_gbs()
     per_op = roofline_of(per_op_ms, FLOPS["chain7"], B, peak, hbm, robot)
     dom = max(OPS, key=lambda n: per_op_ms[n])

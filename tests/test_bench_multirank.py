@@ -1,0 +1,52 @@
+"""The bench's replica aggregation with two gloo ranks on CPU: each rank times
+its own batch, the job's step time is the slowest rank's and the value counts
+both ranks' evaluations; the reference arm runs on rank 0 only."""
+
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        step_ms = [40.0, 50.0][rank]  # the second rank is slower
+        ms, value = bench.whole_job(step_ms, 10, 6 * 1024, world, dist, torch.device("cpu"))
+        out[rank] = (ms, value)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_whole_job_takes_slowest_rank_and_counts_all():
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        ms, value = out[r]
+        assert ms == pytest.approx(5.0)
+        assert value == pytest.approx(2 * 6 * 1024 / 5e-3)
+
+
+def test_reference_arm_prints_on_rank0_only():
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2"],
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == ""
