@@ -141,7 +141,7 @@ FD void fk_one(const Img& M, const float* __restrict__ q, float* __restrict__ po
       pw[0] = P.r;
     } else {
       float s, c;
-      sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &s, &c);
+      joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &s, &c);
       float A[9];
       if (k < 0) {
 #pragma unroll
@@ -238,7 +238,7 @@ FD void rnea_one(const Img& M, const float* __restrict__ q, const float* __restr
       if (qdd) a[0] = a[0] + load6(qdd, 0, col);
     } else {
       const int k = T::parent(M, i);
-      sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
+      joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
       const float qdi = col.in(qd, iv_of<T>(i));
       const float qddi = qdd ? col.in(qdd, iv_of<T>(i)) : 0.f;
       SV vi = k < 0 ? szero() : mot_in(b, cq[i], sq[i], v[k], dh_of<T>(M, i));
@@ -288,7 +288,7 @@ FD void crba_one(const Img& M, const float* __restrict__ q, float* __restrict__ 
   for (int i = 0; i < T::NBMAX; ++i) {
     if (i >= nb) break;
     Ic[i] = rbi_of(M.body[i]);
-    if (!(T::kFree && i == 0)) sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
+    if (!(T::kFree && i == 0)) joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
   }
 #pragma unroll(T::kStatic ? T::NBMAX : 1)
   for (int i = T::NBMAX - 1; i >= 1; --i) {
@@ -469,7 +469,7 @@ FD void aba_core(const Img& M, const float* __restrict__ q, const float* __restr
       cb[0] = szero();
     } else {
       const int k = T::parent(M, i);
-      sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
+      joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
       if (VEL) {
         const float qdi = col.in(qd, iv_of<T>(i));
         SV vi = k < 0 ? szero() : mot_in(b, cq[i], sq[i], v[k], dh_of<T>(M, i));
@@ -574,7 +574,7 @@ FD void rnea_vjp_core(const Img& M, const float* __restrict__ q, const float* __
       Fb[0] = gb_at.root();
     } else {
       const int k = T::parent(M, i);
-      sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
+      joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sq[i], &cq[i]);
       const float qdi = col.in(qd, iv_of<T>(i));
       SV vi = k < 0 ? szero() : mot_in(b, cq[i], sq[i], v[k], dh_of<T>(M, i));
       xa[i] = mot_in(b, cq[i], sq[i], k < 0 ? ag : a_prev[k], dh_of<T>(M, i));

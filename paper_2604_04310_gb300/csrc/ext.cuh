@@ -76,7 +76,7 @@ FD void ext_tau(const Img& M, const float* __restrict__ q, const float* __restri
           p[k] = o;
           if (kind == kActOpen && k == len - 1) {
             float sn, cs;
-            sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn, &cs);
+            joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn, &cs);
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
               const float x = ER[3 * r], y = ER[3 * r + 1];
@@ -87,7 +87,7 @@ FD void ext_tau(const Img& M, const float* __restrict__ q, const float* __restri
             bp[i] = o;
           } else if (k < len - 1) {
             float sn, cs;
-            sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn, &cs);
+            joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn, &cs);
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
               const float x = ER[3 * r], y = ER[3 * r + 1];

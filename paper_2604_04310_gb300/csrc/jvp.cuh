@@ -85,7 +85,7 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
         const BodyImage& b = M.body[i];
         with_dh(b.dh, [&](auto dh) {
           float sn, cs;
-          sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+          joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
           sc[i] = cs;
           ss[i] = sn;
           const int iv = iv_of<T>(i);
@@ -234,7 +234,7 @@ FD void fk_jvp_seg(const Img& M, const float* __restrict__ q, const float* __res
       const int i = M.order[st + k];
       const BodyImage& b = M.body[i];
       float sn, cs;
-      sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+      joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
       float ER[9];
       with_dh(b.dh, [&](auto dh) {
         v = mot_in(b, cs, sn, v, dh);

@@ -60,7 +60,7 @@ __device__ __forceinline__ SE3 joint_tf(const ModelImage<64>& M, int i, const fl
   }
   const BodyImage& b = M.body[i];
   float sn, cs;
-  sincosf(col.in(q, FREE ? i + 6 : i) + b.th0, &sn, &cs);
+  joint_sincos(col.in(q, FREE ? i + 6 : i) + b.th0, &sn, &cs);
   SE3 t;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {

@@ -144,7 +144,7 @@ FD AI osc_inertias(const Img& M, const float* __restrict__ q, uint64_t path, PL&
       const int i = M.order[st + k];
       const BodyImage& b = M.body[i];
       float sn, cs;
-      sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+      joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
       const SV U = ai_col_z(IA);
       const float dinv = 1.f / U.w.z;
       if ((path >> i) & 1ull) {
@@ -208,7 +208,7 @@ FD OscPath osc_path(const Img& M, const float* __restrict__ q, const float* __re
     const int j = low_bit(rest);
     const BodyImage& b = M.body[j];
     float sn, cs;
-    sincosf(col.in(q, iq_of<T>(j)) + b.th0, &sn, &cs);
+    joint_sincos(col.in(q, iq_of<T>(j)) + b.th0, &sn, &cs);
     const float qdj = col.in(qd, iv_of<T>(j));
     with_dh(b.dh, [&](auto dh) {
       // W = X Omega_p X^T

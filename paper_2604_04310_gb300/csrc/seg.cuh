@@ -84,7 +84,7 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
         if (k < len) {
           const int i = M.order[st + k];
           const BodyImage& b = M.body[i];
-          sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn[k], &cc[k]);
+          joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn[k], &cc[k]);
           const float qdi = col.in(qd, iv_of<T>(i));
           const float qddi = qdd ? col.in(qdd, iv_of<T>(i)) : 0.f;
           v = mot_in(b, cc[k], sn[k], v, k > 0);
@@ -204,7 +204,7 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
           const BodyImage& b = M.body[i];
           with_dh(b.dh, [&](auto dh) {
             float sn, cs;
-            sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+            joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
             vv = mot_in(b, cs, sn, vv, dh);
             vv.w.z += col.in(qd, iv_of<T>(i));
           });
@@ -232,7 +232,7 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         const RBI Ib = rbi_of(b);
         const SV vk = vtip;  // velocity of body i, stepped back from the segment's tip
         float sk, ck;
-        sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sk, &ck);
+        joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sk, &ck);
         AI IA = ai_of(Ib);
         SV pAt = szero();
         SV cb = szero();
@@ -292,7 +292,7 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
         float sn, cs;
-        sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+        joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
         SV cb = szero();
         if (VEL) {
           const float qdi = col.in(qd, iv_of<T>(i));
@@ -454,7 +454,7 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
 #pragma unroll 1
       for (int k = 0; k < len; ++k) {
         const int i = M.order[st + k];
-        sincosf(col.in(q, iq_of<T>(i)) + M.body[i].th0, &ss[i], &sc[i]);
+        joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &ss[i], &sc[i]);
       }
       if (kind == kActOpen) {
         ICa[last] = rzero;
@@ -578,7 +578,7 @@ FD void fk_seg(const Img& M, const float* __restrict__ q, float* __restrict__ po
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
         float sn, cs;
-        sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+        joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
         float A[9];
         with_dh(b.dh, [&](auto dh) { mat_mul_b(R, b, A, dh); });
         p = p + rot(R, mk(b.p[0], b.p[1], b.p[2]));
@@ -684,7 +684,7 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
         const BodyImage& b = M.body[i];
         with_dh(SPARSE && b.dh, [&](auto dh) {
           float sn, cs;
-          sincosf(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+          joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
           sc[i] = cs;
           ss[i] = sn;
           const float qdi = col.in(qd, iv_of<T>(i));
@@ -790,7 +790,7 @@ FD void chain_minv(const Img& M, const float* __restrict__ q, const G& g, float*
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     Ic[i] = rbi_of(M.body[i]);
-    sincosf(col.in(q, i) + M.body[i].th0, &sq[i], &cq[i]);
+    joint_sincos(col.in(q, i) + M.body[i].th0, &sq[i], &cq[i]);
   }
 #pragma unroll
   for (int i = N - 1; i >= 1; --i) Ic[i - 1] = rbi_add(Ic[i - 1], rbi_out(M.body[i], cq[i], sq[i], Ic[i], true));

@@ -16,6 +16,19 @@ namespace frax {
 #define FRAX_NOINLINE __attribute__((noinline))
 #endif
 
+// sin and cos of a joint angle: reduced to [-pi, pi] by 2 pi split in two
+// parts (Cody and Waite's additive reduction), then the SFU approximations
+// (absolute error below 5e-7 on [-pi, pi]). Host builds call sincosf.
+FD void joint_sincos(float x, float* s, float* c) {
+#ifdef __CUDA_ARCH__
+  const float k = rintf(x * 0.15915494309189535f);           // x / (2 pi)
+  const float r = fmaf(-k, 6.28318548202514648f, x);         // minus k hi
+  __sincosf(fmaf(k, 1.7484555314695172e-07f, r), s, c);     // minus k lo
+#else
+  sincosf(x, s, c);
+#endif
+}
+
 struct V3 {
   float x, y, z;
 };

@@ -313,3 +313,18 @@ def test_autograd_full_batch_vs_central_differences(fxm, name, B):
         lambda e: rbd.aba(m, dv.retract(m, ss.q, e), ss.qd, ss.tau), m.nv))) < TOL_GRAD
     assert normwise(pick(aqd), vjp_fd(lambda e: rbd.aba(m, ss.q, ss.qd + e, ss.tau), m.nv)) < TOL_GRAD
     assert normwise(pick(at), vjp_fd(lambda e: rbd.aba(m, ss.q, ss.qd, ss.tau + e), m.nv)) < TOL_GRAD
+
+
+def test_joint_angle_sin_cos_accuracy():
+    """The kernels' joint sin/cos (reduction by 2 pi, then the SFU
+    approximations) through FK of one revolute body about z: R = Rot_z(q), so
+    R[0][0] = cos q and R[1][0] = sin q. Absolute error below 1e-6 for angles
+    up to 1000 rad (sincosf's own error is below 2e-7 here)."""
+    from tests.test_oracle_closed_forms import _model, EYE
+    body = _model([-1], [0], [0, 0, 1], EYE + [0, 0, 0], [1.0, 0, 0, 0, 0.1, 0.1, 0.1, 0, 0, 0])
+    h = fx.Model.from_robot(body)
+    q = np.concatenate([np.linspace(-50, 50, 200001), np.linspace(-1000, 1000, 20001)]).astype(np.float32)
+    pose = host(fx.frax_fk(h, torch.from_numpy(q[None, :]).cuda()))
+    qd = q.astype(np.float64)
+    assert np.max(np.abs(pose[:, 0] - np.cos(qd))) < 1e-6
+    assert np.max(np.abs(pose[:, 3] - np.sin(qd))) < 1e-6
