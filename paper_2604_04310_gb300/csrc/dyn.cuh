@@ -363,7 +363,7 @@ FD void crba_one(const Img& M, const float* __restrict__ q, float* __restrict__ 
   if (T::kStatic) {
 #pragma unroll
     for (int k = T::NVMAX - 1; k >= 0; --k) {
-      const float rk = 1.f / H[MSink::tri(k, k)];
+      const float rk = rcp(H[MSink::tri(k, k)]);
 #pragma unroll
       for (int i = k - 1; i >= 0; --i) {
         const float a = H[MSink::tri(k, i)] * rk;
@@ -377,7 +377,7 @@ FD void crba_one(const Img& M, const float* __restrict__ q, float* __restrict__ 
   } else {
     const ColT<false> own{col.ld, col.b};  // LD is rewritten in place: read through L2
     for (int k = nv - 1; k >= 0; --k) {
-      const float rk = 1.f / own.in(LD, MSink::tri(k, k));
+      const float rk = rcp(own.in(LD, MSink::tri(k, k)));
       int i = T::dparent(M, k);
       while (i >= 0) {
         const float a = own.in(LD, MSink::tri(k, i)) * rk;
@@ -417,8 +417,8 @@ FD SV spd6_solve(const AI& I, const SV& rhs) {
     float d = A[j][j];
 #pragma unroll
     for (int k = 0; k < j; ++k) d = fmaf(-L[j][k], L[j][k], d);
-    const float sd = sqrtf(d);
-    dinv[j] = 1.f / sd;
+    dinv[j] = rsqrtf(d);
+    const float sd = d * dinv[j];
     L[j][j] = sd;
 #pragma unroll
     for (int i = j + 1; i < 6; ++i) {
@@ -488,7 +488,7 @@ FD void aba_core(const Img& M, const float* __restrict__ q, const float* __restr
     if (i >= nb) continue;
     if (T::kFree && i == 0) continue;
     const SV Ui = ai_col_z(IA[i]);
-    const float di = 1.f / Ui.w.z;
+    const float di = rcp(Ui.w.z);
     const float ui = rhs_at(i) - pA[i].w.z;
     U[i] = Ui;
     Dinv[i] = di;

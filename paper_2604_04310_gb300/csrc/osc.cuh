@@ -146,7 +146,7 @@ FD AI osc_inertias(const Img& M, const float* __restrict__ q, uint64_t path, PL&
       float sn, cs;
       joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
       const SV U = ai_col_z(IA);
-      const float dinv = 1.f / U.w.z;
+      const float dinv = rcp(U.w.z);
       if ((path >> i) & 1ull) {
         P.at(i, 0) = U.w.x; P.at(i, 1) = U.w.y; P.at(i, 2) = U.w.z;
         P.at(i, 3) = U.v.x; P.at(i, 4) = U.v.y; P.at(i, 5) = U.v.z;

@@ -251,7 +251,7 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
           pAt = pAt + pa;
         }
         const SV U = ai_col_z(IA);
-        const float dinv = 1.f / U.w.z;
+        const float dinv = rcp(U.w.z);
         const float u = rhs_at(i) - pAt.w.z;
         P.at(i, 0) = U.w.x;
         P.at(i, 1) = U.w.y;
@@ -433,7 +433,7 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
         // dense L^T D L of the root block, last dof first
 #pragma unroll
         for (int k = 5; k >= 0; --k) {
-          const float rk = 1.f / H[k][k];
+          const float rk = rcp(H[k][k]);
 #pragma unroll
           for (int i = k - 1; i >= 0; --i) {
             const float a = H[k][i] * rk;
@@ -480,7 +480,7 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
         AI Ia;
         if (wantL) {
           const SV U = ai_col_z(IA);
-          const float dinv = 1.f / U.w.z;
+          const float dinv = rcp(U.w.z);
           putL(di, di, U.w.z);
           FL = dinv * U;
           Ia = IA;
@@ -806,7 +806,7 @@ FD void chain_minv(const Img& M, const float* __restrict__ q, const G& g, float*
   }
 #pragma unroll
   for (int k = N - 1; k >= 0; --k) {
-    const float rk = 1.f / H[MSink::tri(k, k)];
+    const float rk = rcp(H[MSink::tri(k, k)]);
 #pragma unroll
     for (int i = k - 1; i >= 0; --i) {
       const float a = H[MSink::tri(k, i)] * rk;
@@ -825,7 +825,7 @@ FD void chain_minv(const Img& M, const float* __restrict__ q, const G& g, float*
   }
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    float x = u[k] / H[MSink::tri(k, k)];
+    float x = u[k] * rcp(H[MSink::tri(k, k)]);
 #pragma unroll
     for (int j = 0; j < k; ++j) x = fmaf(-H[MSink::tri(k, j)], w[j], x);
     w[k] = x;

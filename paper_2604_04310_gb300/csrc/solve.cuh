@@ -32,7 +32,7 @@ FD void ltdl_solve_one(const Img& M, const float* __restrict__ LD, const Rhs& b_
 #pragma unroll(T::kStatic ? T::NVMAX : 1)
   for (int k = 0; k < T::NVMAX; ++k) {
     if (k >= nv) break;
-    float x = y[k] / col.in(LD, MSink::tri(k, k));
+    float x = y[k] * rcp(col.in(LD, MSink::tri(k, k)));
     int j = T::dparent(M, k);
 #pragma unroll(T::kStatic ? T::NVMAX : 1)
     for (int step = 0; step < T::NVMAX; ++step) {

@@ -29,6 +29,16 @@ FD void joint_sincos(float x, float* s, float* c) {
 #endif
 }
 
+// 1 / x by the SFU reciprocal (at most 2 ulp from the rounded quotient, for
+// the pivots and articulated inertias here, all well inside the normal range)
+FD float rcp(float x) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(1.f, x);
+#else
+  return 1.f / x;
+#endif
+}
+
 struct V3 {
   float x, y, z;
 };
