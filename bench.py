@@ -66,8 +66,8 @@ FLOPS = {
 # workload; an entry is removed when its kernel changes. aba_vjp = the factor
 # solve plus the adjoint sweep.
 NCU_TRAFFIC = {
-    "fk_jac": 29.40e6 + 493.34e6, "rnea": 88.13e6 + 8.78e6, "crba_ltdl": 29.42e6 + 267.21e6,
-    "aba": 88.19e6 + 11.31e6, "rnea_vjp": 117.54e6 + 51.05e6, "aba_vjp": 58.76e6 + 2.52e6 + 117.50e6 + 30.95e6,
+    "fk_jac": 29.45e6 + 490.73e6, "rnea": 88.12e6 + 14.14e6, "crba_ltdl": 25.21e6 + 263.52e6,
+    "aba": 92.32e6 + 96.05e6, "rnea_vjp": 117.50e6 + 50.90e6, "aba_vjp": 54.57e6 + 2.86e6 + 117.57e6 + 31.01e6,
 }
 # operational-space control task bodies (the last end frame of each model)
 OSC_TASK = {"chain7": 6, "humanoid": 29}
