@@ -249,7 +249,7 @@ FD void rnea_one(const Img& M, const float* __restrict__ q, const float* __restr
       v[i] = vi;
       a[i] = ai;
     }
-    f[i] = rbi_mul(I, a[i]) + crf(v[i], rbi_mul(I, v[i]));
+    f[i] = crf_add(rbi_mul(I, a[i]), v[i], rbi_mul(I, v[i]));
   }
 #pragma unroll(T::kStatic ? T::NBMAX : 1)
   for (int i = T::NBMAX - 1; i >= 0; --i) {
@@ -588,7 +588,7 @@ FD void rnea_vjp_core(const Img& M, const float* __restrict__ q, const float* __
       Fb[i] = fb;
     }
     a_prev[i] = ai;
-    F[i] = rbi_mul(I, ai) + crf(v[i], rbi_mul(I, v[i]));
+    F[i] = crf_add(rbi_mul(I, ai), v[i], rbi_mul(I, v[i]));
     ab[i] = szero();
     vb[i] = szero();
   }
@@ -598,7 +598,7 @@ FD void rnea_vjp_core(const Img& M, const float* __restrict__ q, const float* __
     const BodyImage& b = M.body[i];
     const RBI I = rbi_of(b);
     const SV abi = ab[i] + rbi_mul(I, Fb[i]);
-    SV vbi = vb[i] - crf(Fb[i], rbi_mul(I, v[i])) - rbi_mul(I, crm(v[i], Fb[i]));
+    SV vbi = crf_sub(vb[i], Fb[i], rbi_mul(I, v[i])) - rbi_mul(I, crm(v[i], Fb[i]));
     if (T::kFree && i == 0) {
       // root: q enters only through X_0 a_g; translation has no effect
       sink.root(cross(abi.v, xa[0].v), vbi, abi);

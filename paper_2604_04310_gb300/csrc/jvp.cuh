@@ -66,8 +66,8 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
       }
       const SV v = bv[0], dv = bdv[0];
       const SV Iv = rbi_mul(I, v);
-      const SV F = rbi_mul(I, ba[0]) + crf(v, Iv) + aF[0];
-      const SV dF = rbi_mul(I, bda[0]) + crf(dv, Iv) + crf(v, rbi_mul(I, dv)) + adF[0];
+      const SV F = crf_add(rbi_mul_add(aF[0], I, ba[0]), v, Iv);
+      const SV dF = crf_add(crf_add(rbi_mul_add(adF[0], I, bda[0]), dv, Iv), v, rbi_mul(I, dv));
       sink.root(F, dF);
       continue;
     }
@@ -129,8 +129,8 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
         const int iv = iv_of<T>(i);
         const float qdi = col.in(qd, iv), dqi = col.in(dq, iv), dqdi = col.in(dqd, iv);
         const SV Iv = rbi_mul(I, v);
-        const SV F = rbi_mul(I, a) + crf(v, Iv) + Fc;
-        const SV dF = rbi_mul(I, da) + crf(dv, Iv) + crf(v, rbi_mul(I, dv)) + dFc;
+        const SV F = crf_add(rbi_mul_add(Fc, I, a), v, Iv);
+        const SV dF = crf_add(crf_add(rbi_mul_add(dFc, I, da), dv, Iv), v, rbi_mul(I, dv));
         sink(i, F.w.z, dF.w.z);
         Fc = frc_out(b, cs, sn, F, dh);
         dFc = frc_out(b, cs, sn, dF + dqi * ez_crf(F), dh);

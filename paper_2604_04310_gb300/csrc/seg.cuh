@@ -56,7 +56,7 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
         SV a0 = SV{mk(0, 0, 0), rotT(P.E, ag.v)};
         if (qdd) a0 = a0 + load6(qdd, 0, col);
         const RBI I = rbi_of(M.body[0]);
-        SV f0 = rbi_mul(I, a0) + crf(v0, rbi_mul(I, v0));
+        SV f0 = crf_add(rbi_mul(I, a0), v0, rbi_mul(I, v0));
         if constexpr (EXT) {
           if (ext_body == 0) f0 = f0 + fext;
         }
@@ -93,7 +93,7 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
           a.w.z += qddi;
           a = a + ez_velprod(v, qdi);
           const RBI I = rbi_of(b);
-          f[k] = rbi_mul(I, a) + crf(v, rbi_mul(I, v));
+          f[k] = crf_add(rbi_mul(I, a), v, rbi_mul(I, v));
           if constexpr (EXT) {
             if (i == ext_body) f[k] = f[k] + fext;
           }
@@ -648,7 +648,6 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
   float sc[NB], ss[NB];
   const SV ag = gravity_acc(M.g);
   V3 gam = mk(0, 0, 0);
-  auto body_force = [&](const RBI& I, const SV& v, const SV& a) { return rbi_mul(I, a) + crf(v, rbi_mul(I, v)); };
 #pragma unroll 1
   for (int t = 0; t < M.n_act; ++t) {
     const int act = M.act[t];
@@ -666,8 +665,8 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
         if (kind == kActOpen) continue;
       }
       const SV v0 = bv[0], Fb0 = bF[0];
-      const SV ab = rbi_mul(I, Fb0) + aab[0];
-      const SV vb = avb[0] - crf(Fb0, rbi_mul(I, v0)) - rbi_mul(I, crm(v0, Fb0));
+      const SV ab = rbi_mul_add(aab[0], I, Fb0);
+      const SV vb = rbi_mul_sub(crf_sub(avb[0], Fb0, rbi_mul(I, v0)), I, crm(v0, Fb0));
       sink.root(cross(ab.v, gam), vb, ab);
       continue;
     }
@@ -723,9 +722,10 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
         const float qdi = col.in(qd, iv_of<T>(i));
         SV xa = a - ez_velprod(v, qdi);
         xa.w.z -= col.in(qdd, iv_of<T>(i));
-        const SV F = body_force(I, v, a) + Fc;
-        const SV ab = rbi_mul(I, Fb) + abc;
-        const SV vb = vbc - crf(Fb, rbi_mul(I, v)) - rbi_mul(I, crm(v, Fb)) + qdi * ez_crf(ab);
+        const SV Iv = rbi_mul(I, v);
+        const SV F = crf_add(rbi_mul_add(Fc, I, a), v, Iv);
+        const SV ab = rbi_mul_add(abc, I, Fb);
+        const SV vb = rbi_mul_sub(crf_sub(vbc, Fb, Iv), I, crm(v, Fb)) + qdi * ez_crf(ab);
         sink(i, dot(Fb, ez_crf(F)) - dot(ab, ez_crm(xa)) - dot(vb, ez_crm(v)), vb.w.z - dot(ab, ez_crm(v)),
              ab.w.z);
         Fc = frc_out(b, cs, sn, F, dh);

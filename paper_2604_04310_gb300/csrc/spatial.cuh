@@ -55,16 +55,32 @@ FD float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 FD V3 cross(V3 a, V3 b) {
   return mk(fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x));
 }
+// c + a x b and c - a x b, each component two FMAs on the accumulator
+FD V3 cross_add(V3 c, V3 a, V3 b) {
+  return mk(fmaf(a.y, b.z, fmaf(-a.z, b.y, c.x)), fmaf(a.z, b.x, fmaf(-a.x, b.z, c.y)),
+            fmaf(a.x, b.y, fmaf(-a.y, b.x, c.z)));
+}
+FD V3 cross_sub(V3 c, V3 a, V3 b) {
+  return mk(fmaf(-a.y, b.z, fmaf(a.z, b.y, c.x)), fmaf(-a.z, b.x, fmaf(a.x, b.z, c.y)),
+            fmaf(-a.x, b.y, fmaf(a.y, b.x, c.z)));
+}
 FD SV operator+(const SV& a, const SV& b) { return SV{a.w + b.w, a.v + b.v}; }
 FD SV operator-(const SV& a, const SV& b) { return SV{a.w - b.w, a.v - b.v}; }
 FD SV operator*(float s, const SV& a) { return SV{s * a.w, s * a.v}; }
 FD float dot(const SV& a, const SV& b) { return dot(a.w, b.w) + dot(a.v, b.v); }
 FD SV szero() { return SV{mk(0, 0, 0), mk(0, 0, 0)}; }
 
-// motion x motion (Table III's x)
-FD SV crm(const SV& a, const SV& b) { return SV{cross(a.w, b.w), cross(a.w, b.v) + cross(a.v, b.w)}; }
+// motion x motion (Table III's x); sums of cross products as FMA chains
+FD SV crm(const SV& a, const SV& b) { return SV{cross(a.w, b.w), cross_add(cross(a.w, b.v), a.v, b.w)}; }
 // motion x* force (Table III's x*)
-FD SV crf(const SV& a, const SV& f) { return SV{cross(a.w, f.w) + cross(a.v, f.v), cross(a.w, f.v)}; }
+FD SV crf(const SV& a, const SV& f) { return SV{cross_add(cross(a.w, f.w), a.v, f.v), cross(a.w, f.v)}; }
+// acc + a x* f and acc - a x* f, accumulated in place
+FD SV crf_add(const SV& acc, const SV& a, const SV& f) {
+  return SV{cross_add(cross_add(acc.w, a.w, f.w), a.v, f.v), cross_add(acc.v, a.w, f.v)};
+}
+FD SV crf_sub(const SV& acc, const SV& a, const SV& f) {
+  return SV{cross_sub(cross_sub(acc.w, a.w, f.w), a.v, f.v), cross_sub(acc.v, a.w, f.v)};
+}
 
 // --- rotations --------------------------------------------------------------
 template <class RT>
@@ -147,19 +163,19 @@ FD void mat_mul_b(const float* E, const BodyImage& b, float* C, bool dh = false)
 // Motion vectors: parent' -> child' coordinates.
 FD SV mot_in(const BodyImage& b, float c, float s, const SV& m, bool dh = false) {
   V3 p = mk(b.p[0], b.p[1], b.p[2]);
-  return SV{rotzT(c, s, rotT_b(b, m.w, dh)), rotzT(c, s, rotT_b(b, m.v - cross(p, m.w), dh))};
+  return SV{rotzT(c, s, rotT_b(b, m.w, dh)), rotzT(c, s, rotT_b(b, cross_sub(m.v, p, m.w), dh))};
 }
 // Force vectors: child' -> parent' coordinates (the transpose of mot_in).
 FD SV frc_out(const BodyImage& b, float c, float s, const SV& f, bool dh = false) {
   V3 p = mk(b.p[0], b.p[1], b.p[2]);
   V3 fl = rot_b(b, rotz(c, s, f.v), dh);
-  return SV{rot_b(b, rotz(c, s, f.w), dh) + cross(p, fl), fl};
+  return SV{cross_add(rot_b(b, rotz(c, s, f.w), dh), p, fl), fl};
 }
 // Motion vectors child' -> parent' (inverse of mot_in); used by adjoints.
 FD SV mot_out(const BodyImage& b, float c, float s, const SV& m, bool dh = false) {
   V3 p = mk(b.p[0], b.p[1], b.p[2]);
   V3 w = rot_b(b, rotz(c, s, m.w), dh);
-  return SV{w, rot_b(b, rotz(c, s, m.v), dh) + cross(p, w)};
+  return SV{w, cross_add(rot_b(b, rotz(c, s, m.v), dh), p, w)};
 }
 
 // e x m and e x* f for e = [z; 0] (the revolute motion subspace)
@@ -179,9 +195,33 @@ FD V3 symv(float xx, float yy, float zz, float xy, float xz, float yz, V3 a) {
   return mk(fmaf(xx, a.x, fmaf(xy, a.y, xz * a.z)), fmaf(xy, a.x, fmaf(yy, a.y, yz * a.z)),
             fmaf(xz, a.x, fmaf(yz, a.y, zz * a.z)));
 }
+// [I_o w + h x v_lin; m v_lin - h x w], each component one FMA chain
 FD SV rbi_mul(const RBI& I, const SV& v) {
-  return SV{symv(I.xx, I.yy, I.zz, I.xy, I.xz, I.yz, v.w) + cross(I.h, v.v),
-            I.m * v.v - cross(I.h, v.w)};
+  const V3 hv = cross(I.h, v.v);
+  const V3 n = mk(fmaf(I.xx, v.w.x, fmaf(I.xy, v.w.y, fmaf(I.xz, v.w.z, hv.x))),
+                  fmaf(I.xy, v.w.x, fmaf(I.yy, v.w.y, fmaf(I.yz, v.w.z, hv.y))),
+                  fmaf(I.xz, v.w.x, fmaf(I.yz, v.w.y, fmaf(I.zz, v.w.z, hv.z))));
+  const V3 f = mk(fmaf(I.m, v.v.x, fmaf(I.h.z, v.w.y, -I.h.y * v.w.z)),
+                  fmaf(I.m, v.v.y, fmaf(I.h.x, v.w.z, -I.h.z * v.w.x)),
+                  fmaf(I.m, v.v.z, fmaf(I.h.y, v.w.x, -I.h.x * v.w.y)));
+  return SV{n, f};
+}
+// acc + I v and acc - I v, accumulated in place
+FD SV rbi_mul_add(const SV& acc, const RBI& I, const SV& v) {
+  const V3 n0 = cross_add(acc.w, I.h, v.v);
+  const V3 n = mk(fmaf(I.xx, v.w.x, fmaf(I.xy, v.w.y, fmaf(I.xz, v.w.z, n0.x))),
+                  fmaf(I.xy, v.w.x, fmaf(I.yy, v.w.y, fmaf(I.yz, v.w.z, n0.y))),
+                  fmaf(I.xz, v.w.x, fmaf(I.yz, v.w.y, fmaf(I.zz, v.w.z, n0.z))));
+  const V3 f0 = cross_sub(acc.v, I.h, v.w);
+  return SV{n, mk(fmaf(I.m, v.v.x, f0.x), fmaf(I.m, v.v.y, f0.y), fmaf(I.m, v.v.z, f0.z))};
+}
+FD SV rbi_mul_sub(const SV& acc, const RBI& I, const SV& v) {
+  const V3 n0 = cross_sub(acc.w, I.h, v.v);
+  const V3 n = mk(fmaf(-I.xx, v.w.x, fmaf(-I.xy, v.w.y, fmaf(-I.xz, v.w.z, n0.x))),
+                  fmaf(-I.xy, v.w.x, fmaf(-I.yy, v.w.y, fmaf(-I.yz, v.w.z, n0.y))),
+                  fmaf(-I.xz, v.w.x, fmaf(-I.yz, v.w.y, fmaf(-I.zz, v.w.z, n0.z))));
+  const V3 f0 = cross_add(acc.v, I.h, v.w);
+  return SV{n, mk(fmaf(-I.m, v.v.x, f0.x), fmaf(-I.m, v.v.y, f0.y), fmaf(-I.m, v.v.z, f0.z))};
 }
 FD RBI rbi_add(const RBI& a, const RBI& b) {
   return RBI{a.m + b.m, a.h + b.h, a.xx + b.xx, a.yy + b.yy, a.zz + b.zz,
