@@ -49,10 +49,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_aba(const __grid_constant__ Model
   aba_one<T>(M, q, qd, tau, qdd, col);
 }
 
-// RNEA adjoint and JVP: trees capped at 8 blocks/SM, the chain's 8-slot
-// image at the compiler's choice (both measured best).
+// RNEA adjoint and JVP: 8 blocks/SM (64 registers), measured best for the
+// chain and the trees.
 template <class T>
-__global__ void __launch_bounds__(kBlock, (T::NBMAX > 8 ? 8 : 1)) k_rnea_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_rnea_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                       int64_t ld, const float* q, const float* qd,
                                                       const float* qdd, const float* gbar, float* qbar,
                                                       float* qdbar, float* qddbar) {
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_aba_ext(const __grid_constant__ M
 
 // Forward-mode derivatives (segment code; chains run it on the 8-slot image).
 template <class T>
-__global__ void __launch_bounds__(kBlock, (T::NBMAX > 8 ? 8 : 1)) k_rnea_jvp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_rnea_jvp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                       int64_t ld, const float* q, const float* qd,
                                                       const float* qdd, const float* dq, const float* dqd,
                                                       const float* dqdd, float* tau, float* dtau) {

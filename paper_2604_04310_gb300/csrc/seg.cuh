@@ -726,8 +726,15 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
         const SV F = crf_add(rbi_mul_add(Fc, I, a), v, Iv);
         const SV ab = rbi_mul_add(abc, I, Fb);
         const SV vb = rbi_mul_sub(crf_sub(vbc, Fb, Iv), I, crm(v, Fb)) + qdi * ez_crf(ab);
-        sink(i, dot(Fb, ez_crf(F)) - dot(ab, ez_crm(xa)) - dot(vb, ez_crm(v)), vb.w.z - dot(ab, ez_crm(v)),
-             ab.w.z);
+        // Fb . (e_z x* F) - ab . (e_z x xa) - vb . (e_z x v): three short FMA
+        // chains (the z parts of these e_z products vanish)
+        const SV ef = ez_crf(F), ea = ez_crm(xa), ev = ez_crm(v);
+        const float q1 = fmaf(Fb.w.x, ef.w.x, fmaf(Fb.w.y, ef.w.y, fmaf(Fb.v.x, ef.v.x, Fb.v.y * ef.v.y)));
+        const float q2 = fmaf(ab.w.x, ea.w.x, fmaf(ab.w.y, ea.w.y, fmaf(ab.v.x, ea.v.x, ab.v.y * ea.v.y)));
+        const float q3 = fmaf(vb.w.x, ev.w.x, fmaf(vb.w.y, ev.w.y, fmaf(vb.v.x, ev.v.x, vb.v.y * ev.v.y)));
+        const float qb = q1 - q2 - q3;
+        const float qdb = fmaf(-ab.w.x, ev.w.x, fmaf(-ab.w.y, ev.w.y, fmaf(-ab.v.x, ev.v.x, fmaf(-ab.v.y, ev.v.y, vb.w.z))));
+        sink(i, qb, qdb, ab.w.z);
         Fc = frc_out(b, cs, sn, F, dh);
         abc = frc_out(b, cs, sn, ab, dh);
         vbc = frc_out(b, cs, sn, vb, dh);
