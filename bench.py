@@ -189,9 +189,8 @@ def make_inputs(robot, B, seed, device):
 
 def kernels_per_call(robot, op):
     """Kernel launches one public call makes: the chain's ABA adjoint runs as
-    the factor solve plus the adjoint sweep; a tree's FK+J and CRBA add the
-    fill of their structural zeros (rows for non-ancestor pairs) when the
-    model has any."""
+    the factor solve plus the adjoint sweep; a tree's FK+J and CRBA add the fill of their
+    structural zeros (rows for non-ancestor pairs) when the model has any."""
     chain7 = robot.n_bodies == 7 and all(int(p) == i - 1 for i, p in enumerate(robot.parent)) \
         and not robot.has_free_root
     if chain7:

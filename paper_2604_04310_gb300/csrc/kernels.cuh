@@ -105,12 +105,15 @@ __global__ void __launch_bounds__(kBlock, 8) k_rnea_seg(const __grid_constant__ 
   FRAX_TID();
   rnea_seg<T>(M, q, qd, qdd, tau, col);
 }
-template <class T>
-__global__ void __launch_bounds__(kBlock, 4) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
-                                                         int64_t B, int64_t ld, const float* q, float* Mout,
-                                                         float* LD) {
+// CRBA on segments; OUT 1: M only, 2: the factor only, 3: both. A call for
+// one output runs the kernel that carries only that sweep's state (fewer
+// registers); for both, one kernel (two would repeat the sweeps: slower).
+template <class T, int OUT>
+__global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : (OUT == 2 ? 6 : 4)) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
+                                                                       int64_t B, int64_t ld, const float* q,
+                                                                       float* Mout, float* LD) {
   FRAX_TID();
-  crba_seg<T, ModelImage<T::NBMAX>, Col, false>(M, q, Mout, LD, col);
+  crba_seg<T, ModelImage<T::NBMAX>, Col, false, OUT>(M, q, Mout, LD, col);
 }
 template <class T>
 __global__ void __launch_bounds__(kBlock, 8) k_aba_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
@@ -197,7 +200,11 @@ cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a)
       else k_rnea<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.qdd, a.out0);
       break;
     case kOpCrba:
-      if constexpr (T::kSeg) k_crba_seg<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
+      if constexpr (T::kSeg) {
+        if (a.out0 && a.out1) k_crba_seg<T, 3><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
+        else if (a.out0) k_crba_seg<T, 1><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, nullptr);
+        else k_crba_seg<T, 2><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, nullptr, a.out1);
+      }
       else k_crba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
       break;
     case kOpAba:

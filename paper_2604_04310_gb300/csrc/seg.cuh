@@ -332,12 +332,12 @@ FD void aba_seg(const Img& M, const float* __restrict__ q, const float* __restri
 // kernel's code small.
 // With ZEROS false the structural zeros (non-ancestor pairs) are left to the
 // caller (a separate fill of those rows, the same for every instance).
-template <class T, class Img, class C, bool ZEROS>
+template <class T, class Img, class C, bool ZEROS, int OUT>
 FRAX_NOINLINE void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mout,
                                            float* __restrict__ LD, const float* sc, const float* ss, C col) {
   const int nv = T::kFree ? M.nb + 5 : M.nb;
   const int di = iv_of<T>(i);
-  const bool wM = Mout != nullptr, wL = LD != nullptr;
+  const bool wM = (OUT & 1) && Mout != nullptr, wL = (OUT & 2) && LD != nullptr;
   auto put = [&](int c, float m, float l) {  // c < di
     if (wM) {
       col.out(Mout, di * nv + c, m);
@@ -374,16 +374,20 @@ FRAX_NOINLINE void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __res
   }
 }
 
-template <class T, class Img, class C, bool ZEROS = true>
+// OUT selects at compile time what the kernel can produce (1: M, 2: the
+// factor, 3: both): a kernel for one of them carries only that sweep's state.
+template <class T, class Img, class C, bool ZEROS = true, int OUT = 3>
 FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ Mout, float* __restrict__ LD,
                  const C& col) {
   constexpr int NB = T::NBMAX;
-  RBI ICa[NB];
-  AI IAa[NB];
+  constexpr bool kM = (OUT & 1) != 0, kL = (OUT & 2) != 0;
+  RBI ICa[kM ? NB : 1];
+  AI IAa[kL ? NB : 1];
   float sc[NB], ss[NB];
   const int nb = M.nb;
   const int nv = T::kFree ? nb + 5 : nb;
-  const bool wantL = LD != nullptr;
+  const bool wantM = kM && Mout != nullptr;
+  const bool wantL = kL && LD != nullptr;
   auto putM = [&](int r, int c, float val) {  // r >= c
     col.out(Mout, r * nv + c, val);
     if (r != c) col.out(Mout, c * nv + r, val);
@@ -402,11 +406,11 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
     const int st = M.seg_start[s], len = M.seg_len[s];
     if (T::kFree && s == 0) {
       if (kind != kActClose) {
-        ICa[0] = rzero;
-        IAa[0] = azero;
+        if constexpr (kM) ICa[0] = rzero;
+        if constexpr (kL) IAa[0] = azero;
       }
       if (kind == kActOpen) continue;
-      if (Mout) {
+      if constexpr (kM) if (wantM) {
         const RBI Cc = rbi_add(rbi_of(M.body[0]), ICa[0]);
         const float blk[6][6] = {{Cc.xx, Cc.xy, Cc.xz, 0.f, -Cc.h.z, Cc.h.y},
                                  {Cc.xy, Cc.yy, Cc.yz, Cc.h.z, 0.f, -Cc.h.x},
@@ -419,7 +423,7 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
 #pragma unroll
           for (int c = 0; c <= r; ++c) putM(r, c, blk[r][c]);
       }
-      if (wantL) {
+      if constexpr (kL) if (wantL) {
         AI A0 = ai_of(rbi_of(M.body[0]));
         ai_add(A0, IAa[0]);
         const float* Af = A0.A;
@@ -457,16 +461,16 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
         joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &ss[i], &sc[i]);
       }
       if (kind == kActOpen) {
-        ICa[last] = rzero;
-        if (wantL) IAa[last] = azero;
+        if constexpr (kM) ICa[last] = rzero;
+        if constexpr (kL) IAa[last] = azero;
         continue;
       }
     }
     RBI Cc = rbi_of(M.body[last]);
     AI IA = ai_of(Cc);
     if (kind == kActClose) {
-      Cc = rbi_add(Cc, ICa[last]);
-      if (wantL) ai_add(IA, IAa[last]);
+      if constexpr (kM) Cc = rbi_add(Cc, ICa[last]);
+      if constexpr (kL) ai_add(IA, IAa[last]);
     }
 #pragma unroll 1
     for (int k = len - 1; k >= 0; --k) {
@@ -474,11 +478,14 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
         const int i = M.order[st + k];
         const int di = iv_of<T>(i);
         const BodyImage& b = M.body[i];
-        const SV FM{mk(Cc.xz, Cc.yz, Cc.zz), mk(-Cc.h.y, Cc.h.x, 0.f)};  // I^c_i e_z
-        if (Mout) col.out(Mout, di * nv + di, FM.w.z);
+        SV FM = szero();
+        if constexpr (kM) {
+          FM = SV{mk(Cc.xz, Cc.yz, Cc.zz), mk(-Cc.h.y, Cc.h.x, 0.f)};  // I^c_i e_z
+          if (wantM) col.out(Mout, di * nv + di, FM.w.z);
+        }
         SV FL = szero();
         AI Ia;
-        if (wantL) {
+        if constexpr (kL) if (wantL) {
           const SV U = ai_col_z(IA);
           const float dinv = rcp(U.w.z);
           putL(di, di, U.w.z);
@@ -487,25 +494,26 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
           ai_rank1_sub(Ia, U, dinv);
           ai_out(b, sc[i], ss[i], Ia);
         }
-        crba_emit_row<T, Img, C, ZEROS>(M, i, FM, FL, Mout, LD, sc, ss, col);
-        const RBI up = rbi_out(b, sc[i], ss[i], Cc);
-        if (k > 0) {
-          const RBI Ip = rbi_of(M.body[M.order[st + k - 1]]);
-          Cc = rbi_add(Ip, up);
-          if (wantL) {
+        crba_emit_row<T, Img, C, ZEROS, OUT>(M, i, FM, FL, Mout, LD, sc, ss, col);
+        const RBI Ip = rbi_of(M.body[M.order[st + (k > 0 ? k - 1 : 0)]]);
+        if constexpr (kM) {
+          const RBI up = rbi_out(b, sc[i], ss[i], Cc);
+          Cc = k > 0 ? rbi_add(Ip, up) : up;
+        }
+        if constexpr (kL) if (wantL) {
+          if (k > 0) {
             IA = ai_of(Ip);
             ai_add(IA, Ia);
+          } else {
+            IA = Ia;
           }
-        } else {
-          Cc = up;
-          if (wantL) IA = Ia;
         }
       }
     }
     const int p = M.seg_parent[s];
     if (p >= 0) {
-      ICa[p] = rbi_add(ICa[p], Cc);
-      if (wantL) ai_add(IAa[p], IA);
+      if constexpr (kM) ICa[p] = rbi_add(ICa[p], Cc);
+      if constexpr (kL) if (wantL) ai_add(IAa[p], IA);
     }
   }
 }

@@ -328,3 +328,15 @@ def test_joint_angle_sin_cos_accuracy():
     qd = q.astype(np.float64)
     assert np.max(np.abs(pose[:, 0] - np.cos(qd))) < 1e-6
     assert np.max(np.abs(pose[:, 3] - np.sin(qd))) < 1e-6
+
+
+@pytest.mark.parametrize("name", ["humanoid", "tree_big"])
+def test_crba_single_outputs_match_both(fxm, name):
+    """M alone, the factor alone and both at once (three kernel variants on
+    trees) give the same bits."""
+    m, h = MODELS[name], fxm[name]
+    s, d = states(m, 200, 43)
+    M, LD = fx.frax_crba(h, d["q"], want_M=True, want_LD=True)
+    M1, _ = fx.frax_crba(h, d["q"], want_M=True, want_LD=False)
+    _, LD1 = fx.frax_crba(h, d["q"], want_M=False, want_LD=True)
+    assert torch.equal(M, M1) and torch.equal(LD, LD1)
