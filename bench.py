@@ -380,6 +380,49 @@ def run_cpu_baseline(seconds):
     return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
 
 
+def cpu_model():
+    """The host CPU's model string (x86: model name; Arm: implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model name"):
+        for line in info.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    parts = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = (x.strip() for x in line.split(":", 1))
+            parts.setdefault(k, v)
+    if "CPU part" in parts:
+        return f"Arm implementer {parts.get('CPU implementer', '?')} part {parts['CPU part']}"
+    return "unknown"
+
+
+def run_cpu_baseline_all_cores(seconds):
+    """The same oracle timing in one single-threaded process per host core,
+    all at once; the value sums their rates."""
+    n = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--cpu-seconds",
+                               str(seconds)], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env,
+                              cwd=ROOT) for _ in range(n)]
+    total, inst = 0.0, 0
+    for p in procs:
+        out, _ = p.communicate()
+        for line in out.splitlines()[::-1]:
+            if line.startswith("{"):
+                d = json.loads(line)
+                total += d["value"] or 0.0
+                inst += int(d["sample"].split()[0])
+                break
+    return {"value": total, "unit": UNIT, "cores": n, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"{n} single-threaded processes at once, {inst} instances of the 7-DoF chain in all, "
+                      f"all 6 ops, FP64 numpy oracle, {seconds:.0f} s each"}
+
+
 SERVE_OPS = ["rnea", "crba", "aba", "rnea_grad"]
 
 
@@ -653,9 +696,11 @@ def frax_arm(args, rank, world, local_rank):
     if rank == 0 and not args.no_serve:
         serve = serve_stream(fx, args.serve_seconds)
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = run_cpu_baseline(args.cpu_seconds)
+        cpu["cpu_model"] = cpu_model()
+        cpu_all = run_cpu_baseline_all_cores(min(10.0, args.cpu_seconds))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -666,7 +711,8 @@ def frax_arm(args, rank, world, local_rank):
                            "global_batch": B * world, "parallelism": f"replicas x{world}",
                            "l2": "256 MB buffer written between steps (L2 flush)"},
                 "clocks": clk, "gpu_launches": launches, "wall_s": wall, "per_op": per_op, "roofline": roofline,
-                "e2e": e2e, "humanoid": humanoid, "next_rows": nxt, "cpu_baseline": cpu, "serving": serve}
+                "e2e": e2e, "humanoid": humanoid, "next_rows": nxt, "cpu_baseline": cpu,
+                "cpu_baseline_all_cores": cpu_all, "serving": serve}
         print(json.dumps(line))
 
 

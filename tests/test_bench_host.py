@@ -41,3 +41,9 @@ def test_cpu_baseline_child_and_reference_arm():
                        timeout=300)
     d = json.loads(r.stdout.strip().splitlines()[-1])
     assert d["impl"] == "reference" and d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_all_cores_sums_processes():
+    r = bench.run_cpu_baseline_all_cores(1.0)
+    assert r["cores"] == (os.cpu_count() or 1) and r["value"] > 0 and r["kind"] == "oracle"
+    assert "single-threaded processes" in r["sample"] and r["cpu_model"]
