@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_rnea_seg(const __grid_constant__ 
 // one output runs the kernel that carries only that sweep's state (fewer
 // registers); for both, one kernel (two would repeat the sweeps: slower).
 template <class T, int OUT>
-__global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : (OUT == 2 ? 6 : 4)) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
+__global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : 6) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
                                                                        int64_t B, int64_t ld, const float* q,
                                                                        float* Mout, float* LD) {
   FRAX_TID();

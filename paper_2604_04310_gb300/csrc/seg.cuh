@@ -140,20 +140,15 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
 }
 
 // ======================================================================= ABA
-// Between the inward and the final outward sweep every body needs U, 1/D and
-// u (8 floats). They go to a per-thread slice of shared memory (P3Smem,
-// [body][field][thread] so a warp's accesses hit 32 banks) when the kernel
-// provides one, else to thread-local memory (P3Local). The outward sweep
-// recomputes the joint sin/cos and velocities rather than storing them.
-struct P3Smem {
-  float* base;  // this thread's first word
-  int stride;   // threads per block
-  FD float& at(int i, int f) const { return base[(i * 8 + f) * stride]; }
-};
+// Between the inward and the final outward sweep every body needs U / D and
+// u / D (U = I^A e_z, D = U_z, u = tau - e_z^T p^A): the outward step is then
+// qdd_i = u/D - (U/D)^T a', and (U/D)_z = 1 is not stored, so 6 floats per
+// body in thread-local memory. The outward sweep recomputes the joint sin/cos
+// and velocities rather than storing them.
 template <int NB>
 struct P3Local {
-  float v[NB * 8];
-  FD float& at(int i, int f) { return v[i * 8 + f]; }
+  float v[NB * 6];
+  FD float& at(int i, int f) { return v[i * 6 + f]; }
 };
 
 template <class T, class Img, bool VEL, class Rhs, class Out, class C, class P3>
@@ -169,11 +164,13 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
   for (int k = 0; k < 6; ++k) { azero.A[k] = 0.f; azero.C[k] = 0.f; }
 #pragma unroll
   for (int k = 0; k < 9; ++k) azero.B[k] = 0.f;
+  uint64_t opened = 0;  // segments with child segments: their tips' accelerations are kept
 #pragma unroll 1
   for (int t = 0; t < M.n_act; ++t) {
     const int act = M.act[t];
     const int s = act & 63, kind = act >> 6;
     const int st = M.seg_start[s], len = M.seg_len[s];
+    if (kind == kActOpen) opened |= 1ull << s;
     if (T::kFree && s == 0) {
       const RBI I0 = rbi_of(M.body[0]);
       if (kind != kActClose) {
@@ -252,18 +249,18 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         }
         const SV U = ai_col_z(IA);
         const float dinv = rcp(U.w.z);
-        const float u = rhs_at(i) - pAt.w.z;
-        P.at(i, 0) = U.w.x;
-        P.at(i, 1) = U.w.y;
-        P.at(i, 2) = U.w.z;
-        P.at(i, 3) = U.v.x;
-        P.at(i, 4) = U.v.y;
-        P.at(i, 5) = U.v.z;
-        P.at(i, 6) = dinv;
-        P.at(i, 7) = u;
+        const float ud = (rhs_at(i) - pAt.w.z) * dinv;
+        SV Ud = dinv * U;
+        Ud.w.z = 1.f;
+        P.at(i, 0) = Ud.w.x;
+        P.at(i, 1) = Ud.w.y;
+        P.at(i, 2) = Ud.v.x;
+        P.at(i, 3) = Ud.v.y;
+        P.at(i, 4) = Ud.v.z;
+        P.at(i, 5) = ud;
         Ia = IA;
-        ai_rank1_sub(Ia, U, dinv);
-        pa = pAt + ai_mul(Ia, cb) + (u * dinv) * U;
+        ai_rank1_sub_d(Ia, Ud, U);
+        pa = pAt + ai_mul(Ia, cb) + ud * U;
         ai_out(b, ck, sk, Ia, dh);
         pa = frc_out(b, ck, sk, pa, dh);
         if (VEL && k > 0) {
@@ -301,13 +298,13 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
           cb = ez_velprod(vv, qdi);
         }
         a = mot_in(b, cs, sn, a, dh) + cb;
-        const SV U{mk(P.at(i, 0), P.at(i, 1), P.at(i, 2)), mk(P.at(i, 3), P.at(i, 4), P.at(i, 5))};
-        const float x = (P.at(i, 7) - dot(U, a)) * P.at(i, 6);
+        const float x = P.at(i, 5) - (fmaf(P.at(i, 0), a.w.x, fmaf(P.at(i, 1), a.w.y, a.w.z)) +
+                                      fmaf(P.at(i, 2), a.v.x, fmaf(P.at(i, 3), a.v.y, P.at(i, 4) * a.v.z)));
         a.w.z += x;
         out_at(i, x);
       });
     }
-    bA[M.order[st + len - 1]] = a;
+    if ((opened >> s) & 1ull) bA[M.order[st + len - 1]] = a;
   }
 }
 
@@ -328,12 +325,11 @@ FD void aba_seg(const Img& M, const float* __restrict__ q, const float* __restri
 // updated in place.
 // Emits body i's row of M and/or L: S_j^T F at every ancestor dof j (the
 // forces carried to the root through the joint transforms) and zeros at the
-// dofs of non-ancestors. Not inlined: called once per body, it keeps the
-// kernel's code small.
+// dofs of non-ancestors.
 // With ZEROS false the structural zeros (non-ancestor pairs) are left to the
 // caller (a separate fill of those rows, the same for every instance).
 template <class T, class Img, class C, bool ZEROS, int OUT>
-FRAX_NOINLINE void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mout,
+FD void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mout,
                                            float* __restrict__ LD, const float* sc, const float* ss, C col) {
   const int nv = T::kFree ? M.nb + 5 : M.nb;
   const int di = iv_of<T>(i);

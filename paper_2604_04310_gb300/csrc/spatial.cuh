@@ -10,11 +10,6 @@
 namespace frax {
 
 #define FD __host__ __device__ __forceinline__
-#if defined(__CUDACC__)
-#define FRAX_NOINLINE __host__ __device__ __noinline__
-#else
-#define FRAX_NOINLINE __attribute__((noinline))
-#endif
 
 // sin and cos of a joint angle: reduced to [-pi, pi] by 2 pi split in two
 // parts (Cody and Waite's additive reduction), then the SFU approximations
@@ -380,6 +375,22 @@ FD void ai_add(AI& a, const AI& b) {
 // column z of the angular part: I e_z = [A[:,2]; B[2,:]^T]
 FD SV ai_col_z(const AI& I) { return SV{mk(I.A[4], I.A[5], I.A[2]), mk(I.B[6], I.B[7], I.B[8])}; }
 // I -= u u^T * k
+// I -= d u^T for d = k u given (the ABA's U / D): no scaling left to do
+FD void ai_rank1_sub_d(AI& I, const SV& d, const SV& u) {
+  const float a[6] = {u.w.x, u.w.y, u.w.z, u.v.x, u.v.y, u.v.z};
+  const float e[6] = {d.w.x, d.w.y, d.w.z, d.v.x, d.v.y, d.v.z};
+  const int si[6] = {0, 1, 2, 0, 0, 1}, sj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    I.A[t] = fmaf(-e[si[t]], a[sj[t]], I.A[t]);
+    I.C[t] = fmaf(-e[3 + si[t]], a[3 + sj[t]], I.C[t]);
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) I.B[3 * r + c] = fmaf(-e[r], a[3 + c], I.B[3 * r + c]);
+}
+
 FD void ai_rank1_sub(AI& I, const SV& u, float k) {
   float a[6] = {u.w.x, u.w.y, u.w.z, u.v.x, u.v.y, u.v.z};
   const int si[6] = {0, 1, 2, 0, 0, 1}, sj[6] = {0, 1, 2, 1, 2, 2};
