@@ -276,9 +276,15 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
       pAa[p] = pAa[p] + pa;
     }
   }
-  // outward sweep: accelerations, segment by segment in topological order
+  // outward sweep: accelerations, segment by segment in the reverse of the
+  // order in which the inward sweep finished them (a parent still comes
+  // before its children): the factors written last, still in L2, are read
+  // first
 #pragma unroll 1
-  for (int s = (T::kFree ? 1 : 0); s < M.n_seg; ++s) {
+  for (int t = M.n_act - 1; t >= 0; --t) {
+    const int act = M.act[t];
+    const int s = act & 63;
+    if ((act >> 6) == kActOpen || (T::kFree && s == 0)) continue;
     const int st = M.seg_start[s], len = M.seg_len[s];
     const int p = M.seg_parent[s];
     SV a = p < 0 ? ag : bA[p];
