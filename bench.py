@@ -189,8 +189,9 @@ def make_inputs(robot, B, seed, device):
 
 def kernels_per_call(robot, op):
     """Kernel launches one public call makes: the chain's ABA adjoint runs as
-    the factor solve plus the adjoint sweep; a tree's FK+J and CRBA add the fill of their
-    structural zeros (rows for non-ancestor pairs) when the model has any."""
+    the factor solve plus the adjoint sweep; a tree's FK+J adds the fill of its
+    structural zeros (rows for non-ancestor frame bodies) when it has any (the
+    tree CRBA kernel writes its own)."""
     chain7 = robot.n_bodies == 7 and all(int(p) == i - 1 for i, p in enumerate(robot.parent)) \
         and not robot.has_free_root
     if chain7:
@@ -199,11 +200,8 @@ def kernels_per_call(robot, op):
     for i, p in enumerate(robot.parent):
         anc.append((anc[int(p)] if p >= 0 else 0) | (1 << i))
     bodies = range(robot.n_bodies)
-    unrelated = any(not (anc[a] >> b) & 1 and not (anc[b] >> a) & 1 for a in bodies for b in bodies)
     if op == "fk_jac":
         return 1 + any(not (anc[f] >> b) & 1 for f in robot.end_frames for b in bodies)
-    if op == "crba_ltdl":
-        return 1 + unrelated
     return 1
 
 

@@ -55,8 +55,9 @@ frax_status dispatch(frax_model_t model, frax::Op op, const frax::OpArgs& a, con
   return ok();
 }
 
-// Structural zeros of a tree's outputs, written by one row fill after the
-// per-instance kernel (which skips them). ZeroRows is large (14 KB): one
+// Structural zeros of a tree's outputs: the Jacobian's by one row fill after
+// the per-instance kernel (which skips them), M's and the factor's by the
+// CRBA kernel itself from the same row list. ZeroRows is large (14 KB): one
 // per thread, reused.
 frax_status fill_zeros(frax::ZeroRows& z, float* base0, float* base1, const frax::OpArgs& a, const char* fn) {
   const cudaError_t e = frax::launch_zero_rows(z, base0, base1, a.ld, a.B, a.stream);
@@ -175,17 +176,18 @@ frax_status frax_crba(frax_model_t model, int64_t B, int64_t ld, const float* q,
   if (!M && !LD) return fail(FRAX_EINVAL, "frax_crba: M and LD are both NULL");
   frax::OpArgs a;
   a.B = B; a.ld = ld; a.q = q; a.out0 = M; a.out1 = LD; a.stream = static_cast<cudaStream_t>(stream);
-  FRAX_TRY(dispatch(model, frax::kOpCrba, a, "frax_crba"));
   const frax::HostModel& m = model->m;
-  if (m.kind == frax::kKindChain) return ok();
-  frax::ZeroRows& z = g_zero_rows;
-  z.n0 = z.n = 0;
-  if (M)
-    for (uint16_t r : m.zero_M) z.row[z.n++] = r;
-  z.n0 = z.n;
-  if (LD)
-    for (uint16_t r : m.zero_LD) z.row[z.n++] = r;
-  return fill_zeros(z, M, LD, a, "frax_crba");
+  if (m.kind != frax::kKindChain) {  // the tree kernel writes the structural zeros too
+    frax::ZeroRows& z = g_zero_rows;
+    z.n0 = z.n = 0;
+    if (M)
+      for (uint16_t r : m.zero_M) z.row[z.n++] = r;
+    z.n0 = z.n;
+    if (LD)
+      for (uint16_t r : m.zero_LD) z.row[z.n++] = r;
+    a.zeros = &z;
+  }
+  return dispatch(model, frax::kOpCrba, a, "frax_crba");
 }
 
 frax_status frax_aba(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,

@@ -108,12 +108,20 @@ __global__ void __launch_bounds__(kBlock, 8) k_rnea_seg(const __grid_constant__ 
 // CRBA on segments; OUT 1: M only, 2: the factor only, 3: both. A call for
 // one output runs the kernel that carries only that sweep's state (fewer
 // registers); for both, one kernel (two would repeat the sweeps: slower).
+// The structural zeros (the same entries for every instance) are written by
+// the same threads after their sweeps, from the row list Z: the stores fill
+// the memory system while other warps compute.
 template <class T, int OUT>
 __global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : 6) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
-                                                                       int64_t B, int64_t ld, const float* q,
-                                                                       float* Mout, float* LD) {
+                                                                       const __grid_constant__ ZeroRows Z, int64_t B,
+                                                                       int64_t ld, const float* q, float* Mout,
+                                                                       float* LD) {
   FRAX_TID();
   crba_seg<T, ModelImage<T::NBMAX>, Col, false, OUT>(M, q, Mout, LD, col);
+#pragma unroll 4
+  for (int r = 0; r < Z.n0; ++r) col.out(Mout, Z.row[r], 0.f);
+#pragma unroll 4
+  for (int r = Z.n0; r < Z.n; ++r) col.out(LD, Z.row[r], 0.f);
 }
 template <class T>
 __global__ void __launch_bounds__(kBlock, 8) k_aba_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
@@ -201,9 +209,11 @@ cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a)
       break;
     case kOpCrba:
       if constexpr (T::kSeg) {
-        if (a.out0 && a.out1) k_crba_seg<T, 3><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
-        else if (a.out0) k_crba_seg<T, 1><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, nullptr);
-        else k_crba_seg<T, 2><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, nullptr, a.out1);
+        static const ZeroRows kNone{};
+        const ZeroRows& Z = a.zeros ? *a.zeros : kNone;
+        if (a.out0 && a.out1) k_crba_seg<T, 3><<<grid, block, 0, a.stream>>>(img, Z, a.B, a.ld, a.q, a.out0, a.out1);
+        else if (a.out0) k_crba_seg<T, 1><<<grid, block, 0, a.stream>>>(img, Z, a.B, a.ld, a.q, a.out0, nullptr);
+        else k_crba_seg<T, 2><<<grid, block, 0, a.stream>>>(img, Z, a.B, a.ld, a.q, nullptr, a.out1);
       }
       else k_crba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
       break;

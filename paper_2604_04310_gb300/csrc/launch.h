@@ -16,6 +16,15 @@ struct FramesArg {
   int body[8];
 };
 
+// Rows (entries of an SoA output) to be zeroed: rows [0, n0) of the first
+// array, [n0, n) of the second. Sized for M and the packed factor of the
+// largest model (69 x 69 + 69 x 70 / 2 entries).
+constexpr int kMaxZeroRows = kMaxDofs * kMaxDofs + kMaxDofs * (kMaxDofs + 1) / 2;
+struct ZeroRows {
+  int32_t n0 = 0, n = 0;
+  uint16_t row[kMaxZeroRows];
+};
+
 struct OpArgs {
   int64_t B = 0, ld = 0;
   const float* q = nullptr;
@@ -33,17 +42,10 @@ struct OpArgs {
   float* out1 = nullptr;  // J / LD / qdbar / Lambda
   float* out2 = nullptr;  // qddbar / taubar
   FramesArg frames{0, {0}};  // kOpOsc: body[0] is the task body
+  const ZeroRows* zeros = nullptr;  // kOpCrba on trees: structural zeros the kernel writes
   cudaStream_t stream = nullptr;
 };
 
-// Rows (entries of an SoA output) to be zeroed: rows [0, n0) of the first
-// array, [n0, n) of the second. Sized for M and the packed factor of the
-// largest model (69 x 69 + 69 x 70 / 2 entries).
-constexpr int kMaxZeroRows = kMaxDofs * kMaxDofs + kMaxDofs * (kMaxDofs + 1) / 2;
-struct ZeroRows {
-  int32_t n0 = 0, n = 0;
-  uint16_t row[kMaxZeroRows];
-};
 cudaError_t launch_zero_rows(const ZeroRows& z, float* base0, float* base1, int64_t ld, int64_t B,
                              cudaStream_t stream);
 
