@@ -81,6 +81,15 @@ struct ColT {
 };
 using Col = ColT<true>;
 
+// Asks L2 for this instance's n entries of p (one line per warp and entry)
+// ahead of a sweep that reads them one body at a time.
+template <class C>
+FD void prefetch_entries(const float* p, int n, const C& col) {
+#ifdef __CUDA_ARCH__
+  for (int k = 0; k < n; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + k * col.ld + col.b));
+#endif
+}
+
 // Whether body i's R takes the Rot_x form here: always after the first body
 // of a chain (known once the loops are unrolled), from the image when the
 // topology asks for it, else never.

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : 6) k_crba_seg(const __g
                                                                        int64_t ld, const float* q, float* Mout,
                                                                        float* LD) {
   FRAX_TID();
+  prefetch_entries(q, M.nq, col);  // measured: helps here, not in the kernels that also read qd, tau
   crba_seg<T, ModelImage<T::NBMAX>, Col, false, OUT>(M, q, Mout, LD, col);
 #pragma unroll 4
   for (int r = 0; r < Z.n0; ++r) col.out(Mout, Z.row[r], 0.f);

@@ -31,14 +31,6 @@
 
 namespace frax {
 
-FD int low_bit(uint64_t m) {
-#ifdef __CUDA_ARCH__
-  return __ffsll(static_cast<long long>(m)) - 1;
-#else
-  return __builtin_ctzll(m);
-#endif
-}
-
 // Dense [[A, B], [B^T, C]] of a symmetric 6x6 tensor.
 FD void ai_dense(const AI& I, float A[6][6]) {
   const float* Af = I.A;

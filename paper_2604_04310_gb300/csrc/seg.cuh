@@ -617,6 +617,25 @@ FD void fk_seg(const Img& M, const float* __restrict__ q, float* __restrict__ po
       const uint64_t anc = M.anc[kf];
       const int base = f * 6 * nv;
       const V3 pk = ps[kf];
+      if constexpr (!ZEROS) {  // the ancestors' columns only
+        uint64_t rest = anc;
+        if (T::kFree) {  // the root is an ancestor of every body
+          const V3 d = pk - p0;
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            const V3 zr = mk(R0[m], R0[3 + m], R0[6 + m]);
+            jcol(base, m, true, zr, cross(zr, d));
+            jcol(base, 3 + m, true, mk(0, 0, 0), zr);
+          }
+          rest &= ~1ull;
+        }
+#pragma unroll 1
+        for (; rest; rest &= rest - 1) {
+          const int j = low_bit(rest);
+          jcol(base, iv_of<T>(j), true, zs[j], cross(zs[j], pk - ps[j]));
+        }
+        continue;
+      }
 #pragma unroll 1
       for (int j = 0; j < nb; ++j) {
         const bool on = (anc >> j) & 1ull;

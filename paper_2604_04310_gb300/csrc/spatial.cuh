@@ -11,6 +11,15 @@ namespace frax {
 
 #define FD __host__ __device__ __forceinline__
 
+// index of the lowest set bit of a non-zero mask
+FD int low_bit(uint64_t m) {
+#ifdef __CUDA_ARCH__
+  return __ffsll(static_cast<long long>(m)) - 1;
+#else
+  return __builtin_ctzll(m);
+#endif
+}
+
 // sin and cos of a joint angle: reduced to [-pi, pi] by 2 pi split in two
 // parts (Cody and Waite's additive reduction), then the SFU approximations
 // (absolute error below 5e-7 on [-pi, pi]). Host builds call sincosf.
