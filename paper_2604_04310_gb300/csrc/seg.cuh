@@ -143,13 +143,17 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
 // Between the inward and the final outward sweep every body needs U / D and
 // u / D (U = I^A e_z, D = U_z, u = tau - e_z^T p^A): the outward step is then
 // qdd_i = u/D - (U/D)^T a', and (U/D)_z = 1 is not stored, so 6 floats per
-// body in thread-local memory. The outward sweep recomputes the joint sin/cos
-// and velocities rather than storing them.
+// body. The outward sweep recomputes the joint sin/cos and velocities rather
+// than storing them.
 template <int NB>
-struct P3Local {
+struct P3Local {  // all in thread-local memory
   float v[NB * 6];
-  FD float& at(int i, int f) { return v[i * 6 + f]; }
+  FD void put(int i, int f, float x) { v[i * 6 + f] = x; }
+  FD float get(int i, int f) const { return v[i * 6 + f]; }
 };
+// (Holding the first bodies' factors in shared memory instead, with the
+// occupancy that leaves, measured 22-36 % slower: the shared memory comes out
+// of the L1 that serves the thread-local arrays.)
 
 template <class T, class Img, bool VEL, class Rhs, class Out, class C, class P3>
 FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __restrict__ qd, const Rhs& rhs_at,
@@ -252,12 +256,12 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         const float ud = (rhs_at(i) - pAt.w.z) * dinv;
         SV Ud = dinv * U;
         Ud.w.z = 1.f;
-        P.at(i, 0) = Ud.w.x;
-        P.at(i, 1) = Ud.w.y;
-        P.at(i, 2) = Ud.v.x;
-        P.at(i, 3) = Ud.v.y;
-        P.at(i, 4) = Ud.v.z;
-        P.at(i, 5) = ud;
+        P.put(i, 0, Ud.w.x);
+        P.put(i, 1, Ud.w.y);
+        P.put(i, 2, Ud.v.x);
+        P.put(i, 3, Ud.v.y);
+        P.put(i, 4, Ud.v.z);
+        P.put(i, 5, ud);
         Ia = IA;
         ai_rank1_sub_d(Ia, Ud, U);
         pa = pAt + ai_mul(Ia, cb) + ud * U;
@@ -304,8 +308,8 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
           cb = ez_velprod(vv, qdi);
         }
         a = mot_in(b, cs, sn, a, dh) + cb;
-        const float x = P.at(i, 5) - (fmaf(P.at(i, 0), a.w.x, fmaf(P.at(i, 1), a.w.y, a.w.z)) +
-                                      fmaf(P.at(i, 2), a.v.x, fmaf(P.at(i, 3), a.v.y, P.at(i, 4) * a.v.z)));
+        const float x = P.get(i, 5) - (fmaf(P.get(i, 0), a.w.x, fmaf(P.get(i, 1), a.w.y, a.w.z)) +
+                                       fmaf(P.get(i, 2), a.v.x, fmaf(P.get(i, 3), a.v.y, P.get(i, 4) * a.v.z)));
         a.w.z += x;
         out_at(i, x);
       });

@@ -260,7 +260,8 @@ def test_ltdl_solve_and_inverse(fxm, name):
 def test_structural_zeros_are_written(fxm, name):
     """Outputs pre-filled with NaN: every entry of J, M and the factor is
     written, the structural zeros (non-ancestor pairs, the same for every
-    instance) by the row fill, the rest by the per-instance kernels."""
+    instance) included: the Jacobian's by the row fill, M's and the factor's
+    by the CRBA kernel's own threads, for each of its three output variants."""
     m, h = MODELS[name], fxm[name]
     B = 300
     s, d = states(m, B, 27)
@@ -277,6 +278,9 @@ def test_structural_zeros_are_written(fxm, name):
     LD2 = nan(m.nv * (m.nv + 1) // 2)
     fx.frax_crba(h, d["q"], LD=LD2, want_M=False)
     assert torch.equal(LD2, LD)
+    M2 = nan(m.nv * m.nv)
+    fx.frax_crba(h, d["q"], M=M2, want_LD=False)
+    assert torch.equal(M2, M)
 
 
 @pytest.mark.parametrize("name,B", [("chain7", 65536), ("humanoid", 16384)])
