@@ -59,6 +59,15 @@ FD int iq_of(int i) { return (T::kFree && i > 0) ? i + 6 : i; }
 // kNC = true loads through the read-only (non-coherent) path; false loads
 // through L2 only (ld.cg), for memory a running kernel sees rewritten by
 // copies (the serving slab).
+// streaming store (evict-first in L2) of a value written once
+FD void st_cs(float* p, float v) {
+#ifdef __CUDA_ARCH__
+  __stcs(p, v);
+#else
+  *p = v;
+#endif
+}
+
 template <bool kNC>
 struct ColT {
   int64_t ld, b;
@@ -71,13 +80,7 @@ struct ColT {
   }
   // outputs are written once and not read again by the kernel that writes
   // them (except through ColT<false>): streaming stores (evict-first in L2)
-  FD void out(float* __restrict__ p, int k, float v) const {
-#ifdef __CUDA_ARCH__
-    __stcs(p + k * ld + b, v);
-#else
-    p[k * ld + b] = v;
-#endif
-  }
+  FD void out(float* __restrict__ p, int k, float v) const { st_cs(p + k * ld + b, v); }
 };
 using Col = ColT<true>;
 

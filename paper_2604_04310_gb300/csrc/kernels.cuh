@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_rnea_seg(const __grid_constant__ 
 // the same threads after their sweeps, from the row list Z: the stores fill
 // the memory system while other warps compute.
 template <class T, int OUT>
-__global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : 6) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
+__global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : (OUT == 3 ? 5 : 6)) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
                                                                        const __grid_constant__ ZeroRows Z, int64_t B,
                                                                        int64_t ld, const float* q, float* Mout,
                                                                        float* LD) {

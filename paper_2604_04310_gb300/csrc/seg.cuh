@@ -344,12 +344,18 @@ FD void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mou
   const int nv = T::kFree ? M.nb + 5 : M.nb;
   const int di = iv_of<T>(i);
   const bool wM = (OUT & 1) && Mout != nullptr, wL = (OUT & 2) && LD != nullptr;
+  // this instance's row di of M, column di of M and row di of the factor:
+  // entry c of each one multiply and one add away
+  float* const rowM = wM ? Mout + int64_t(di) * nv * col.ld + col.b : nullptr;
+  float* const colM = wM ? Mout + int64_t(di) * col.ld + col.b : nullptr;
+  float* const rowL = wL ? LD + int64_t(MSink::tri(di, 0)) * col.ld + col.b : nullptr;
+  const int64_t ldM = int64_t(nv) * col.ld;
   auto put = [&](int c, float m, float l) {  // c < di
     if (wM) {
-      col.out(Mout, di * nv + c, m);
-      col.out(Mout, c * nv + di, m);
+      st_cs(rowM + c * col.ld, m);
+      st_cs(colM + c * ldM, m);
     }
-    if (wL) col.out(LD, MSink::tri(di, c), l);
+    if (wL) st_cs(rowL + c * col.ld, l);
   };
   int j = i;
   while (true) {
