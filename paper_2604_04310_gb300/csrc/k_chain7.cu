@@ -1,5 +1,5 @@
 // Serial chains of 7 revolute bodies: topology compiled in, registers only
-// (the adjoints run the segment code on the same chain).
+// (OSC and the JVPs run the segment code on the same chain).
 #include "kernels.cuh"
 
 namespace frax {
@@ -85,9 +85,21 @@ __global__ void __launch_bounds__(kBlock) k_aba_vjp_tail_chain7(const __grid_con
                                                                  const float* qdd, const float* w, float* qbar,
                                                                  float* qdbar) {
   FRAX_TID();
-  using S = SegTopo<8, false>;
-  rnea_vjp_seg<S>(M, q, qd, qdd, RhsFromGlobal<S, Col>{w, col}, vjp_sink<S>(M, q, qbar, qdbar, nullptr, -1.f, col),
-                  col);
+  using T = ChainTopo<7>;
+  rnea_vjp_chain<7>(M, q, qd, qdd, RhsFromGlobal<T, Col>{w, col}, vjp_sink<T>(M, q, qbar, qdbar, nullptr, -1.f, col),
+                    col);
+}
+
+// 7-body chains: the RNEA adjoint, both sweeps unrolled. No register cap:
+// at 95 registers (5 blocks per SM) it ran faster than capped at 72 or 64.
+__global__ void __launch_bounds__(kBlock) k_rnea_vjp_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+                                                              int64_t ld, const float* q, const float* qd,
+                                                              const float* qdd, const float* gbar, float* qbar,
+                                                              float* qdbar, float* qddbar) {
+  FRAX_TID();
+  using T = ChainTopo<7>;
+  rnea_vjp_chain<7>(M, q, qd, qdd, RhsFromGlobal<T, Col>{gbar, col},
+                    vjp_sink<T>(M, q, qbar, qdbar, qddbar, 1.f, col), col);
 }
 
 cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
@@ -130,9 +142,16 @@ cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
                                                     a.out2);
     return cudaGetLastError();
   }
-  if (op == kOpRneaVjp || op == kOpOsc || op == kOpRneaJvp || op == kOpFkJvp) {
-    // the adjoints step the forward state back through the joints instead
-    // of keeping it per body: far fewer live registers than the unrolled form
+  if (op == kOpRneaVjp) {
+    ModelImage<8> img8;
+    m.pack(&img8);
+    const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
+    k_rnea_vjp_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1,
+                                                     a.out2);
+    return cudaGetLastError();
+  }
+  if (op == kOpOsc || op == kOpRneaJvp || op == kOpFkJvp) {
+    // rolled segment loops (these have not been measured unrolled)
     ModelImage<8> img8;
     m.pack(&img8);
     return launch_topo<SegTopo<8, false>>(img8, op, a);

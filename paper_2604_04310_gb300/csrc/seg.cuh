@@ -797,6 +797,71 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
   }
 }
 
+// The same adjoint for a fixed-base serial chain of N bodies with both
+// sweeps unrolled: the body index, and with it every model constant's offset
+// in the parameter image and each joint's frame form (k > 0), is known at
+// compile time, so no index arithmetic or table lookup is left. The inward
+// sweep steps the forward state back as rnea_vjp_seg does; the joint sin/cos
+// pairs stay in registers.
+// A seed held in a register array (entry k = dof k of a fixed-base chain).
+struct RegVec {
+  const float* x;
+  FD float operator()(int k) const { return x[k]; }
+};
+
+template <int N, class Img, class Seed, class Sink, class C>
+FD void rnea_vjp_chain(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
+                       const float* __restrict__ qdd, const Seed& gb_at, const Sink& sink, const C& col) {
+  float sc[N], ss[N];
+  SV v = szero(), a = gravity_acc(M.g), Fb = szero();
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const BodyImage& b = M.body[k];
+    joint_sincos(col.in(q, k) + b.th0, &ss[k], &sc[k]);
+    const float qdi = col.in(qd, k);
+    v = mot_in(b, sc[k], ss[k], v, k > 0);
+    v.w.z += qdi;
+    a = mot_in(b, sc[k], ss[k], a, k > 0);
+    a.w.z += col.in(qdd, k);
+    a = a + ez_velprod(v, qdi);
+    Fb = mot_in(b, sc[k], ss[k], Fb, k > 0);
+    Fb.w.z += gb_at(k);
+  }
+  SV Fc = szero(), abc = szero(), vbc = szero();
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    const BodyImage& b = M.body[k];
+    const bool dh = k > 0;
+    const RBI I = rbi_of(b);
+    const float cs = sc[k], sn = ss[k];
+    const float qdi = col.in(qd, k);
+    SV xa = a - ez_velprod(v, qdi);
+    xa.w.z -= col.in(qdd, k);
+    const SV Iv = rbi_mul(I, v);
+    const SV F = crf_add(rbi_mul_add(Fc, I, a), v, Iv);
+    const SV ab = rbi_mul_add(abc, I, Fb);
+    const SV vb = rbi_mul_sub(crf_sub(vbc, Fb, Iv), I, crm(v, Fb)) + qdi * ez_crf(ab);
+    const SV ef = ez_crf(F), ea = ez_crm(xa), ev = ez_crm(v);
+    const float q1 = fmaf(Fb.w.x, ef.w.x, fmaf(Fb.w.y, ef.w.y, fmaf(Fb.v.x, ef.v.x, Fb.v.y * ef.v.y)));
+    const float q2 = fmaf(ab.w.x, ea.w.x, fmaf(ab.w.y, ea.w.y, fmaf(ab.v.x, ea.v.x, ab.v.y * ea.v.y)));
+    const float q3 = fmaf(vb.w.x, ev.w.x, fmaf(vb.w.y, ev.w.y, fmaf(vb.v.x, ev.v.x, vb.v.y * ev.v.y)));
+    const float qdb = fmaf(-ab.w.x, ev.w.x, fmaf(-ab.w.y, ev.w.y, fmaf(-ab.v.x, ev.v.x, fmaf(-ab.v.y, ev.v.y, vb.w.z))));
+    sink(k, q1 - q2 - q3, qdb, ab.w.z);
+    if (k > 0) {
+      Fc = frc_out(b, cs, sn, F, dh);
+      abc = frc_out(b, cs, sn, ab, dh);
+      vbc = frc_out(b, cs, sn, vb, dh);
+      SV vp = v;
+      vp.w.z -= qdi;
+      v = mot_out(b, cs, sn, vp, dh);
+      a = mot_out(b, cs, sn, xa, dh);
+      SV Fp = Fb;
+      Fp.w.z -= gb_at(k);
+      Fb = mot_out(b, cs, sn, Fp, dh);
+    }
+  }
+}
+
 template <class T, class Img, class C>
 FD void rnea_vjp_seg_one(const Img& M, const float* q, const float* qd, const float* qdd, const float* gbar,
                          float* qbar, float* qdbar, float* qddbar, const C& col) {
@@ -824,7 +889,7 @@ FD void aba_vjp_seg_one(const Img& M, const float* q, const float* qd, const flo
 // mass matrix than through articulated inertias: composite inertias give M's
 // lower triangle (registers), factored in place as M = L^T D L, then
 // L^T u = gbar (back substitution), L w = D^-1 u (forward substitution).
-// The rest is the segment RNEA adjoint seeded with w.
+// The rest is the unrolled chain RNEA adjoint seeded with w.
 // g(k): right-hand side entry k (a global column or a thread-local vector).
 template <int N, class Img, class G, class C>
 FD void chain_minv(const Img& M, const float* __restrict__ q, const G& g, float* w, const C& col) {
@@ -882,15 +947,13 @@ FD void chain_minv(const Img& M, const float* __restrict__ q, const G& g, float*
 template <int N, class Img, class C>
 FD void aba_vjp_chain_one(const Img& M, const float* q, const float* qd, const float* qdd, const float* gbar,
                           float* qbar, float* qdbar, float* taubar, const C& col) {
-  using S = SegTopo<N + 1, false>;
-  LocalVec<S> w;
-  chain_minv<N>(M, q, RhsFromGlobal<ChainTopo<N>, C>{gbar, col}, w.x, col);
+  float w[N];
+  chain_minv<N>(M, q, RhsFromGlobal<ChainTopo<N>, C>{gbar, col}, w, col);
   if (taubar) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) col.out(taubar, k, w.x[k]);
+    for (int k = 0; k < N; ++k) col.out(taubar, k, w[k]);
   }
-  const auto sink = vjp_sink<S>(M, q, qbar, qdbar, nullptr, -1.f, col);
-  rnea_vjp_seg<S, Img, LocalVec<S>, decltype(sink), C, false>(M, q, qd, qdd, w, sink, col);
+  rnea_vjp_chain<N>(M, q, qd, qdd, RegVec{w}, vjp_sink<ChainTopo<N>>(M, q, qbar, qdbar, nullptr, -1.f, col), col);
 }
 
 }  // namespace frax

@@ -269,14 +269,16 @@ def frax_rnea_vjp(model: Model, q, qd, qdd, gbar, qbar=None, qdbar=None, qddbar=
     return qbar, qdbar, qddbar
 
 
-def frax_aba_vjp(model: Model, q, qd, tau, qdd, gbar, qbar=None, qdbar=None, taubar=None):
-    """VJP of Eq. 2 at qdd = ABA(q, qd, tau): (qbar [nq], qdbar, taubar = M^-1 gbar)."""
+def frax_aba_vjp(model: Model, q, qd, tau, qdd, gbar, qbar=None, qdbar=None, taubar=None, want_taubar=True):
+    """VJP of Eq. 2 at qdd = ABA(q, qd, tau): (qbar [nq], qdbar, taubar = M^-1 gbar);
+    with want_taubar False and no taubar buffer, taubar is not written (None)."""
     nv = model.nv
     B, ld = _prep(model, q, qd=(qd, nv), tau=(tau, nv), qdd=(qdd, nv), gbar=(gbar, nv),
                   qbar=(qbar, model.nq), qdbar=(qdbar, nv), taubar=(taubar, nv))
     qbar = _out(model.nq, q, ld, B) if qbar is None else qbar
     qdbar = _out(nv, q, ld, B) if qdbar is None else qdbar
-    taubar = _out(nv, q, ld, B) if taubar is None else taubar
+    if taubar is None and want_taubar:
+        taubar = _out(nv, q, ld, B)
     _check(lib().frax_aba_vjp(model.handle, B, ld, _p(q), _p(qd), _p(tau), _p(qdd), _p(gbar), _p(qbar),
                               _p(qdbar), _p(taubar), _stream(q)))
     return qbar, qdbar, taubar

@@ -344,3 +344,21 @@ def test_crba_single_outputs_match_both(fxm, name):
     M1, _ = fx.frax_crba(h, d["q"], want_M=True, want_LD=False)
     _, LD1 = fx.frax_crba(h, d["q"], want_M=False, want_LD=True)
     assert torch.equal(M, M1) and torch.equal(LD, LD1)
+
+
+
+@pytest.mark.parametrize("name", ["chain7", "humanoid", "tree101"])
+def test_aba_vjp_without_taubar_matches(fxm, name):
+    """taubar NULL: the chain runs its one-launch adjoint (factor solve and
+    sweep fused) instead of the two launches; trees skip the taubar stores.
+    Same q and qd gradients either way."""
+    m, h = MODELS[name], fxm[name]
+    s, d = states(m, 300, 45)
+    g = dev(gen.draw_gbar(m.nv, 300, 46))
+    qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+    qb, qdb, tb = fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], qdd, g)
+    qb0, qdb0, tb0 = fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], qdd, g, want_taubar=False)
+    assert tb0 is None and tb is not None
+    for x, y in ((qb, qb0), (qdb, qdb0)):
+        xh, yh = host(x), host(y)
+        assert np.max(np.abs(xh - yh)) <= 1e-5 * np.max(np.abs(xh))
