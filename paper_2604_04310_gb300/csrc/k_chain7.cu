@@ -35,7 +35,7 @@ struct TauMinusBias {
   ColT<false> own;  // bias was written by this thread: read through L2
   FD float operator()(int k) const { return col.in(tau, k) - own.in(bias, k); }
 };
-__global__ void __launch_bounds__(kBlock, 8) k_aba_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+__global__ void __launch_bounds__(kBlock) k_aba_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
                                                          int64_t ld, const float* q, const float* qd,
                                                          const float* tau, float* qdd) {
   FRAX_TID();
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_aba_ext_chain7(const __grid_const
 // The ABA adjoint in two launches when taubar is asked for (it is w itself):
 // w = M^-1 gbar through the factor into taubar, then the RNEA adjoint seeded
 // with it. Each kernel stays small enough for the instruction cache.
-__global__ void __launch_bounds__(kBlock, 10) k_minv_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_minv_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
                                                           int64_t ld, const float* q, const float* g, float* w) {
   FRAX_TID();
   float x[7];

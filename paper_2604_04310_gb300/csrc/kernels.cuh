@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_fk(const __grid_constant__ ModelI
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock, 10) k_rnea(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 8) k_rnea(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                   int64_t ld, const float* q, const float* qd,
                                                   const float* qdd, float* tau) {
   FRAX_TID();
