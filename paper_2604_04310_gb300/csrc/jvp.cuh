@@ -145,6 +145,54 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
   }
 }
 
+// The same tangent recursion for a fixed-base serial chain of N bodies with
+// both sweeps unrolled (compile-time body index and frame form, k > 0), as
+// rnea_vjp_chain does for the adjoint.
+template <int N, class Img, class C, class Sink>
+FD void rnea_jvp_chain(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
+                       const float* __restrict__ qdd, const float* __restrict__ dq, const float* __restrict__ dqd,
+                       const float* __restrict__ dqdd, const Sink& sink, const C& col) {
+  float sc[N], ss[N];
+  auto in0 = [&](const float* p, int k) { return p ? col.in(p, k) : 0.f; };
+  SV v = szero(), a = gravity_acc(M.g), dv = szero(), da = szero();
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const BodyImage& b = M.body[k];
+    const bool dh = k > 0;
+    joint_sincos(col.in(q, k) + b.th0, &ss[k], &sc[k]);
+    const float cs = sc[k], sn = ss[k];
+    const float qdi = col.in(qd, k), dqi = col.in(dq, k), dqdi = col.in(dqd, k);
+    const SV Xv = mot_in(b, cs, sn, v, dh);
+    const SV Xa = mot_in(b, cs, sn, a, dh);
+    dv = mot_in(b, cs, sn, dv, dh) - dqi * ez_crm(Xv);
+    dv.w.z += dqdi;
+    v = Xv;
+    v.w.z += qdi;
+    da = mot_in(b, cs, sn, da, dh) - dqi * ez_crm(Xa) + ez_velprod(dv, qdi) + ez_velprod(v, dqdi);
+    da.w.z += in0(dqdd, k);
+    a = Xa + ez_velprod(v, qdi);
+    a.w.z += in0(qdd, k);
+  }
+  SV Fc = szero(), dFc = szero();
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    const BodyImage& b = M.body[k];
+    const bool dh = k > 0;
+    const RBI I = rbi_of(b);
+    const float cs = sc[k], sn = ss[k];
+    const float qdi = col.in(qd, k), dqi = col.in(dq, k), dqdi = col.in(dqd, k);
+    const SV Iv = rbi_mul(I, v);
+    const SV F = crf_add(rbi_mul_add(Fc, I, a), v, Iv);
+    const SV dF = crf_add(crf_add(rbi_mul_add(dFc, I, da), dv, Iv), v, rbi_mul(I, dv));
+    sink(k, F.w.z, dF.w.z);
+    if (k > 0) {
+      Fc = frc_out(b, cs, sn, F, dh);
+      dFc = frc_out(b, cs, sn, dF + dqi * ez_crf(F), dh);
+      jvp_step_back(b, cs, sn, qdi, in0(qdd, k), dqi, dqdi, in0(dqdd, k), v, a, dv, da, dh);
+    }
+  }
+}
+
 // tau (optional) and dtau to global memory
 template <class T, class C>
 struct JvpToGlobal {
@@ -190,9 +238,9 @@ FD void aba_jvp_seg_one(const Img& M, const float* q, const float* qd, const flo
 template <int N, class Img, class C>
 FD void aba_jvp_chain_one(const Img& M, const float* q, const float* qd, const float* qdd, const float* dq,
                           const float* dqd, const float* dtau, float* dqdd, const C& col) {
-  using S = SegTopo<N + 1, false>;
-  LocalVec<S> r;
-  rnea_jvp_seg<S>(M, q, qd, qdd, dq, dqd, nullptr, JvpResidual<S, C>{&r, dtau, col}, col);
+  using T = ChainTopo<N>;
+  LocalVec<T> r;
+  rnea_jvp_chain<N>(M, q, qd, qdd, dq, dqd, nullptr, JvpResidual<T, C>{&r, dtau, col}, col);
   float w[N];
   chain_minv<N>(M, q, r, w, col);
 #pragma unroll

@@ -90,6 +90,15 @@ __global__ void __launch_bounds__(kBlock) k_aba_vjp_tail_chain7(const __grid_con
                     col);
 }
 
+// 7-body chains: the RNEA JVP, both sweeps unrolled.
+__global__ void __launch_bounds__(kBlock) k_rnea_jvp_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+                                                            int64_t ld, const float* q, const float* qd,
+                                                            const float* qdd, const float* dq, const float* dqd,
+                                                            const float* dqdd, float* tau, float* dtau) {
+  FRAX_TID();
+  rnea_jvp_chain<7>(M, q, qd, qdd, dq, dqd, dqdd, JvpToGlobal<ChainTopo<7>, Col>{tau, dtau, col}, col);
+}
+
 // 7-body chains: the RNEA adjoint, both sweeps unrolled. No register cap:
 // at 95 registers (5 blocks per SM) it ran faster than capped at 72 or 64.
 __global__ void __launch_bounds__(kBlock) k_rnea_vjp_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
@@ -150,7 +159,15 @@ cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
                                                      a.out2);
     return cudaGetLastError();
   }
-  if (op == kOpOsc || op == kOpRneaJvp || op == kOpFkJvp) {
+  if (op == kOpRneaJvp) {
+    ModelImage<8> img8;
+    m.pack(&img8);
+    const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
+    k_rnea_jvp_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.in_dq, a.in_dqd, a.in_dx,
+                                                     a.out0, a.out1);
+    return cudaGetLastError();
+  }
+  if (op == kOpOsc || op == kOpFkJvp) {
     // rolled segment loops (these have not been measured unrolled)
     ModelImage<8> img8;
     m.pack(&img8);
