@@ -305,4 +305,31 @@ FD void fk_jvp_seg(const Img& M, const float* __restrict__ q, const float* __res
   }
 }
 
+// The FK JVP of a fixed-base serial chain of N bodies, unrolled.
+template <int N, class Img, class C>
+FD void fk_jvp_chain(const Img& M, const float* __restrict__ q, const float* __restrict__ dq, const Frames& fr,
+                     float* __restrict__ out, const C& col) {
+  SV v = szero();
+  float E[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const BodyImage& b = M.body[k];
+    float sn, cs;
+    joint_sincos(col.in(q, k) + b.th0, &sn, &cs);
+    float ER[9];
+    v = mot_in(b, cs, sn, v, k > 0);
+    mat_mul_b(E, b, ER, k > 0);
+    v.w.z += col.in(dq, k);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float x = ER[3 * r], y = ER[3 * r + 1];
+      E[3 * r] = fmaf(cs, x, sn * y);
+      E[3 * r + 1] = fmaf(-sn, x, cs * y);
+      E[3 * r + 2] = ER[3 * r + 2];
+    }
+    for (int f = 0; f < fr.n; ++f)
+      if (fr.body[f] == k) store6(out, 6 * f, col, SV{rot(E, v.w), rot(E, v.v)});
+  }
+}
+
 }  // namespace frax

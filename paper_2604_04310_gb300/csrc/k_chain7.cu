@@ -90,6 +90,14 @@ __global__ void __launch_bounds__(kBlock) k_aba_vjp_tail_chain7(const __grid_con
                     col);
 }
 
+// 7-body chains: the FK JVP, unrolled.
+__global__ void __launch_bounds__(kBlock) k_fk_jvp_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+                                                          int64_t ld, const float* q, const float* dq,
+                                                          const __grid_constant__ Frames fr, float* out) {
+  FRAX_TID();
+  fk_jvp_chain<7>(M, q, dq, fr, out, col);
+}
+
 // 7-body chains: the RNEA JVP, both sweeps unrolled.
 __global__ void __launch_bounds__(kBlock) k_rnea_jvp_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
                                                             int64_t ld, const float* q, const float* qd,
@@ -167,7 +175,16 @@ cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
                                                      a.out0, a.out1);
     return cudaGetLastError();
   }
-  if (op == kOpOsc || op == kOpFkJvp) {
+  if (op == kOpFkJvp) {
+    ModelImage<8> img8;
+    m.pack(&img8);
+    Frames fr{a.frames.n, {0}};
+    for (int f = 0; f < a.frames.n; ++f) fr.body[f] = a.frames.body[f];
+    const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
+    k_fk_jvp_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.in_dq, fr, a.out0);
+    return cudaGetLastError();
+  }
+  if (op == kOpOsc) {
     // rolled segment loops (these have not been measured unrolled)
     ModelImage<8> img8;
     m.pack(&img8);
