@@ -66,8 +66,8 @@ FLOPS = {
 # workload; an entry is removed when its kernel changes. aba_vjp = the factor
 # solve plus the adjoint sweep.
 NCU_TRAFFIC = {
-    "fk_jac": 29.47e6 + 490.82e6, "rnea": 88.12e6 + 13.59e6, "crba_ltdl": 25.20e6 + 264.38e6,
-    "aba": 90.08e6 + 59.33e6, "rnea_vjp": 117.49e6 + 51.90e6, "aba_vjp": 54.56e6 + 3.84e6 + 117.50e6 + 31.62e6,
+    "fk_jac": 29.39e6 + 491.59e6, "rnea": 88.10e6 + 8.12e6, "crba_ltdl": 25.22e6 + 264.27e6,
+    "aba": 88.12e6 + 9.87e6, "rnea_vjp": 117.49e6 + 43.77e6, "aba_vjp": 54.55e6 + 2.12e6 + 117.51e6 + 26.20e6,
 }
 # operational-space control task bodies (the last end frame of each model)
 OSC_TASK = {"chain7": 6, "humanoid": 29}
