@@ -814,24 +814,26 @@ FD void rnea_vjp_chain(const Img& M, const float* __restrict__ q, const float* _
                        const float* __restrict__ qdd, const Seed& gb_at, const Sink& sink, const C& col) {
   float sc[N], ss[N];
   SV v = szero(), a = gravity_acc(M.g), Fb = szero();
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
+  auto outward = [&](int k, auto dh) {
     const BodyImage& b = M.body[k];
     joint_sincos(col.in(q, k) + b.th0, &ss[k], &sc[k]);
     const float qdi = col.in(qd, k);
-    v = mot_in(b, sc[k], ss[k], v, k > 0);
+    v = mot_in(b, sc[k], ss[k], v, dh);
     v.w.z += qdi;
-    a = mot_in(b, sc[k], ss[k], a, k > 0);
+    a = mot_in(b, sc[k], ss[k], a, dh);
     a.w.z += col.in(qdd, k);
     a = a + ez_velprod(v, qdi);
-    Fb = mot_in(b, sc[k], ss[k], Fb, k > 0);
+    Fb = mot_in(b, sc[k], ss[k], Fb, dh);
     Fb.w.z += gb_at(k);
-  }
-  SV Fc = szero(), abc = szero(), vbc = szero();
+  };
+  // (Rolling these loops after peeling body 0, which keeps the unrolled code
+  // out of the instruction cache's way, measured 5-6 % slower.)
+  outward(0, DhOff{});
 #pragma unroll
-  for (int k = N - 1; k >= 0; --k) {
+  for (int k = 1; k < N; ++k) outward(k, DhOn{});
+  SV Fc = szero(), abc = szero(), vbc = szero();
+  auto inward = [&](int k, auto dh) {
     const BodyImage& b = M.body[k];
-    const bool dh = k > 0;
     const RBI I = rbi_of(b);
     const float cs = sc[k], sn = ss[k];
     const float qdi = col.in(qd, k);
@@ -847,7 +849,7 @@ FD void rnea_vjp_chain(const Img& M, const float* __restrict__ q, const float* _
     const float q3 = fmaf(vb.w.x, ev.w.x, fmaf(vb.w.y, ev.w.y, fmaf(vb.v.x, ev.v.x, vb.v.y * ev.v.y)));
     const float qdb = fmaf(-ab.w.x, ev.w.x, fmaf(-ab.w.y, ev.w.y, fmaf(-ab.v.x, ev.v.x, fmaf(-ab.v.y, ev.v.y, vb.w.z))));
     sink(k, q1 - q2 - q3, qdb, ab.w.z);
-    if (k > 0) {
+    if (dh) {  // not the first body: carry the adjoints to the parent, step the state back
       Fc = frc_out(b, cs, sn, F, dh);
       abc = frc_out(b, cs, sn, ab, dh);
       vbc = frc_out(b, cs, sn, vb, dh);
@@ -859,7 +861,10 @@ FD void rnea_vjp_chain(const Img& M, const float* __restrict__ q, const float* _
       Fp.w.z -= gb_at(k);
       Fb = mot_out(b, cs, sn, Fp, dh);
     }
-  }
+  };
+#pragma unroll
+  for (int k = N - 1; k >= 1; --k) inward(k, DhOn{});
+  inward(0, DhOff{});
 }
 
 template <class T, class Img, class C>
