@@ -132,6 +132,42 @@ FD void ext_tau(const Img& M, const float* __restrict__ q, const float* __restri
   }
 }
 
+// The same for a fixed-base serial chain of N bodies, unrolled: the world
+// axes and joint origins stay in registers.
+template <int N, class Img, class C, class Sink>
+FD void ext_tau_chain(const Img& M, const float* __restrict__ q, const float* __restrict__ fext, const C& col,
+                      const Sink& sink) {
+  V3 z[N], p[N];
+  float E[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+  V3 o = mk(0, 0, 0);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const BodyImage& b = M.body[k];
+    o = o + rot(E, mk(b.p[0], b.p[1], b.p[2]));
+    float ER[9];
+    mat_mul_b(E, b, ER, k > 0);
+    z[k] = mk(ER[2], ER[5], ER[8]);
+    p[k] = o;
+    if (k < N - 1) {
+      float sn, cs;
+      joint_sincos(col.in(q, k) + b.th0, &sn, &cs);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float x = ER[3 * r], y = ER[3 * r + 1];
+        E[3 * r] = fmaf(cs, x, sn * y);
+        E[3 * r + 1] = fmaf(-sn, x, cs * y);
+        E[3 * r + 2] = ER[3 * r + 2];
+      }
+    }
+  }
+  SV F = szero();
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    F = F + load6(fext, 6 * k, col);
+    sink(k, dot(z[k], F.w - cross(p[k], F.v)));
+  }
+}
+
 // tau -= x: the RNEA output, read back through L2 (this thread wrote it).
 template <class T>
 struct SubFromGlobal {

@@ -50,19 +50,19 @@ __global__ void __launch_bounds__(kBlock) k_aba_chain7(const __grid_constant__ M
 struct TauExtMinusBias {
   const float* tau;
   const float* bias;
-  const LocalVec<SegTopo<8, false>>* ext;
+  const LocalVec<ChainTopo<7>>* ext;
   Col col;
   ColT<false> own;
   FD float operator()(int k) const { return (col.in(tau, k) + (*ext)(k)) - own.in(bias, k); }
 };
-__global__ void __launch_bounds__(kBlock, 6) k_aba_ext_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+__global__ void __launch_bounds__(kBlock) k_aba_ext_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
                                                              int64_t ld, const float* q, const float* qd,
                                                              const float* tau, const float* fext, float* qdd) {
   FRAX_TID();
-  using S = SegTopo<8, false>;
-  LocalVec<S> w;
-  ext_tau<S>(M, q, fext, col, OutToLocal<S>{&w});
-  rnea_one<ChainTopo<7>>(M, q, qd, nullptr, qdd, col);
+  using T = ChainTopo<7>;
+  LocalVec<T> w;
+  ext_tau_chain<7>(M, q, fext, col, OutToLocal<T>{&w});
+  rnea_one<T>(M, q, qd, nullptr, qdd, col);
   float x[7];
   chain_minv<7>(M, q, TauExtMinusBias{tau, qdd, &w, col, ColT<false>{ld, b}}, x, col);
 #pragma unroll
@@ -88,6 +88,16 @@ __global__ void __launch_bounds__(kBlock) k_aba_vjp_tail_chain7(const __grid_con
   using T = ChainTopo<7>;
   rnea_vjp_chain<7>(M, q, qd, qdd, RhsFromGlobal<T, Col>{w, col}, vjp_sink<T>(M, q, qbar, qdbar, nullptr, -1.f, col),
                     col);
+}
+
+// 7-body chains: RNEA with external forces, tau_ext unrolled.
+__global__ void __launch_bounds__(kBlock) k_rnea_ext_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+                                                            int64_t ld, const float* q, const float* qd,
+                                                            const float* qdd, const float* fext, float* tau) {
+  FRAX_TID();
+  using T = ChainTopo<7>;
+  rnea_one<T>(M, q, qd, qdd, tau, col);
+  ext_tau_chain<7>(M, q, fext, col, SubFromGlobal<T>{tau, ColT<false>{ld, b}});
 }
 
 // 7-body chains: the FK JVP, unrolled.
@@ -127,6 +137,13 @@ cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
     k_minv_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.gbar, a.out2);
     k_aba_vjp_tail_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.out2, a.out0,
                                                          a.out1);
+    return cudaGetLastError();
+  }
+  if (op == kOpRneaExt) {
+    ModelImage<8> img8;
+    m.pack(&img8);
+    const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
+    k_rnea_ext_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.in_fext, a.out0);
     return cudaGetLastError();
   }
   if (op == kOpAbaExt) {
