@@ -362,3 +362,43 @@ def test_aba_vjp_without_taubar_matches(fxm, name):
     for x, y in ((qb, qb0), (qdb, qdb0)):
         xh, yh = host(x), host(y)
         assert np.max(np.abs(xh - yh)) <= 1e-5 * np.max(np.abs(xh))
+
+
+@pytest.mark.parametrize("B", [1, 33, 129])
+def test_chain_unrolled_kernels_edge_batches(fxm, B):
+    """The chain's own kernels (unrolled adjoint, JVP and external-force
+    sweeps, the factor-based solves) on ragged batches with ld > B: results
+    match the oracle and the padding columns of every output stay untouched."""
+    m, h = MODELS["chain7"], fxm["chain7"]
+    ld = B + 13
+    s, d = states(m, B, 47, ld=ld)
+    rng = np.random.default_rng(48)
+    draw = lambda rows: rng.standard_normal((B, rows)).astype(np.float32).astype(np.float64)
+    g, dq, dqd, dx = draw(7), draw(7), draw(7), draw(7)
+    F = draw(6 * 7)
+    pad = lambda rows: torch.full((rows, ld), 7.0, device="cuda")
+    outs = {k: pad(r) for k, r in (("qb", 7), ("qdb", 7), ("qddb", 7), ("aqb", 7), ("aqdb", 7), ("tb", 7),
+                                     ("dt", 7), ("da", 7), ("dp", 6), ("te", 7), ("ae", 7))}
+    v = lambda k: outs[k][:, :B]
+    fx.frax_rnea_vjp(h, d["q"], d["qd"], d["qdd"], dev(g, ld), qbar=v("qb"), qdbar=v("qdb"), qddbar=v("qddb"))
+    qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+    fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], qdd, dev(g, ld), qbar=v("aqb"), qdbar=v("aqdb"), taubar=v("tb"))
+    fx.frax_rnea_jvp(h, d["q"], d["qd"], d["qdd"], dev(dq, ld), dev(dqd, ld), dev(dx, ld), dtau=v("dt"))
+    fx.frax_aba_jvp(h, d["q"], d["qd"], d["tau"], qdd, dev(dq, ld), dev(dqd, ld), dev(dx, ld), dqdd=v("da"))
+    fx.frax_fk_jvp(h, d["q"], dev(dq, ld), [6], dpose=v("dp"))
+    fx.frax_rnea_ext(h, d["q"], d["qd"], d["qdd"], dev(F, ld), tau=v("te"))
+    fx.frax_aba_ext(h, d["q"], d["qd"], d["tau"], dev(F, ld), qdd=v("ae"))
+    for k, t in outs.items():
+        assert torch.all(t[:, B:] == 7.0), k
+    qb, qdb, qddb = dv.rnea_vjp(m, s.q, s.qd, s.qdd, g)
+    assert normwise(host(v("qb")), qb) < TOL_GRAD and normwise(host(v("qdb")), qdb) < TOL_GRAD
+    assert normwise(host(v("qddb")), qddb) < TOL_GRAD
+    aq, aqd, at = dv.aba_vjp(m, s.q, s.qd, s.tau, g)
+    assert normwise(host(v("aqb")), aq) < TOL_GRAD and normwise(host(v("aqdb")), aqd) < TOL_GRAD
+    assert normwise(host(v("tb")), at) < TOL_GRAD
+    assert normwise(host(v("dt")), dv.rnea_jvp(m, s.q, s.qd, s.qdd, dq, dqd, dx)) < TOL_GRAD
+    assert normwise(host(v("da")), dv.aba_jvp(m, s.q, s.qd, s.tau, dq, dqd, dx)) < TOL_GRAD
+    assert normwise(host(v("dp")), dv.fk_jvp(m, s.q, dq, [6]).reshape(B, -1)) < TOL
+    Fb = F.reshape(B, 7, 6)
+    assert normwise(host(v("te")), rbd.rnea(m, s.q, s.qd, s.qdd, fext=Fb)) < TOL
+    assert normwise(host(v("ae")), rbd.aba(m, s.q, s.qd, s.tau, fext=Fb)) < TOL
