@@ -293,6 +293,51 @@ def time_step(step, steps, warmup, flush, world, dist, clocks=None):
     return step_ms, per_op_ms, launches, wall, clk
 
 
+def time_graph(step, steps, warmup, flush, world, dist, clocks=None):
+    """The same step captured once as a CUDA graph (the same calls, the same
+    kernels; replaying it trims the host's launch gaps between them) and
+    replayed `steps` times, L2 flushed between replays outside the events.
+    Returns (step_ms, launches, wall, clocks, None), or five Nones but the
+    last, the reason, when the capture fails."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(max(3, warmup)):
+            step.run()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    try:
+        with torch.cuda.graph(g):
+            step.run()
+    except Exception as e:  # noqa: BLE001 - reported in the bench line
+        torch.cuda.synchronize()
+        return None, None, None, None, str(e).splitlines()[0][:200]
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+        time.sleep(0.3)
+    t0 = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()
+        sev[k][0].record()
+        g.replay()
+        sev[k][1].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks is not None else None
+    return sum(a.elapsed_time(b) for a, b in sev), steps * step.kernels, wall, clk, None
+
+
 def whole_job(step_ms, steps, evals_per_step, world, dist, device):
     """Replicas: every rank times its own batch; the job's step time is the
     slowest rank's (max over ranks) and the value counts every rank's
@@ -604,7 +649,18 @@ def frax_arm(args, rank, world, local_rank):
     host, dev = make_inputs(robot, B, 1001 + rank, device)
     step = Step(fx, model, robot, dev, device, OPS)
     clocks = ClockSampler(phys)
-    step_ms, per_op_ms, launches, wall, clk = time_step(step, args.steps, args.warmup, flush, world, dist, clocks)
+    # per op: the calls one by one with CUDA events between them; the step
+    # itself: the same calls replayed as one CUDA graph
+    step_ms, per_op_ms, launches, wall, clk = time_step(step, args.steps, args.warmup, flush, world, dist,
+                                                        clocks if args.eager else None)
+    launch_mode = "eager: one public call per op"
+    if not args.eager:
+        g_ms, g_launches, g_wall, g_clk, why = time_graph(step, args.steps, args.warmup, flush, world, dist, clocks)
+        if g_ms is not None:
+            step_ms, launches, wall, clk = g_ms, g_launches, g_wall, g_clk
+            launch_mode = "the step's public calls captured once as a CUDA graph and replayed"
+        else:
+            launch_mode += f" (graph capture failed: {why})"
     ms_per_step, value = whole_job(step_ms, args.steps, len(OPS) * B, world, dist, device)
     hbm, hbm_src = measured_hbm_gbs()
     per_op = roofline_of(per_op_ms, FLOPS["chain7"], B, peak, hbm, robot)
@@ -707,7 +763,7 @@ def frax_arm(args, rank, world, local_rank):
                 "config": {"workload": "7-DoF revolute chain (seed 0), 2^20 instances per GPU; one step = "
                                        "FK+EE Jacobian, RNEA, CRBA+LTDL, ABA, RNEA-VJP, ABA-VJP",
                            "global_batch": B * world, "parallelism": f"replicas x{world}",
-                           "l2": "256 MB buffer written between steps (L2 flush)"},
+                           "l2": "256 MB buffer written between steps (L2 flush)", "launch": launch_mode},
                 "clocks": clk, "gpu_launches": launches, "wall_s": wall, "per_op": per_op, "roofline": roofline,
                 "e2e": e2e, "humanoid": humanoid, "next_rows": nxt, "cpu_baseline": cpu,
                 "cpu_baseline_all_cores": cpu_all, "serving": serve}
@@ -726,6 +782,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-humanoid", action="store_true")
     ap.add_argument("--no-next", action="store_true")
+    ap.add_argument("--eager", action="store_true", help="time the step as separate calls, not a CUDA graph")
     ap.add_argument("--humanoid-batch", type=int, default=1 << 18)
     ap.add_argument("--count-flops", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
