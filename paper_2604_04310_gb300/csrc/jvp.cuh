@@ -79,11 +79,10 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
       a = p < 0 ? ag : ba[p];
       dv = p < 0 ? szero() : bdv[p];
       da = p < 0 ? szero() : bda[p];
-#pragma unroll 1
-      for (int k = 0; k < len; ++k) {
+      seg_outward(len, M.body[M.order[st]].dh, [&](int k, auto dh) {
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
-        with_dh(b.dh, [&](auto dh) {
+        {
           float sn, cs;
           joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
           sc[i] = cs;
@@ -100,8 +99,8 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
           da.w.z += in0(dqdd, iv);
           a = Xa + ez_velprod(v, qdi);
           a.w.z += in0(qdd, iv);
-        });
-      }
+        }
+      });
       if (kind == kActOpen) {
         bv[last] = v;
         ba[last] = a;
@@ -119,11 +118,10 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
     const bool closing = kind == kActClose;
     SV Fc = closing ? aF[last] : szero();
     SV dFc = closing ? adF[last] : szero();
-#pragma unroll 1
-    for (int k = len - 1; k >= 0; --k) {
+    seg_inward(len, M.body[M.order[st]].dh, [&](int k, auto dh) {
       const int i = M.order[st + k];
       const BodyImage& b = M.body[i];
-      with_dh(b.dh, [&](auto dh) {
+      {
         const RBI I = rbi_of(b);
         const float cs = sc[i], sn = ss[i];
         const int iv = iv_of<T>(i);
@@ -135,8 +133,8 @@ FD void rnea_jvp_seg(const Img& M, const float* __restrict__ q, const float* __r
         Fc = frc_out(b, cs, sn, F, dh);
         dFc = frc_out(b, cs, sn, dF + dqi * ez_crf(F), dh);
         if (k > 0) jvp_step_back(b, cs, sn, qdi, in0(qdd, iv), dqi, dqdi, in0(dqdd, iv), v, a, dv, da, dh);
-      });
-    }
+      }
+    });
     const int p = M.seg_parent[s];
     if (p >= 0) {
       aF[p] = aF[p] + Fc;

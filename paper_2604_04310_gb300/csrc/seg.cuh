@@ -199,17 +199,14 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
       const int p = M.seg_parent[s];
       SV vv = (!VEL || p < 0) ? szero() : bv[p];
       if (VEL) {
-#pragma unroll 1
-        for (int k = 0; k < len; ++k) {
+        seg_outward(len, M.body[M.order[st]].dh, [&](int k, auto dh) {
           const int i = M.order[st + k];
           const BodyImage& b = M.body[i];
-          with_dh(b.dh, [&](auto dh) {
-            float sn, cs;
-            joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
-            vv = mot_in(b, cs, sn, vv, dh);
-            vv.w.z += col.in(qd, iv_of<T>(i));
-          });
-        }
+          float sn, cs;
+          joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+          vv = mot_in(b, cs, sn, vv, dh);
+          vv.w.z += col.in(qd, iv_of<T>(i));
+        });
       }
       vtip = vv;
       if (kind == kActOpen) {
@@ -225,9 +222,8 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
     AI Ia;
     SV pa;
     const bool closing = kind == kActClose;
-#pragma unroll 1
-    for (int k = len - 1; k >= 0; --k) {
-      with_dh(M.body[M.order[st + k]].dh, [&](auto dh) {
+    seg_inward(len, M.body[M.order[st]].dh, [&](int k, auto dh) {
+      {
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
         const RBI Ib = rbi_of(b);
@@ -272,8 +268,8 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
           vp.w.z -= col.in(qd, iv_of<T>(i));
           vtip = mot_out(b, ck, sk, vp, dh);
         }
-      });
-    }
+      }
+    });
     const int p = M.seg_parent[s];
     if (p >= 0) {
       ai_add(IAa[p], Ia);
@@ -293,9 +289,8 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
     const int p = M.seg_parent[s];
     SV a = p < 0 ? ag : bA[p];
     SV vv = (!VEL || p < 0) ? szero() : bv[p];
-#pragma unroll 1
-    for (int k = 0; k < len; ++k) {
-      with_dh(M.body[M.order[st + k]].dh, [&](auto dh) {
+    seg_outward(len, M.body[M.order[st]].dh, [&](int k, auto dh) {
+      {
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
         float sn, cs;
@@ -312,8 +307,8 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
                                        fmaf(P.get(i, 2), a.v.x, fmaf(P.get(i, 3), a.v.y, P.get(i, 4) * a.v.z)));
         a.w.z += x;
         out_at(i, x);
-      });
-    }
+      }
+    });
     if ((opened >> s) & 1ull) bA[M.order[st + len - 1]] = a;
   }
 }
@@ -675,10 +670,7 @@ FD void fk_seg(const Img& M, const float* __restrict__ q, float* __restrict__ po
 // a_parent = X^-1 (a - e qdd - v x e qd), Fb_parent = X^-1 (Fb - e gbar)),
 // and the body force is recomputed; only segment tips and the accumulated
 // adjoints handed to branch bodies are kept per body.
-// With SPARSE false every joint takes the general form: one copy of each
-// loop body (the chain ABA adjoint, whose kernel also holds the factor solve,
-// runs faster so).
-template <class T, class Img, class Seed, class Sink, class C, bool SPARSE = true>
+template <class T, class Img, class Seed, class Sink, class C>
 FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
                      const float* __restrict__ qdd, const Seed& gb_at, const Sink& sink, const C& col) {
   constexpr int NB = T::NBMAX;
@@ -716,11 +708,10 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
       v = p < 0 ? szero() : bv[p];
       a = p < 0 ? ag : ba[p];
       Fb = p < 0 ? szero() : bF[p];
-#pragma unroll 1
-      for (int k = 0; k < len; ++k) {
+      seg_outward(len, M.body[M.order[st]].dh, [&](int k, auto dh) {
         const int i = M.order[st + k];
         const BodyImage& b = M.body[i];
-        with_dh(SPARSE && b.dh, [&](auto dh) {
+        {
           float sn, cs;
           joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
           sc[i] = cs;
@@ -733,8 +724,8 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
           a = a + ez_velprod(v, qdi);
           Fb = mot_in(b, cs, sn, Fb, dh);
           Fb.w.z += gb_at(i);
-        });
-      }
+        }
+      });
       if (kind == kActOpen) {
         bv[last] = v;
         ba[last] = a;
@@ -751,11 +742,10 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
     SV Fc = closing ? aF[last] : szero();
     SV abc = closing ? aab[last] : szero();
     SV vbc = closing ? avb[last] : szero();
-#pragma unroll 1
-    for (int k = len - 1; k >= 0; --k) {
+    seg_inward(len, M.body[M.order[st]].dh, [&](int k, auto dh) {
       const int i = M.order[st + k];
       const BodyImage& b = M.body[i];
-      with_dh(SPARSE && b.dh, [&](auto dh) {
+      {
         const RBI I = rbi_of(b);
         const float cs = sc[i], sn = ss[i];
         const float qdi = col.in(qd, iv_of<T>(i));
@@ -786,8 +776,8 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
           Fp.w.z -= gb_at(i);
           Fb = mot_out(b, cs, sn, Fp, dh);
         }
-      });
-    }
+      }
+    });
     const int p = M.seg_parent[s];
     if (p >= 0) {
       aF[p] = aF[p] + Fc;

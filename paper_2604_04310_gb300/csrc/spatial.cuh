@@ -135,6 +135,22 @@ FD void with_dh(bool dh, const F& f) {
   if (dh) f(DhOn{});
   else f(DhOff{});
 }
+// f(k, dh) over the len bodies of a segment, outward (k = 0, 1, ...) or
+// inward: the first body (k = 0) with the frame form its flag dh0 gives,
+// every later one sparse (a segment body after the first is its parent's
+// only child), so the rolled loop holds one copy of its body and no branch.
+template <class F>
+FD void seg_outward(int len, bool dh0, const F& f) {
+  with_dh(dh0, [&](auto dh) { f(0, dh); });
+#pragma unroll 1
+  for (int k = 1; k < len; ++k) f(k, DhOn{});
+}
+template <class F>
+FD void seg_inward(int len, bool dh0, const F& f) {
+#pragma unroll 1
+  for (int k = len - 1; k >= 1; --k) f(k, DhOn{});
+  with_dh(dh0, [&](auto dh) { f(0, dh); });
+}
 // With dh (the caller knows R = Rot_x(alpha), see BodyImage) the sparse form,
 // else the general one; callers pass a value the compiler can fold (a loop
 // index after unrolling), so each call site keeps one form.
