@@ -66,8 +66,8 @@ FLOPS = {
 # workload; an entry is removed when its kernel changes. aba_vjp = the factor
 # solve plus the adjoint sweep.
 NCU_TRAFFIC = {
-    "fk_jac": 29.39e6 + 491.59e6, "rnea": 88.10e6 + 8.12e6, "crba_ltdl": 25.22e6 + 264.27e6,
-    "aba": 88.12e6 + 9.87e6, "rnea_vjp": 117.49e6 + 43.77e6, "aba_vjp": 54.55e6 + 2.12e6 + 117.51e6 + 26.20e6,
+    "fk_jac": 29.40e6 + 491.16e6, "rnea": 88.12e6 + 7.86e6, "crba_ltdl": 25.20e6 + 263.56e6,
+    "aba": 88.13e6 + 9.34e6, "rnea_vjp": 117.51e6 + 43.44e6, "aba_vjp": 54.55e6 + 2.02e6 + 117.52e6 + 25.56e6,
 }
 # operational-space control task bodies (the last end frame of each model)
 OSC_TASK = {"chain7": 6, "humanoid": 29}
