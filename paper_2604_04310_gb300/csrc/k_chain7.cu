@@ -1,11 +1,12 @@
 // Serial chains of 7 revolute bodies: topology compiled in, registers only
-// (OSC and the JVPs run the segment code on the same chain).
+// (OSC runs the segment code on the same chain).
 #include "kernels.cuh"
 
 namespace frax {
 
-// 7-body chains: the ABA adjoint with its solve through the mass-matrix
-// factor (chain_minv), on the 8-slot image the segment code reads.
+// 7-body chains: the ABA adjoint in one launch (used when taubar is not
+// wanted): the solve through the mass-matrix factor (chain_minv), then the
+// unrolled RNEA adjoint.
 __global__ void __launch_bounds__(kBlock) k_aba_vjp_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
                                                             int64_t ld, const float* q, const float* qd,
                                                             const float* qdd, const float* gbar, float* qbar,
@@ -202,7 +203,7 @@ cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
     return cudaGetLastError();
   }
   if (op == kOpOsc) {
-    // rolled segment loops (these have not been measured unrolled)
+    // OSC: the segment code (rolled loops)
     ModelImage<8> img8;
     m.pack(&img8);
     return launch_topo<SegTopo<8, false>>(img8, op, a);

@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(kBlock, 8) k_aba_ext(const __grid_constant__ M
   }
 }
 
-// Forward-mode derivatives (segment code; chains run it on the 8-slot image).
+// Forward-mode derivatives on segments (the 7-body chain has unrolled
+// kernels of its own).
 template <class T>
 __global__ void __launch_bounds__(kBlock, 8) k_rnea_jvp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                       int64_t ld, const float* q, const float* qd,
