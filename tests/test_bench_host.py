@@ -47,3 +47,21 @@ def test_cpu_baseline_all_cores_sums_processes():
     r = bench.run_cpu_baseline_all_cores(1.0)
     assert r["cores"] == (os.cpu_count() or 1) and r["value"] > 0 and r["kind"] == "oracle"
     assert "single-threaded processes" in r["sample"] and r["cpu_model"]
+
+
+def test_kernels_per_call_matches_the_dispatch():
+    """The gpu_launches claim counts kernels per public call: the chain's ABA
+    adjoint with taubar is two launches (factor solve, adjoint sweep); a tree's
+    FK+J adds the fill of its Jacobians' structural zeros; the tree CRBA
+    writes its zeros itself (one launch); everything else is one launch."""
+    c, h, t = gen.chain7(0), gen.humanoid(0), gen.random_tree(101)
+    assert bench.kernels_per_call(c, "aba_vjp") == 2
+    assert all(bench.kernels_per_call(c, op) == 1 for op in bench.OPS if op != "aba_vjp")
+    assert bench.kernels_per_call(h, "fk_jac") == 2
+    assert bench.kernels_per_call(h, "crba_ltdl") == 1
+    assert all(bench.kernels_per_call(h, op) == 1 for op in ("rnea", "bias", "aba", "rnea_vjp", "aba_vjp"))
+    # a frame whose ancestors are every body has no zero column: no fill
+    chain_tree = gen.serial_chain(3, 5)
+    assert bench.kernels_per_call(chain_tree, "fk_jac") == 1
+    assert bench.kernels_per_call(t, "crba_ltdl") == 1
+
