@@ -1,0 +1,179 @@
+// The kernels' per-instance device functions compiled as host code (a
+// test harness, not part of the library): reads one model and a batch of
+// states (SoA, FP32) from a file, evaluates every op with the same device
+// functions the CUDA kernels call, and writes the outputs to a file for the
+// oracle to check on the CPU. Build (no GPU needed):
+//   g++ -std=c++17 -O1 -x c++ -I<cuda>/include -I<repo> tests/host_kernels.cpp \
+//       paper_2604_04310_gb300/csrc/model.cpp -o host_kernels
+// Usage: host_kernels <input file> <output file>
+#include <math.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+// the device builtin rsqrtf has no host counterpart in the C library
+static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+
+#include "paper_2604_04310_gb300/csrc/model.h"
+#include "paper_2604_04310_gb300/csrc/osc.cuh"
+#include "paper_2604_04310_gb300/csrc/ext.cuh"
+#include "paper_2604_04310_gb300/csrc/jvp.cuh"
+
+using namespace frax;
+
+namespace {
+
+struct Reader {
+  FILE* f;
+  template <class X>
+  std::vector<X> take(size_t n) {
+    std::vector<X> v(n);
+    if (n && std::fread(v.data(), sizeof(X), n, f) != n) throw std::string("short input");
+    return v;
+  }
+};
+
+struct Out {
+  std::deque<std::pair<std::string, std::vector<float>>> arrays;  // references stay valid as it grows
+  std::vector<float>& add(const std::string& name, size_t rows, int B) {
+    arrays.emplace_back(name, std::vector<float>(rows * size_t(B), 0.f));
+    return arrays.back().second;
+  }
+};
+
+// Every op for one topology T (segment code, or the chain's own unrolled code
+// where the CUDA dispatch uses it).
+template <class T, int NBI>
+void run_all(const HostModel& hm, int B, int nf, const int* frames, const float* q, const float* qd,
+             const float* qdd, const float* tau, const float* gbar, const float* dq, const float* dqd,
+             const float* dx, const float* fext, Out& o, bool chain7) {
+  ModelImage<NBI> img;
+  hm.pack(&img);
+  const int nb = hm.nb, nq = hm.nq, nv = hm.nv;
+  Frames fr{nf, {0}};
+  for (int f = 0; f < nf; ++f) fr.body[f] = frames[f];
+  auto& pose = o.add("pose", 12 * nb, B);
+  auto& J = o.add("J", size_t(nf) * 6 * nv, B);
+  auto& tau_r = o.add("rnea", nv, B);
+  auto& M = o.add("M", size_t(nv) * nv, B);
+  auto& LD = o.add("LD", size_t(nv) * (nv + 1) / 2, B);
+  auto& qdd_a = o.add("aba", nv, B);
+  auto& rq = o.add("rnea_vjp_q", nq, B);
+  auto& rqd = o.add("rnea_vjp_qd", nv, B);
+  auto& rqdd = o.add("rnea_vjp_qdd", nv, B);
+  auto& aq = o.add("aba_vjp_q", nq, B);
+  auto& aqd = o.add("aba_vjp_qd", nv, B);
+  auto& at = o.add("aba_vjp_tau", nv, B);
+  auto& dtau = o.add("rnea_jvp", nv, B);
+  auto& dqdd = o.add("aba_jvp", nv, B);
+  auto& dpose = o.add("fk_jvp", size_t(6) * nf, B);
+  auto& tau_e = o.add("rnea_ext", nv, B);
+  auto& qdd_e = o.add("aba_ext", nv, B);
+  for (int b = 0; b < B; ++b) {
+    const Col col{B, b};
+    fk_seg<T, ModelImage<NBI>, Col, true>(img, q, pose.data(), fr, J.data(), col);
+    rnea_seg<T>(img, q, qd, qdd, tau_r.data(), col);
+    crba_seg<T, ModelImage<NBI>, Col, true, 3>(img, q, M.data(), LD.data(), col);
+    {
+      P3Local<T::NBMAX> P;
+      aba_seg<T>(img, q, qd, tau, qdd_a.data(), col, P);
+    }
+    rnea_jvp_seg<T>(img, q, qd, qdd, dq, dqd, dx, JvpToGlobal<T, Col>{nullptr, dtau.data(), col}, col);
+    if (chain7) {
+      using C7 = ChainTopo<7>;
+      rnea_vjp_chain<7>(img, q, qd, qdd, RhsFromGlobal<C7, Col>{gbar, col},
+                        vjp_sink<C7>(img, q, rq.data(), rqd.data(), rqdd.data(), 1.f, col), col);
+      aba_vjp_chain_one<7>(img, q, qd, qdd_a.data(), gbar, aq.data(), aqd.data(), at.data(), col);
+      aba_jvp_chain_one<7>(img, q, qd, qdd_a.data(), dq, dqd, dx, dqdd.data(), col);
+      fk_jvp_chain<7>(img, q, dq, fr, dpose.data(), col);
+      rnea_one<C7>(img, q, qd, qdd, tau_e.data(), col);
+      ext_tau_chain<7>(img, q, fext, col, SubFromGlobal<C7>{tau_e.data(), ColT<false>{B, b}});
+    } else {
+      rnea_vjp_seg_one<T>(img, q, qd, qdd, gbar, rq.data(), rqd.data(), rqdd.data(), col);
+      aba_vjp_seg_one<T>(img, q, qd, tau, qdd_a.data(), gbar, aq.data(), aqd.data(), at.data(), col);
+      aba_jvp_seg_one<T>(img, q, qd, qdd_a.data(), dq, dqd, dx, dqdd.data(), col);
+      fk_jvp_seg<T>(img, q, dq, fr, dpose.data(), col);
+      rnea_seg<T>(img, q, qd, qdd, tau_e.data(), col);
+      ext_tau<T>(img, q, fext, col, SubFromGlobal<T>{tau_e.data(), ColT<false>{B, b}});
+    }
+    {  // ABA with external forces: right-hand side tau + tau_ext
+      LocalVec<T> w;
+      ext_tau<T>(img, q, fext, col, OutToLocal<T>{&w});
+      const RhsPlusLocal<T, Col> rhs{tau, col, &w};
+      P3Local<T::NBMAX> P;
+      aba_seg_core<T, ModelImage<NBI>, true>(img, q, qd, rhs, OutToGlobal<T, Col>{qdd_e.data(), col}, col, P);
+    }
+  }
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc != 3) {
+    std::fprintf(stderr, "usage: %s <input> <output>\n", argv[0]);
+    return 2;
+  }
+  try {
+    FILE* f = std::fopen(argv[1], "rb");
+    if (!f) throw std::string("cannot open input");
+    Reader r{f};
+    const auto hdr = r.take<int32_t>(3);
+    const int n = hdr[0], B = hdr[1], nf = hdr[2];
+    const auto parent = r.take<int32_t>(n);
+    const auto jt = r.take<int32_t>(n);
+    const auto axis = r.take<double>(3 * n);
+    const auto place = r.take<double>(12 * n);
+    const auto inert = r.take<double>(10 * n);
+    const auto grav = r.take<double>(3);
+    const auto frames = r.take<int32_t>(nf);
+    HostModel hm;
+    const std::string err =
+        build_model(n, parent.data(), jt.data(), axis.data(), place.data(), inert.data(), grav.data(), &hm);
+    if (!err.empty()) throw err;
+    const int nq = hm.nq, nv = hm.nv;
+    const auto q = r.take<float>(size_t(nq) * B);
+    const auto qd = r.take<float>(size_t(nv) * B);
+    const auto qdd = r.take<float>(size_t(nv) * B);
+    const auto tau = r.take<float>(size_t(nv) * B);
+    const auto gbar = r.take<float>(size_t(nv) * B);
+    const auto dq = r.take<float>(size_t(nv) * B);
+    const auto dqd = r.take<float>(size_t(nv) * B);
+    const auto dx = r.take<float>(size_t(nv) * B);
+    const auto fext = r.take<float>(size_t(6) * n * B);
+    std::fclose(f);
+    Out o;
+    const bool chain7 = hm.kind == kKindChain && n == 7;
+    if (chain7)
+      run_all<SegTopo<8, false>, 8>(hm, B, nf, frames.data(), q.data(), qd.data(), qdd.data(), tau.data(),
+                                    gbar.data(), dq.data(), dqd.data(), dx.data(), fext.data(), o, true);
+    else if (hm.free_root)
+      run_all<SegTopo<64, true>, 64>(hm, B, nf, frames.data(), q.data(), qd.data(), qdd.data(), tau.data(),
+                                     gbar.data(), dq.data(), dqd.data(), dx.data(), fext.data(), o, false);
+    else
+      run_all<SegTopo<64, false>, 64>(hm, B, nf, frames.data(), q.data(), qd.data(), qdd.data(), tau.data(),
+                                      gbar.data(), dq.data(), dqd.data(), dx.data(), fext.data(), o, false);
+    FILE* g = std::fopen(argv[2], "wb");
+    if (!g) throw std::string("cannot open output");
+    const int32_t count = static_cast<int32_t>(o.arrays.size());
+    std::fwrite(&count, sizeof(count), 1, g);
+    for (auto& a : o.arrays) {
+      char name[32] = {0};
+      std::strncpy(name, a.first.c_str(), sizeof(name) - 1);
+      const int64_t len = static_cast<int64_t>(a.second.size());
+      std::fwrite(name, 1, sizeof(name), g);
+      std::fwrite(&len, sizeof(len), 1, g);
+      std::fwrite(a.second.data(), sizeof(float), a.second.size(), g);
+    }
+    std::fclose(g);
+  } catch (const std::string& e) {
+    std::fprintf(stderr, "host_kernels: %s\n", e.c_str());
+    return 1;
+  }
+  return 0;
+}
