@@ -170,6 +170,9 @@ FRAX_API frax_status frax_rnea_vjp(frax_model_t model, int64_t B, int64_t ld, co
  * frax_aba_vjp — reverse-mode derivative of Eq. 2 at qdd = ABA(q, qd, tau)
  * (qdd is passed in, as saved by the forward call). With w = M^-1 gbar:
  *   taubar = w, qbar = -(dtau/dq)^T w (ambient layout), qdbar = -(dtau/dqd)^T w.
+ * Any output may be NULL (not all three): it is not written. For a 7-body
+ * serial chain a NULL taubar runs the one-launch form, a non-NULL one the
+ * factor solve into taubar followed by the adjoint sweep (two launches).
  */
 FRAX_API frax_status frax_aba_vjp(frax_model_t model, int64_t B, int64_t ld, const float* q,
                          const float* qd, const float* tau, const float* qdd, const float* gbar,
