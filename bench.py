@@ -55,10 +55,10 @@ FP32_LANES_PER_SM = 128
 # plain kernel's count plus the force sweep's (554 chain, 2585 humanoid).
 FLOPS = {
     "chain7": {"fk_jac": 748, "fk": 664, "rnea": 1683, "bias": 1683, "crba_ltdl": 1586, "crba": 1453,
-               "aba": 3360, "rnea_vjp": 4272, "aba_vjp": 5949, "osc": 8219, "rnea_ext": 2237,
+               "aba": 3360, "aba_sweep": 4073, "rnea_vjp": 4272, "aba_vjp": 5949, "osc": 8219, "rnea_ext": 2237,
                "aba_ext": 3914, "fk_jvp": 593, "rnea_jvp": 4175, "aba_jvp": 5859},
     "humanoid": {"fk_jac": 4685, "fk": 3173, "rnea": 7761, "bias": 7755, "crba_ltdl": 13474, "crba": 9704,
-                 "aba": 20322, "rnea_vjp": 19471, "aba_vjp": 36261, "osc": 24675, "rnea_ext": 10346,
+                 "aba": 20322, "aba_sweep": 20322, "rnea_vjp": 19471, "aba_vjp": 36261, "osc": 24675, "rnea_ext": 10346,
                  "aba_ext": 22907, "fk_jvp": 2584, "rnea_jvp": 17866, "aba_jvp": 34310},
 }
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
@@ -92,7 +92,7 @@ def bytes_per_instance(op, nq, nv, nb, nframes, j_nonzero=None):
         "fk_jac": f * (nq + 12 * nb + (nframes * 6 * nv if j_nonzero is None else j_nonzero)),
         "rnea": f * (nq + 3 * nv), "bias": f * (nq + 2 * nv),
         "crba_ltdl": f * (nq + nv * nv + nv * (nv + 1) // 2),
-        "aba": f * (nq + 3 * nv),
+        "aba": f * (nq + 3 * nv), "aba_sweep": f * (nq + 3 * nv),
         "rnea_vjp": f * (2 * nq + 5 * nv), "aba_vjp": f * (2 * nq + 5 * nv),
         "osc": f * (nq + 2 * nv + 6),
         "rnea_ext": f * (nq + 3 * nv + 6 * nb), "aba_ext": f * (nq + 3 * nv + 6 * nb),
@@ -230,6 +230,7 @@ class Step:
             "bias": lambda: fx_.frax_rnea(m, d["q"], d["qd"], None, tau=o["tau"]),
             "crba_ltdl": lambda: fx_.frax_crba(m, d["q"], M=o["M"], LD=o["LD"]),
             "aba": lambda: fx_.frax_aba(m, d["q"], d["qd"], d["tau"], qdd=o["qdd"]),
+            "aba_sweep": lambda: fx_.frax_aba_articulated(m, d["q"], d["qd"], d["tau"], qdd=o["qdd"]),
             "rnea_vjp": lambda: fx_.frax_rnea_vjp(m, d["q"], d["qd"], d["qdd"], d["gbar"], qbar=o["rq"],
                                                   qdbar=o["rqd"], qddbar=o["rqdd"]),
             "aba_vjp": lambda: fx_.frax_aba_vjp(m, d["q"], d["qd"], d["tau"], o["qdd"], d["gbar"], qbar=o["aq"],
@@ -262,7 +263,9 @@ class Step:
 def time_step(step, steps, warmup, flush, world, dist, clocks=None):
     """Times `steps` passes of the step with CUDA events (per step and per
     kernel) on torch's current stream, the stream the kernels are launched
-    on; L2 is flushed between steps outside the events."""
+    on; L2 is flushed between steps outside the events. Returns the median
+    step time (ms), the median time of each op, launches, wall seconds and
+    the clock record."""
     import torch
     for _ in range(warmup):
         step.run()
@@ -288,8 +291,8 @@ def time_step(step, steps, warmup, flush, world, dist, clocks=None):
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks is not None else None
-    step_ms = sum(a.elapsed_time(b) for a, b in sev)
-    per_op_ms = {n: sum(e[n][0].elapsed_time(e[n][1]) for e in ev) / steps for n in step.ops}
+    step_ms = statistics.median(a.elapsed_time(b) for a, b in sev)
+    per_op_ms = {n: statistics.median(e[n][0].elapsed_time(e[n][1]) for e in ev) for n in step.ops}
     return step_ms, per_op_ms, launches, wall, clk
 
 
@@ -297,8 +300,8 @@ def time_graph(step, steps, warmup, flush, world, dist, clocks=None):
     """The same step captured once as a CUDA graph (the same calls, the same
     kernels; replaying it trims the host's launch gaps between them) and
     replayed `steps` times, L2 flushed between replays outside the events.
-    Returns (step_ms, launches, wall, clocks, None), or five Nones but the
-    last, the reason, when the capture fails."""
+    Returns (median step ms, launches, wall, clocks, None), or five Nones but
+    the last, the reason, when the capture fails."""
     import torch
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -335,18 +338,18 @@ def time_graph(step, steps, warmup, flush, world, dist, clocks=None):
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks is not None else None
-    return sum(a.elapsed_time(b) for a, b in sev), steps * step.kernels, wall, clk, None
+    return statistics.median(a.elapsed_time(b) for a, b in sev), steps * step.kernels, wall, clk, None
 
 
-def whole_job(step_ms, steps, evals_per_step, world, dist, device):
+def whole_job(step_ms, evals_per_step, world, dist, device):
     """Replicas: every rank times its own batch; the job's step time is the
-    slowest rank's (max over ranks) and the value counts every rank's
-    evaluations. Returns (ms per step, evaluations per second)."""
+    slowest rank's median step (max over ranks) and the value counts every
+    rank's evaluations. Returns (ms per step, evaluations per second)."""
     import torch
     t = torch.tensor([step_ms], dtype=torch.float64, device=device)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / steps
+    ms_per_step = float(t.item())
     return ms_per_step, world * evals_per_step / (ms_per_step / 1e3)
 
 
@@ -379,44 +382,73 @@ def measured_hbm_gbs():
         return 6800.0, "fallback"
 
 
+HUMANOID_OPS = ["fk_jac", "bias", "crba_ltdl", "aba", "rnea_vjp", "aba_vjp"]
+
+
 def cpu_baseline_child(args):
-    """Times the FP64 oracle (as it stands) on a bounded sample of the chain
-    workload, single-threaded. Prints one JSON object."""
+    """Times the FP64 oracle (as it stands), single-threaded, op by op, on
+    bounded samples of one robot's workload (the chain's six ops, or the
+    humanoid's with bias forces in place of RNEA): each op runs on batches
+    of fresh seeded states until its share of the time budget is spent
+    (perf_counter around many batches, as the paper times its Python
+    calls). Prints one JSON object with each op's evaluations per second
+    and the six-op aggregate 6 / sum(1 / rate)."""
     import numpy as np
 
     import gen
     from oracle import derivatives as dv
     from oracle import rbd
-    robot = gen.chain7(0)
-    t_budget = args.cpu_seconds
-    S = 256
-    done_inst = 0
-    t0 = time.perf_counter()
-    while True:
-        s = gen.draw_states(robot, S, 99 + done_inst)
-        g = gen.draw_gbar(robot.nv, S, 5 + done_inst)
-        rbd.fk_flat(robot, s.q)
-        rbd.jacobian(robot, s.q, list(robot.end_frames))
-        rbd.rnea(robot, s.q, s.qd, s.qdd)
-        M = rbd.crba(robot, s.q)
-        rbd.ltdl(M)
-        qdd = rbd.aba(robot, s.q, s.qd, s.tau)
-        dv.rnea_vjp(robot, s.q, s.qd, s.qdd, g)
-        dv.aba_vjp(robot, s.q, s.qd, s.tau, g)
-        done_inst += S
-        if time.perf_counter() - t0 > t_budget:
-            break
-    el = time.perf_counter() - t0
-    print(json.dumps({"value": len(OPS) * done_inst / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-                      "sample": f"{done_inst} instances of the 7-DoF chain, all 6 ops, FP64 numpy oracle, "
-                                f"{el:.1f} s, 1 thread"}))
+    robot = gen.chain7(0) if args.cpu_robot == "chain7" else gen.humanoid(0)
+    ops = OPS if args.cpu_robot == "chain7" else HUMANOID_OPS
+    frames = list(robot.end_frames)
+    per_op, inst = {}, {}
+    budget = args.cpu_seconds / len(ops)
+    for n, op in enumerate(ops):
+        S = 256 if args.cpu_robot == "chain7" else 64  # the oracle's cost per call is mostly per batch
+        done, el, k = 0, 0.0, 0
+        while el < budget:
+            s = gen.draw_states(robot, S, 99 + 1000 * n + k)
+            g = gen.draw_gbar(robot.nv, S, 5 + 1000 * n + k)
+            t0 = time.perf_counter()
+            if op == "fk_jac":
+                rbd.fk_flat(robot, s.q)
+                rbd.jacobian(robot, s.q, frames)
+            elif op == "rnea":
+                rbd.rnea(robot, s.q, s.qd, s.qdd)
+            elif op == "bias":
+                rbd.rnea(robot, s.q, s.qd, np.zeros_like(s.qd))
+            elif op == "crba_ltdl":
+                rbd.ltdl(rbd.crba(robot, s.q))
+            elif op == "aba":
+                rbd.aba(robot, s.q, s.qd, s.tau)
+            elif op == "rnea_vjp":
+                dv.rnea_vjp(robot, s.q, s.qd, s.qdd, g)
+            else:
+                dv.aba_vjp(robot, s.q, s.qd, s.tau, g)
+            el += time.perf_counter() - t0
+            done += S
+            k += 1
+        per_op[op] = done / el
+        inst[op] = done
+    agg = len(ops) / sum(1.0 / r for r in per_op.values())
+    print(json.dumps({"value": agg, "unit": UNIT, "cores": 1, "kind": "oracle", "per_op": per_op,
+                      "instances_per_op": inst,
+                      "sample": f"{args.cpu_robot}: each of {len(ops)} ops on fresh seeded states for "
+                                f"{budget:.1f} s ({sum(inst.values())} instances in all), FP64 numpy oracle, "
+                                f"1 thread; value = {len(ops)} / sum over ops of 1 / (evals/s)"}))
 
 
-def run_cpu_baseline(seconds):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--cpu-seconds",
-                        str(seconds)], capture_output=True, text=True, env=env, cwd=ROOT)
+def _child_cmd(robot, seconds):
+    return [sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--cpu-robot", robot,
+            "--cpu-seconds", str(seconds)]
+
+
+_CPU_ENV = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+
+
+def run_cpu_baseline(seconds, robot="chain7"):
+    env = dict(os.environ, **_CPU_ENV)
+    r = subprocess.run(_child_cmd(robot, seconds), capture_output=True, text=True, env=env, cwd=ROOT)
     for line in r.stdout.splitlines()[::-1]:
         if line.startswith("{"):
             return json.loads(line)
@@ -443,39 +475,41 @@ def cpu_model():
     return "unknown"
 
 
-def run_cpu_baseline_all_cores(seconds):
-    """The same oracle timing in one single-threaded process per host core,
-    all at once; the value sums their rates."""
+def run_cpu_baseline_all_cores(seconds, robot="chain7"):
+    """The same per-op oracle timing in one single-threaded process per host
+    core, all at once; each op's value sums the processes' rates."""
     n = os.cpu_count() or 1
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    procs = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--cpu-seconds",
-                               str(seconds)], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env,
-                              cwd=ROOT) for _ in range(n)]
-    total, inst = 0.0, 0
+    env = dict(os.environ, **_CPU_ENV)
+    procs = [subprocess.Popen(_child_cmd(robot, seconds), stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                              env=env, cwd=ROOT) for _ in range(n)]
+    per_op, inst = {}, 0
     for p in procs:
         out, _ = p.communicate()
         for line in out.splitlines()[::-1]:
             if line.startswith("{"):
                 d = json.loads(line)
-                total += d["value"] or 0.0
-                inst += int(d["sample"].split()[0])
+                for k, v in d["per_op"].items():
+                    per_op[k] = per_op.get(k, 0.0) + v
+                inst += sum(d["instances_per_op"].values())
                 break
-    return {"value": total, "unit": UNIT, "cores": n, "kind": "oracle", "cpu_model": cpu_model(),
-            "sample": f"{n} single-threaded processes at once, {inst} instances of the 7-DoF chain in all, "
-                      f"all 6 ops, FP64 numpy oracle, {seconds:.0f} s each"}
+    agg = len(per_op) / sum(1.0 / r for r in per_op.values()) if per_op else None
+    return {"value": agg, "unit": UNIT, "cores": n, "kind": "oracle", "cpu_model": cpu_model(), "per_op": per_op,
+            "sample": f"{n} single-threaded processes at once, {robot}, {inst} instances in all, FP64 numpy "
+                      f"oracle, {seconds:.0f} s each"}
 
 
 SERVE_OPS = ["rnea", "crba", "aba", "rnea_grad"]
 
 
-def serve_stream(fx, seconds, check_oracle=True):
+def serve_stream(fx, seconds, check_oracle=True, repeats=3):
     """Served workload: requests for the 7-DoF chain, the humanoid and 32
     random trees (3-64 bodies), op uniform over rnea / crba / aba /
     rnea-gradient, instance count log-uniform in [1, 4096]. The request
     traces are replayed natively (frax_server_replay): first a burst that
-    gives the saturation rate, then Poisson arrivals at 50 % and 90 % of it;
-    latency = completion seen by the host - arrival."""
+    gives the saturation rate, then Poisson arrivals at 50 % and 90 % of it,
+    each point repeated (p50/p99 per repeat and their medians); latency =
+    completion seen by the host - arrival. The server's device error word
+    and kernel launch count are reported with the results."""
     import numpy as np
 
     import gen
@@ -513,14 +547,21 @@ def serve_stream(fx, seconds, check_oracle=True):
     for frac in (0.5, 0.9):
         rate = frac * sat_req
         n = int(max(200, rate * seconds))
-        ks, tr = trace(n)
-        arrival = np.cumsum(trace_rng.exponential(1e6 / rate, size=n))
-        t0 = time.perf_counter()
-        lat, _ = srv.replay(tr, arrival)
-        el = time.perf_counter() - t0
-        points.append({"load": frac, "offered_rate_hz": rate, "requests": n,
-                       "p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
-                       "mean_us": float(lat.mean()), "evals_per_s": sum(pool[k][2] for k in ks) / el})
+        reps = []
+        for _ in range(repeats):
+            ks, tr = trace(n)
+            arrival = np.cumsum(trace_rng.exponential(1e6 / rate, size=n))
+            t0 = time.perf_counter()
+            lat, _ = srv.replay(tr, arrival)
+            el = time.perf_counter() - t0
+            reps.append({"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                         "mean_us": float(lat.mean()), "max_us": float(lat.max()),
+                         "evals_per_s": sum(pool[k][2] for k in ks) / el,
+                         "device_status": srv.info()["device_status"]})
+        points.append({"load": frac, "offered_rate_hz": rate, "requests_per_repeat": n, "repeats": reps,
+                       "p50_us": statistics.median(r["p50_us"] for r in reps),
+                       "p99_us": statistics.median(r["p99_us"] for r in reps),
+                       "evals_per_s": statistics.median(r["evals_per_s"] for r in reps)})
     err, checked = {}, 0
     if check_oracle:
         from oracle import derivatives as dv
@@ -547,7 +588,104 @@ def serve_stream(fx, seconds, check_oracle=True):
                         "host-seen completion - arrival",
             "saturation_req_per_s": sat_req, "saturation_evals_per_s": sat_inst, "points": points,
             "max_rel_err_vs_oracle": err, "checked_requests": checked,
-            "kernel_launches": info["kernel_launches"], "resident_ctas": info["resident_ctas"]}
+            "kernel_launches": info["kernel_launches"], "resident_ctas": info["resident_ctas"],
+            "device_status": info["device_status"], "completed": info["completed"],
+            "idle_exit_ms": 20.0}
+
+
+SWEEP_B = [1, 4, 16, 64, 256, 1024, 4096, 16384, 1 << 16, 1 << 18, 1 << 20]
+
+
+def batch_sweep(fx, device, flush):
+    """Throughput against batch size (the shape of the paper's Fig. 2) for the
+    chain's and the humanoid's six-op steps: kernel time (the step's public
+    calls captured once as a CUDA graph and replayed, CUDA events, L2 flushed
+    between replays), the calls issued one by one (CUDA events between them),
+    the host time to issue one public call (Python binding + C ABI + launch,
+    no synchronisation), and end to end through the public API (pinned inputs
+    copied in, the six calls, every output copied back, synchronised; host
+    clock). Medians over the repetitions."""
+    import torch
+
+    import gen
+    res = {"workload": "six-op steps of the 7-DoF chain (FK+J, RNEA, CRBA+LTDL, ABA, RNEA-VJP, ABA-VJP) and the "
+                       "humanoid (bias in place of RNEA) at each batch size; evals = 6 x B per step",
+           "statistic": "median over repetitions", "launches": 0}
+    for name, robot, ops, bmax in (("chain7", gen.chain7(0), OPS, 1 << 20),
+                                   ("humanoid", gen.humanoid(0), HUMANOID_OPS, 1 << 18)):
+        model = fx.Model.from_robot(robot)
+        rows = []
+        for B in [b for b in SWEEP_B if b <= bmax]:
+            host, dev = make_inputs(robot, B, 4004, device)
+            step = Step(fx, model, robot, dev, device, ops)
+            reps = 200 if B <= 4096 else (40 if B <= (1 << 16) else 12)
+            g_ms, g_l, _, _, why = time_graph(step, reps, 3, flush, 1, None)
+            e_ms, _, e_l, _, _ = time_step(step, reps, 3, flush, 1, None)
+            res["launches"] += (g_l or 0) + e_l
+            torch.cuda.synchronize()
+            host_us = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                step.run()
+                host_us.append((time.perf_counter() - t0) * 1e6 / len(ops))
+                torch.cuda.synchronize()
+            res["launches"] += reps * step.kernels
+            pin = {k: v.pin_memory() for k, v in host.items()}
+            keys = [k for n in ops for k in OUT_OF[n]]
+            outh = {k: torch.empty(step.out[k].shape, dtype=torch.float32).pin_memory() for k in keys}
+            e2e_us = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for k in dev:
+                    dev[k].copy_(pin[k], non_blocking=True)
+                step.run()
+                for k in keys:
+                    outh[k].copy_(step.out[k], non_blocking=True)
+                torch.cuda.synchronize()
+                e2e_us.append((time.perf_counter() - t0) * 1e6)
+            res["launches"] += reps * step.kernels
+            ev = len(ops) * B
+            e2e = statistics.median(e2e_us)
+            rows.append({"B": B, "reps": reps,
+                         "kernel_us": g_ms * 1e3 if g_ms is not None else None,
+                         "kernel_evals_per_s": ev / (g_ms / 1e3) if g_ms is not None else None,
+                         "graph": why or "replayed",
+                         "eager_us": e_ms * 1e3, "eager_evals_per_s": ev / (e_ms / 1e3),
+                         "host_us_per_call": statistics.median(host_us),
+                         "e2e_us": e2e, "e2e_evals_per_s": ev / (e2e / 1e6),
+                         "h2d_bytes": sum(v.numel() * 4 for v in pin.values()),
+                         "d2h_bytes": sum(v.numel() * 4 for v in outh.values())})
+            del step, dev, host, pin, outh
+        res[name] = rows
+    return res
+
+
+def fp32_probe(fx, device, phys):
+    """The FP32 rate a kernel of independent FMA chains attains here (scalar
+    FFMA and the packed two-lane form), best of five 10 ms launches, with the
+    SM clock sampled meanwhile."""
+    import torch
+    blocks = SM_COUNT * 8
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=device)
+    clocks = ClockSampler(phys)
+    out = {}
+    clocks.start()
+    time.sleep(0.2)
+    for packed in (False, True):
+        fx.frax_fp32_probe(packed, blocks, 2000, sink)
+        best = 0.0
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fl = fx.frax_fp32_probe(packed, blocks, 50000, sink)
+            b.record()
+            torch.cuda.synchronize()
+            best = max(best, fl / (a.elapsed_time(b) / 1e3) / 1e12)
+        out["packed_tflops" if packed else "scalar_tflops"] = best
+    out["clocks"] = clocks.stop()
+    out["kernel"] = "frax_fp32_probe: 152 x 8 blocks of 256 threads, 8 independent FMA chains per thread"
+    return out
 
 
 # ---------------------------------------------------------------- main arms
@@ -555,6 +693,7 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     base = run_cpu_baseline(min(30.0, args.cpu_seconds * 2))
+    base["cpu_model"] = cpu_model()
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -566,6 +705,7 @@ def reference_arm(args, rank, world):
 
 
 OUT_OF = {"fk_jac": ("pose", "J"), "rnea": ("tau",), "bias": ("tau",), "crba_ltdl": ("M", "LD"), "aba": ("qdd",),
+          "aba_sweep": ("qdd",),
           "rnea_vjp": ("rq", "rqd", "rqdd"), "aba_vjp": ("aq", "aqd", "at")}
 
 
@@ -661,7 +801,7 @@ def frax_arm(args, rank, world, local_rank):
             launch_mode = "the step's public calls captured once as a CUDA graph and replayed"
         else:
             launch_mode += f" (graph capture failed: {why})"
-    ms_per_step, value = whole_job(step_ms, args.steps, len(OPS) * B, world, dist, device)
+    ms_per_step, value = whole_job(step_ms, len(OPS) * B, world, dist, device)
     hbm, hbm_src = measured_hbm_gbs()
     per_op = roofline_of(per_op_ms, FLOPS["chain7"], B, peak, hbm, robot)
     dom = max(OPS, key=lambda n: per_op_ms[n])
@@ -694,13 +834,13 @@ def frax_arm(args, rank, world, local_rank):
         _, hdev = make_inputs(hrobot, hB, 2002 + rank, device)
         hops = ["fk_jac", "bias", "crba_ltdl", "aba", "rnea_vjp", "aba_vjp"]
         hstep = Step(fx, hmodel, hrobot, hdev, device, hops)
-        hsteps = max(5, args.steps // 5)
+        hsteps = max(20, args.steps // 4)
         hms, hper, hl, _, _ = time_step(hstep, hsteps, max(3, args.warmup), flush, world, dist)
         launches += hl
         humanoid = {"workload": "floating-base humanoid (root + 29 revolute, seed 0), 2^18 instances; FK + 4 "
                                 "end-frame Jacobians, bias forces, CRBA + LTDL, ABA, RNEA-VJP, ABA-VJP",
-                    "batch": hB, "steps": hsteps, "ms_per_step": hms / hsteps,
-                    "evals_per_s": world * len(hops) * hB / (hms / hsteps / 1e3),
+                    "batch": hB, "steps": hsteps, "ms_per_step": hms, "statistic": "median over steps",
+                    "evals_per_s": world * len(hops) * hB / (hms / 1e3),
                     "per_op": roofline_of(hper, FLOPS["humanoid"], hB, peak, hbm, hrobot)}
         del hstep, hdev
 
@@ -710,7 +850,9 @@ def frax_arm(args, rank, world, local_rank):
     nxt = None
     if not args.no_next:
         nxt = {"workload": "operational-space control tau = J^T Lambda (xdd - Jdot qd) + c + g for the last end "
-                           "frame (xdd uniform in [-3, 3]); RNEA and ABA with standard-normal external spatial "
+                           "frame (xdd uniform in [-3, 3]); for the chain, forward dynamics by the O(n) "
+                           "articulated-body sweeps (aba_sweep, frax_aba_articulated) beside frax_aba's factor "
+                           "solve; RNEA and ABA with standard-normal external spatial "
                            "forces on every body; JVPs of FK (end frames), RNEA and ABA along standard-normal "
                            "directions (the ABA JVP at the input qdd as saved forward result); 7-DoF chain 2^20, "
                            "humanoid 2^18 instances"}
@@ -723,8 +865,10 @@ def frax_arm(args, rank, world, local_rank):
             for k in ("dq", "dqd", "dx"):
                 odev[k] = torch.from_numpy(rng.standard_normal((orobot.nv, oB), np.float32)).to(device)
             oops = ["osc", "rnea_ext", "aba_ext", "fk_jvp", "rnea_jvp", "aba_jvp"]
+            if oname == "chain7":  # the O(n) articulated-body sweeps beside the factor solve frax_aba runs
+                oops.append("aba_sweep")
             ostep = Step(fx, omodel, orobot, odev, device, oops, task=OSC_TASK[oname])
-            osteps = max(5, args.steps // 5)
+            osteps = max(20, args.steps // 4)
             oms, oper, ol, _, _ = time_step(ostep, osteps, max(3, args.warmup), flush, world, dist)
             launches += ol
             nxt[oname] = {"osc_task_body": OSC_TASK[oname], "batch": oB, "steps": osteps,
@@ -746,6 +890,25 @@ def frax_arm(args, rank, world, local_rank):
             nxt["fk_scan"][f"B{sB}"] = {"fk_us": sper["fk"] * 1e3, "fk_scan_us": sper["fk_scan"] * 1e3}
             del sstep, sdev
 
+    sweep = None
+    if not args.no_sweep:
+        sweep = batch_sweep(fx, device, flush)
+        launches += sweep.pop("launches")
+
+    # the FP32 rate a kernel of independent FMA chains attains: each ALU-bound
+    # op's rate is also given as a fraction of it (scalar and packed)
+    probe = fp32_probe(fx, device, phys)
+    launches += 12
+    tables = [per_op] + ([humanoid["per_op"]] if humanoid else []) + \
+        ([nxt[k]["per_op"] for k in ("chain7", "humanoid")] if nxt else [])
+    for tab in tables:
+        for r in tab.values():
+            r["frac_of_measured_fp32_scalar"] = r["tflops"] / probe["scalar_tflops"]
+            r["frac_of_measured_fp32_packed"] = r["tflops"] / probe["packed_tflops"]
+    if roofline["bound"] == "alu":
+        roofline["frac_of_measured_fp32_scalar"] = roofline["achieved"] / probe["scalar_tflops"]
+        roofline["frac_of_measured_fp32_packed"] = roofline["achieved"] / probe["packed_tflops"]
+
     serve = None
     if rank == 0 and not args.no_serve:
         serve = serve_stream(fx, args.serve_seconds)
@@ -754,18 +917,23 @@ def frax_arm(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = run_cpu_baseline(args.cpu_seconds)
         cpu["cpu_model"] = cpu_model()
-        cpu_all = run_cpu_baseline_all_cores(min(10.0, args.cpu_seconds))
+        hcpu = run_cpu_baseline(args.cpu_seconds, "humanoid")
+        cpu["humanoid"] = {k: hcpu.get(k) for k in ("value", "per_op", "sample")}
+        cpu_all = run_cpu_baseline_all_cores(min(8.0, args.cpu_seconds))
+        hall = run_cpu_baseline_all_cores(min(8.0, args.cpu_seconds), "humanoid")
+        cpu_all["humanoid"] = {k: hall.get(k) for k in ("value", "per_op", "sample")}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "statistic": "median over steps",
                 "config": {"workload": "7-DoF revolute chain (seed 0), 2^20 instances per GPU; one step = "
                                        "FK+EE Jacobian, RNEA, CRBA+LTDL, ABA, RNEA-VJP, ABA-VJP",
                            "global_batch": B * world, "parallelism": f"replicas x{world}",
                            "l2": "256 MB buffer written between steps (L2 flush)", "launch": launch_mode},
                 "clocks": clk, "gpu_launches": launches, "wall_s": wall, "per_op": per_op, "roofline": roofline,
-                "e2e": e2e, "humanoid": humanoid, "next_rows": nxt, "cpu_baseline": cpu,
+                "e2e": e2e, "humanoid": humanoid, "next_rows": nxt, "batch_sweep": sweep,
+                "fp32_peak_measured": probe, "cpu_baseline": cpu,
                 "cpu_baseline_all_cores": cpu_all, "serving": serve}
         print(json.dumps(line))
 
@@ -782,12 +950,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-humanoid", action="store_true")
     ap.add_argument("--no-next", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time the step as separate calls, not a CUDA graph")
     ap.add_argument("--humanoid-batch", type=int, default=1 << 18)
     ap.add_argument("--count-flops", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--cpu-baseline-child", action="store_true")
+    ap.add_argument("--cpu-robot", default="chain7", choices=["chain7", "humanoid"])
     args = ap.parse_args()
     if args.cpu_baseline_child:
         cpu_baseline_child(args)

@@ -153,6 +153,17 @@ FRAX_API frax_status frax_aba(frax_model_t model, int64_t B, int64_t ld, const f
                      const float* tau, float* qdd, void* stream);
 
 /*
+ * frax_aba_articulated — the same forward dynamics (Eq. 2 with f = 0),
+ * always by the O(n) articulated-body algorithm: a velocity sweep outward,
+ * articulated inertias and bias forces inward, accelerations outward. For
+ * trees this is what frax_aba runs; for 7-body chains (where frax_aba solves
+ * through the mass-matrix factor) it runs the unrolled articulated-body
+ * sweeps. Arguments, layout and errors as frax_aba.
+ */
+FRAX_API frax_status frax_aba_articulated(frax_model_t model, int64_t B, int64_t ld, const float* q,
+                                          const float* qd, const float* tau, float* qdd, void* stream);
+
+/*
  * frax_rnea_vjp — reverse-mode derivative of Eq. 1 (analytic RNEA
  * derivatives, Sec. VI future work). Given gbar (adjoint of tau):
  *   qbar   = (dtau/dq)^T gbar     [nq][ld] (ambient layout: a free-flyer
@@ -349,7 +360,12 @@ FRAX_API frax_status frax_server_replay(frax_server_t srv, int n, const int* mod
  * calls ordered on one stream are correct, but calls whose kernels overlap
  * (unordered streams) race on it. The first call on each device looks up the
  * array's address (cudaGetSymbolAddress) and caches it: make that first call
- * before any stream capture. Asynchronous on `stream`.
+ * before any stream capture. The kernel runs asynchronously on `stream`, but
+ * the descriptors and model images are copied from a pageable host buffer,
+ * so the call may block the host until the stream's earlier work is done: a
+ * control loop that must never block should order its calls accordingly.
+ * While `stream` is being captured the call returns FRAX_EINVAL and enqueues
+ * nothing (a captured copy would read the staging buffer at replay time).
  * ---------------------------------------------------------------------- */
 enum { FRAX_NOALLOC_MAX_REQUESTS = 256, FRAX_NOALLOC_MAX_MODELS = 16 };
 typedef struct {
@@ -360,6 +376,36 @@ typedef struct {
   float* out[3];      /* device outputs, unused entries NULL     */
 } frax_batch_request_t;
 FRAX_API frax_status frax_serve_batch_noalloc(const frax_batch_request_t* reqs, int n_reqs, void* stream);
+
+/* ------------------------------------------------------------------------
+ * frax_debug_inject_fault — test support for the server's error paths (no
+ * counterpart in the paper). Arms one host-side injection point: the
+ * (after+1)-th time the library reaches it, the host allocation or CUDA call
+ * there is skipped and treated as failed, once; the public call then returns
+ * the error it documents (FRAX_ENOMEM or FRAX_ECUDA) and releases what it
+ * had taken. Nothing is injected on the GPU. Points: FRAX_FAULT_SERVER_ALLOC
+ * (frax_server_create's host struct), FRAX_FAULT_SLAB_HOST (its pinned host
+ * mirror of the slab), FRAX_FAULT_SUBMIT_INPUT (frax_server_submit's input
+ * copy), FRAX_FAULT_SUBMIT_PUBLISH (its descriptor copy),
+ * FRAX_FAULT_COLLECT_COPY (frax_server_collect's output copy);
+ * FRAX_FAULT_NONE disarms. Returns FRAX_EINVAL unless the process was
+ * started with FRAX_FAULT_INJECTION=1 in its environment.
+ * ---------------------------------------------------------------------- */
+enum { FRAX_FAULT_NONE = 0, FRAX_FAULT_SERVER_ALLOC = 1, FRAX_FAULT_SLAB_HOST = 2, FRAX_FAULT_SUBMIT_INPUT = 3,
+       FRAX_FAULT_SUBMIT_PUBLISH = 4, FRAX_FAULT_COLLECT_COPY = 5 };
+FRAX_API frax_status frax_debug_inject_fault(int point, int after);
+
+/* ------------------------------------------------------------------------
+ * frax_fp32_probe — measurement support (no counterpart in the paper):
+ * launches `blocks` blocks of 256 threads that each run 8 independent chains
+ * of `iters` dependent FP32 fused multiply-adds, scalar (packed = 0) or in
+ * the two-lane packed form (packed = 1), and store one float per thread
+ * into `sink` (device, at least blocks * 256 floats). *flops (may be NULL)
+ * receives the FP32 operations the launch performs (an FMA counts 2), so
+ * flops / (launch time) is the FP32 rate this GPU attains. Asynchronous on
+ * `stream`; FRAX_EINVAL on bad sizes.
+ * ---------------------------------------------------------------------- */
+FRAX_API frax_status frax_fp32_probe(int packed, int blocks, int iters, float* sink, double* flops, void* stream);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 FRAX_API const char* frax_last_error(void);

@@ -28,6 +28,9 @@ SIGNATURES = {
     "frax_rnea": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_crba": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "frax_aba": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_aba_articulated": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "frax_debug_inject_fault": (c_int, [c_int, c_int]),
+    "frax_fp32_probe": (c_int, [c_int, c_int, c_int, c_vp, ctypes.POINTER(ctypes.c_double), c_vp]),
     "frax_rnea_vjp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_aba_vjp": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "frax_ltdl_solve": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),

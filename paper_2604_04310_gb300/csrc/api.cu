@@ -1,10 +1,14 @@
 // C ABI: argument validation, model handles, kernel dispatch.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <new>
 #include <string>
 
+#include "fault.h"
 #include "handles.h"
 #include "launch.h"
 
@@ -20,6 +24,25 @@ frax_status set_error(frax_status s, const std::string& msg) {
 frax_status clear_error() {
   g_last_error.clear();
   return FRAX_OK;
+}
+
+namespace {
+std::atomic<int> g_fault_point{kFaultNone};
+std::atomic<int> g_fault_countdown{0};
+bool fault_injection_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("FRAX_FAULT_INJECTION");
+    return v && std::strcmp(v, "1") == 0;
+  }();
+  return on;
+}
+}  // namespace
+
+bool fault_hit(int point) {
+  if (g_fault_point.load(std::memory_order_relaxed) != point) return false;
+  if (g_fault_countdown.fetch_sub(1) > 0) return false;
+  int expected = point;
+  return g_fault_point.compare_exchange_strong(expected, kFaultNone);
 }
 }  // namespace frax
 
@@ -77,6 +100,16 @@ thread_local frax::ZeroRows g_zero_rows;
 extern "C" {
 
 const char* frax_last_error(void) { return g_last_error.c_str(); }
+
+frax_status frax_debug_inject_fault(int point, int after) {
+  if (!frax::fault_injection_enabled())
+    return fail(FRAX_EINVAL, "frax_debug_inject_fault: disabled (start the process with FRAX_FAULT_INJECTION=1)");
+  if (point < frax::kFaultNone || point >= frax::kFaultCount || after < 0)
+    return fail(FRAX_EINVAL, "frax_debug_inject_fault: bad point or count");
+  frax::g_fault_countdown.store(after);
+  frax::g_fault_point.store(point);
+  return ok();
+}
 const char* frax_version(void) { return "frax-gb300 0.1 (sm_103a)"; }
 
 frax_status frax_model_create(int n_bodies, const int32_t* parent, const int32_t* joint_type,
@@ -91,6 +124,22 @@ frax_status frax_model_create(int n_bodies, const int32_t* parent, const int32_t
   if (!err.empty()) {
     delete h;
     return fail(FRAX_EINVAL, "frax_model_create: " + err);
+  }
+  if (h->m.kind != frax::kKindChain) {
+    for (int want = 1; want <= 3; ++want) {
+      frax::ZeroRows* z = new (std::nothrow) frax::ZeroRows;
+      if (!z) {
+        delete h;
+        return fail(FRAX_ENOMEM, "frax_model_create: out of host memory");
+      }
+      z->n0 = z->n = 0;
+      if (want & 1)
+        for (uint16_t r : h->m.zero_M) z->row[z->n++] = r;
+      z->n0 = z->n;
+      if (want & 2)
+        for (uint16_t r : h->m.zero_LD) z->row[z->n++] = r;
+      h->crba_zeros[want].reset(z);
+    }
   }
   *out = h;
   return ok();
@@ -177,16 +226,8 @@ frax_status frax_crba(frax_model_t model, int64_t B, int64_t ld, const float* q,
   frax::OpArgs a;
   a.B = B; a.ld = ld; a.q = q; a.out0 = M; a.out1 = LD; a.stream = static_cast<cudaStream_t>(stream);
   const frax::HostModel& m = model->m;
-  if (m.kind != frax::kKindChain) {  // the tree kernel writes the structural zeros too
-    frax::ZeroRows& z = g_zero_rows;
-    z.n0 = z.n = 0;
-    if (M)
-      for (uint16_t r : m.zero_M) z.row[z.n++] = r;
-    z.n0 = z.n;
-    if (LD)
-      for (uint16_t r : m.zero_LD) z.row[z.n++] = r;
-    a.zeros = &z;
-  }
+  if (m.kind != frax::kKindChain)  // the tree kernel writes the structural zeros too
+    a.zeros = model->crba_zeros[(M ? 1 : 0) | (LD ? 2 : 0)].get();
   return dispatch(model, frax::kOpCrba, a, "frax_crba");
 }
 
@@ -202,6 +243,20 @@ frax_status frax_aba(frax_model_t model, int64_t B, int64_t ld, const float* q, 
   a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.tau = tau; a.out0 = qdd;
   a.stream = static_cast<cudaStream_t>(stream);
   return dispatch(model, frax::kOpAba, a, "frax_aba");
+}
+
+frax_status frax_aba_articulated(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,
+                                 const float* tau, float* qdd, void* stream) {
+  FRAX_TRY(check_batch(model, B, ld, "frax_aba_articulated"));
+  if (B == 0) return ok();
+  FRAX_TRY(need(q, "frax_aba_articulated", "q"));
+  FRAX_TRY(need(qd, "frax_aba_articulated", "qd"));
+  FRAX_TRY(need(tau, "frax_aba_articulated", "tau"));
+  FRAX_TRY(need(qdd, "frax_aba_articulated", "qdd"));
+  frax::OpArgs a;
+  a.B = B; a.ld = ld; a.q = q; a.qd = qd; a.tau = tau; a.out0 = qdd;
+  a.stream = static_cast<cudaStream_t>(stream);
+  return dispatch(model, frax::kOpAbaSweep, a, "frax_aba_articulated");
 }
 
 frax_status frax_rnea_vjp(frax_model_t model, int64_t B, int64_t ld, const float* q, const float* qd,

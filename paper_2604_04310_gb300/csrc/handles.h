@@ -4,10 +4,16 @@
 #include <string>
 
 #include "../../include/frax.h"
+#include <memory>
+
+#include "launch.h"
 #include "model.h"
 
 struct frax_model_s {
   frax::HostModel m;
+  // Trees: the structural zeros the CRBA kernel writes, per requested output
+  // (index 1: M only, 2: the factor only, 3: both), listed once at creation.
+  std::unique_ptr<frax::ZeroRows> crba_zeros[4];
 };
 
 namespace frax {

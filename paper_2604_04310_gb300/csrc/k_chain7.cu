@@ -132,8 +132,7 @@ __global__ void __launch_bounds__(kBlock) k_rnea_vjp_chain7(const __grid_constan
 
 cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
   if (op == kOpAbaVjp && a.out2) {
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
     k_minv_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.gbar, a.out2);
     k_aba_vjp_tail_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.out2, a.out0,
@@ -141,61 +140,53 @@ cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
     return cudaGetLastError();
   }
   if (op == kOpRneaExt) {
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
     k_rnea_ext_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.in_fext, a.out0);
     return cudaGetLastError();
   }
   if (op == kOpAbaExt) {
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
     k_aba_ext_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.tau, a.in_fext, a.out0);
     return cudaGetLastError();
   }
   if (op == kOpAba) {
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
     k_aba_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.tau, a.out0);
     return cudaGetLastError();
   }
   if (op == kOpAbaJvp) {
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
     k_aba_jvp_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.in_dq, a.in_dqd, a.in_dx,
                                                     a.out0);
     return cudaGetLastError();
   }
   if (op == kOpAbaVjp) {
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
     k_aba_vjp_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1,
                                                     a.out2);
     return cudaGetLastError();
   }
   if (op == kOpRneaVjp) {
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
     k_rnea_vjp_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1,
                                                      a.out2);
     return cudaGetLastError();
   }
   if (op == kOpRneaJvp) {
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
     k_rnea_jvp_chain7<<<grid, kBlock, 0, a.stream>>>(img8, a.B, a.ld, a.q, a.qd, a.qdd, a.in_dq, a.in_dqd, a.in_dx,
                                                      a.out0, a.out1);
     return cudaGetLastError();
   }
   if (op == kOpFkJvp) {
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     Frames fr{a.frames.n, {0}};
     for (int f = 0; f < a.frames.n; ++f) fr.body[f] = a.frames.body[f];
     const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
@@ -204,12 +195,9 @@ cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
   }
   if (op == kOpOsc) {
     // OSC: the segment code (rolled loops)
-    ModelImage<8> img8;
-    m.pack(&img8);
+    const ModelImage<8>& img8 = m.image<8>();
     return launch_topo<SegTopo<8, false>>(img8, op, a);
   }
-  ModelImage<7> img;
-  m.pack(&img);
-  return launch_topo<ChainTopo<7>>(img, op, a);
+  return launch_topo<ChainTopo<7>>(m.image<7>(), op, a);
 }
 }  // namespace frax

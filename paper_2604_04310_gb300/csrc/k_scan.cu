@@ -109,8 +109,7 @@ __global__ void __launch_bounds__(kBlock) k_fk_scan(const __grid_constant__ Mode
 }
 
 cudaError_t launch_fk_scan(const HostModel& m, const OpArgs& a) {
-  ModelImage<64> img;
-  m.pack(&img);
+  const ModelImage<64>& img = m.image<64>();
   const int64_t threads = a.B * 32;
   const dim3 grid(unsigned((threads + kBlock - 1) / kBlock));
   if (m.free_root)

@@ -3,8 +3,7 @@
 
 namespace frax {
 cudaError_t launch_tree32(const HostModel& m, Op op, const OpArgs& a) {
-  ModelImage<32> img;
-  m.pack(&img);
+  const ModelImage<32>& img = m.image<32>();
   return m.free_root ? launch_topo<SegTopo<32, true>>(img, op, a) : launch_topo<SegTopo<32, false>>(img, op, a);
 }
 }  // namespace frax

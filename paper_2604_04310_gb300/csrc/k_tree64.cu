@@ -3,8 +3,7 @@
 
 namespace frax {
 cudaError_t launch_tree64(const HostModel& m, Op op, const OpArgs& a) {
-  ModelImage<64> img;
-  m.pack(&img);
+  const ModelImage<64>& img = m.image<64>();
   return m.free_root ? launch_topo<SegTopo<64, true>>(img, op, a) : launch_topo<SegTopo<64, false>>(img, op, a);
 }
 }  // namespace frax

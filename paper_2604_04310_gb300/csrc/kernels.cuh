@@ -220,6 +220,7 @@ cudaError_t launch_topo(const ModelImage<T::NBMAX>& img, Op op, const OpArgs& a)
       else k_crba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.out0, a.out1);
       break;
     case kOpAba:
+    case kOpAbaSweep:
       if constexpr (T::kSeg) k_aba_seg<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.out0);
       else k_aba<T><<<grid, block, 0, a.stream>>>(img, a.B, a.ld, a.q, a.qd, a.tau, a.out0);
       break;

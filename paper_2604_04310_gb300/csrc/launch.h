@@ -9,7 +9,9 @@
 namespace frax {
 
 enum Op { kOpFk = 0, kOpJac, kOpRnea, kOpCrba, kOpAba, kOpRneaVjp, kOpAbaVjp, kOpLtdlSolve, kOpLtdlInverse,
-          kOpOsc, kOpRneaExt, kOpAbaExt, kOpFkJvp, kOpRneaJvp, kOpAbaJvp, kOpCount };
+          kOpOsc, kOpRneaExt, kOpAbaExt, kOpFkJvp, kOpRneaJvp, kOpAbaJvp,
+          kOpAbaSweep,  // forward dynamics by the articulated-body sweeps whatever the topology
+          kOpCount };
 
 struct FramesArg {
   int n;

@@ -1,6 +1,9 @@
 // Model validation, derived tree structure and FP32 image packing (host only).
 #include "model.h"
 
+#include <memory>
+#include <type_traits>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -332,6 +335,19 @@ std::string build_model(int n, const int32_t* parent, const int32_t* joint_type,
   // the segment's first: each such body is the only child of a revolute body
   for (int i = 0; i < n; ++i)
     if (m.pos_of[i] > 0 && !m.bodies[i].dh) return fmt("body %d: segment body without a Rot_x frame", i);
+  auto packed = [&](auto* tag) {
+    using Img = std::remove_pointer_t<decltype(tag)>;
+    auto p = std::make_shared<Img>();
+    m.pack(p.get());
+    return std::shared_ptr<const Img>(std::move(p));
+  };
+  m.img64 = packed(static_cast<ModelImage<64>*>(nullptr));
+  if (m.kind == kKindChain) {
+    m.img7 = packed(static_cast<ModelImage<7>*>(nullptr));
+    m.img8 = packed(static_cast<ModelImage<8>*>(nullptr));
+  } else if (n <= 32) {
+    m.img32 = packed(static_cast<ModelImage<32>*>(nullptr));
+  }
   *out = std::move(m);
   return "";
 }

@@ -3,6 +3,7 @@
 #pragma once
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -31,7 +32,27 @@ struct HostModel {
 
   template <int NB>
   void pack(ModelImage<NB>* img) const;
+
+  // The packed images the batched kernels receive, made once by
+  // build_model so a call only copies them into its launch: the chain's
+  // (7 and 8 body slots) for 7-body chains, the 32-slot image for trees of
+  // up to 32 bodies, and the 64-slot image for every model.
+  std::shared_ptr<const ModelImage<7>> img7;
+  std::shared_ptr<const ModelImage<8>> img8;
+  std::shared_ptr<const ModelImage<32>> img32;
+  std::shared_ptr<const ModelImage<64>> img64;
+  template <int NB>
+  const ModelImage<NB>& image() const;
 };
+
+template <>
+inline const ModelImage<7>& HostModel::image<7>() const { return *img7; }
+template <>
+inline const ModelImage<8>& HostModel::image<8>() const { return *img8; }
+template <>
+inline const ModelImage<32>& HostModel::image<32>() const { return *img32; }
+template <>
+inline const ModelImage<64>& HostModel::image<64>() const { return *img64; }
 
 // Validates and derives everything; returns "" on success, else a message.
 std::string build_model(int n, const int32_t* parent, const int32_t* joint_type, const double* axis,

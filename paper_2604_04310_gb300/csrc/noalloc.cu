@@ -20,6 +20,14 @@
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress (with that device current) and caches it; make
 // that first call before any stream capture.
+//
+// Staging: descriptors and model images are copied from one static, pageable
+// host buffer. A copy from pageable memory returns only once the buffer has
+// been consumed, which is what lets the next call rewrite it at once, and it
+// may wait for the stream's earlier work first: the call can block the host.
+// A captured copy would instead read that buffer when the graph is replayed,
+// by then holding another call's requests, so the call refuses to run while
+// `stream` is capturing.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -127,6 +135,21 @@ using namespace frax;
 extern "C" frax_status frax_serve_batch_noalloc(const frax_batch_request_t* reqs, int n_reqs, void* stream) {
   if (n_reqs == 0) return clear_error();
   if (!reqs || n_reqs < 0) return set_error(FRAX_EINVAL, "frax_serve_batch_noalloc: bad request list");
+  {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap);
+    if (ce == cudaErrorStreamCaptureImplicit) {  // the legacy stream while another stream captures
+      cudaGetLastError();
+      return set_error(FRAX_EINVAL, "frax_serve_batch_noalloc: a stream capture is in progress");
+    }
+    if (ce != cudaSuccess)
+      return set_error(FRAX_ECUDA, std::string("frax_serve_batch_noalloc: cudaStreamIsCapturing: ") +
+                                       cudaGetErrorString(ce));
+    if (cap != cudaStreamCaptureStatusNone)
+      return set_error(FRAX_EINVAL,
+                       "frax_serve_batch_noalloc: stream is capturing; the staged copies would replay another "
+                       "call's requests");
+  }
   if (n_reqs > kNoallocMaxRequests)
     return set_error(FRAX_EINVAL, "frax_serve_batch_noalloc: more than FRAX_NOALLOC_MAX_REQUESTS (256) requests");
   std::lock_guard<std::mutex> lk(g_noalloc_mu);

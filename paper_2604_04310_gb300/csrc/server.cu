@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstddef>
 #include <chrono>
 #include <cstring>
 #include <map>
@@ -20,8 +21,9 @@
 #include <unordered_map>
 #include <vector>
 
-#include "seg.cuh"
+#include "fault.h"
 #include "handles.h"
+#include "seg.cuh"
 
 namespace frax {
 namespace {
@@ -45,10 +47,21 @@ struct ReqDesc {
 struct ServeCtl {
   unsigned long long next_tile;        // tiles claimed so far (monotonic)
   unsigned long long tiles_published;  // tiles whose request is visible
+  long long oldest;                    // no claimable tile belongs to a request older than this
+  unsigned long long last_claim_ns;    // globaltimer of the latest claim by any CTA
   unsigned int stop;                   // set by the host to end the kernel
   unsigned int pad;
   unsigned int done[kRing];            // finished tiles of the request in each slot
 };
+
+// What every submit publishes in one copy: the new tile count and the oldest
+// request still in flight (adjacent fields of ServeCtl). Both only grow, so
+// the kernel may read them separately.
+struct PubStage {
+  unsigned long long tiles_published;
+  long long oldest;
+};
+static_assert(offsetof(ServeCtl, oldest) == offsetof(ServeCtl, tiles_published) + 8, "PubStage layout");
 
 struct ServeArgs {
   const ReqDesc* ring;
@@ -67,8 +80,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
-  return *reinterpret_cast<const volatile unsigned long long*>(p);
+template <class U>
+__device__ __forceinline__ U ld_volatile(const U* p) {
+  return *reinterpret_cast<const volatile U*>(p);
 }
 
 // Chains of 7 run the unrolled chain code for the forward ops; every other
@@ -117,26 +131,44 @@ __global__ void __launch_bounds__(kTile) k_serve(const ServeArgs a) {
         if (cur < pub) {
           if (atomicCAS(&a.ctl->next_tile, cur, cur + 1) == cur) {
             got = static_cast<long long>(cur);
+            atomicMax(&a.ctl->last_claim_ns, global_ns());
             break;
           }
           continue;
         }
-        if (*reinterpret_cast<volatile unsigned int*>(&a.ctl->stop)) break;
-        if (global_ns() - t0 > a.idle_ns) break;  // bounded idle wait
+        if (ld_volatile(&a.ctl->stop)) break;
+        // Bounded idle wait, left together: a CTA leaves only once no CTA
+        // has claimed a tile for idle_ns (and it has waited that long
+        // itself), so under light load the pool does not shrink CTA by CTA.
+        const unsigned long long now = global_ns();
+        const unsigned long long last = max(t0, ld_volatile(&a.ctl->last_claim_ns));
+        if (now > last && now - last > a.idle_ns) break;
         __nanosleep(500);
       }
       if (got >= 0) {
-        // find the request that owns tile `got`: ranges grow with the request
-        // number, and the owner is still in flight, so its slot is intact
+        // Find the request that owns tile `got`. Tile ranges grow with the
+        // request number; the owner is still in flight, and it is neither
+        // older than this CTA's last request (tiles are claimed in order) nor
+        // than the oldest request in flight when the host last published.
+        // Between that request and the newest one there are at most kRing
+        // requests, none of whose ring slots has been reused, so one pass of
+        // kRing + 1 entries finds the owner. A miss (a descriptor not yet
+        // visible) is retried, bounded by idle_ns.
+        const unsigned long long tl0 = global_ns();
         long long r = hint;
         bool found = false;
-        for (int it = 0; it < 4 * kRing + 4; ++it, ++r) {
-          const ReqDesc* rd = &a.ring[r % kRing];
-          const long long seq = __ldcg(&rd->seq);
-          if (seq == r && got >= __ldcg(&rd->tile_begin) && got < __ldcg(&rd->tile_end)) {
-            found = true;
-            break;
+        while (true) {
+          r = max(hint, ld_volatile(&a.ctl->oldest));
+          for (int it = 0; it <= kRing; ++it, ++r) {
+            const ReqDesc* rd = &a.ring[r % kRing];
+            const long long seq = __ldcg(&rd->seq);
+            if (seq == r && got >= __ldcg(&rd->tile_begin) && got < __ldcg(&rd->tile_end)) {
+              found = true;
+              break;
+            }
           }
+          if (found || global_ns() - tl0 > a.idle_ns) break;
+          __nanosleep(1000);
         }
         if (!found) {
           atomicCAS(a.status, kDevOk, kDevLookup);
@@ -247,7 +279,7 @@ struct frax_server_s {
   int* status_h = nullptr;
   int* status_d = nullptr;
   ReqDesc* desc_stage = nullptr;          // pinned
-  unsigned long long* pub_stage = nullptr;  // pinned, one per slot
+  PubStage* pub_stage = nullptr;            // pinned, one per slot
   ModelImage<64>* model_stage = nullptr;    // pinned
   int n_models = 0;
   int model_kind[kMaxModels] = {};
@@ -381,7 +413,7 @@ frax_status frax_server_create(int64_t budget_bytes, double idle_exit_ms, frax_s
   if (budget_bytes < kAlign) return set_error(FRAX_EINVAL, "frax_server_create: budget_bytes too small");
   if (!(idle_exit_ms > 0) || idle_exit_ms > 60000)
     return set_error(FRAX_EINVAL, "frax_server_create: idle_exit_ms must be in (0, 60000]");
-  frax_server_s* s = new (std::nothrow) frax_server_s;
+  frax_server_s* s = fault_hit(kFaultServerAlloc) ? nullptr : new (std::nothrow) frax_server_s;
   if (!s) return set_error(FRAX_ENOMEM, "frax_server_create: out of host memory");
   s->budget = round_up(budget_bytes);
   s->idle_ms = idle_exit_ms;
@@ -397,7 +429,7 @@ frax_status frax_server_create(int64_t budget_bytes, double idle_exit_ms, frax_s
     cudaGetLastError();
     return bail(set_error(FRAX_ENOMEM, "frax_server_create: slab of budget_bytes does not fit on the device"));
   }
-  if ((e = cudaHostAlloc(&s->slab_h, s->budget, cudaHostAllocDefault)) != cudaSuccess) {
+  if (fault_hit(kFaultSlabHost) || (e = cudaHostAlloc(&s->slab_h, s->budget, cudaHostAllocDefault)) != cudaSuccess) {
     cudaGetLastError();
     return bail(set_error(FRAX_ENOMEM, "frax_server_create: pinned host staging of budget_bytes failed"));
   }
@@ -413,7 +445,7 @@ frax_status frax_server_create(int64_t budget_bytes, double idle_exit_ms, frax_s
     return bail(cuda_fail("cudaHostAlloc status", e));
   if ((e = cudaHostAlloc(&s->desc_stage, sizeof(ReqDesc) * kRing, cudaHostAllocDefault)) != cudaSuccess)
     return bail(cuda_fail("cudaHostAlloc", e));
-  if ((e = cudaHostAlloc(&s->pub_stage, sizeof(unsigned long long) * kRing, cudaHostAllocDefault)) != cudaSuccess)
+  if ((e = cudaHostAlloc(&s->pub_stage, sizeof(PubStage) * kRing, cudaHostAllocDefault)) != cudaSuccess)
     return bail(cuda_fail("cudaHostAlloc", e));
   if ((e = cudaHostAlloc(&s->model_stage, sizeof(ModelImage<64>), cudaHostAllocDefault)) != cudaSuccess)
     return bail(cuda_fail("cudaHostAlloc", e));
@@ -501,7 +533,10 @@ frax_status frax_server_submit(frax_server_t s, int model_id, int op, int64_t B,
   r.out_bytes = off + total - cur;
   // inputs, then the descriptor, then the published-tile count, in stream
   // order on one copy stream: the kernel can only see the count after both
-  cudaError_t e0 = cudaMemcpyAsync(s->slab + off, s->slab_h + off, r.in_bytes, cudaMemcpyHostToDevice, s->cstream);
+  cudaError_t e0 = fault_hit(kFaultSubmitInputCopy)
+                       ? cudaErrorUnknown
+                       : cudaMemcpyAsync(s->slab + off, s->slab_h + off, r.in_bytes, cudaMemcpyHostToDevice,
+                                         s->cstream);
   if (e0 != cudaSuccess) {
     slab_free(s, off, total);
     return cuda_fail("frax_server_submit: input copy", e0);
@@ -512,11 +547,16 @@ frax_status frax_server_submit(frax_server_t s, int model_id, int op, int64_t B,
     r.out_rows[k] = out_rows[k];
     cur += out_bytes[k];
   }
-  s->pub_stage[slot] = static_cast<unsigned long long>(s->tiles_total + ntiles);
-  cudaError_t e = cudaMemcpyAsync(s->ring + slot, &d, sizeof(ReqDesc), cudaMemcpyHostToDevice, s->cstream);
+  s->pub_stage[slot].tiles_published = static_cast<unsigned long long>(s->tiles_total + ntiles);
+  // the oldest request not yet collected (this one if none): a lower bound
+  // on the owner of any tile the kernel can still claim
+  s->pub_stage[slot].oldest = s->inflight.empty() ? seq : std::min(seq, s->inflight.begin()->first);
+  cudaError_t e = fault_hit(kFaultSubmitPublish)
+                      ? cudaErrorUnknown
+                      : cudaMemcpyAsync(s->ring + slot, &d, sizeof(ReqDesc), cudaMemcpyHostToDevice, s->cstream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&s->ctl->tiles_published, &s->pub_stage[slot], sizeof(unsigned long long),
-                        cudaMemcpyHostToDevice, s->cstream);
+    e = cudaMemcpyAsync(&s->ctl->tiles_published, &s->pub_stage[slot], sizeof(PubStage), cudaMemcpyHostToDevice,
+                        s->cstream);
   if (e != cudaSuccess) {
     slab_free(s, off, total);
     return cuda_fail("frax_server_submit: publish", e);
@@ -606,6 +646,7 @@ frax_status frax_server_collect(frax_server_t s, int64_t request, float* const* 
     cudaError_t e = cudaMemcpyAsync(s->slab_h + r.out_begin, s->slab + r.out_begin, r.out_bytes,
                                     cudaMemcpyDeviceToHost, s->dstream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->dstream);
+    if (e == cudaSuccess && fault_hit(kFaultCollectCopy)) e = cudaErrorUnknown;
     if (e != cudaSuccess) st = cuda_fail("frax_server_collect: output copy", e);
     for (int k = 0; k < r.nout && st == FRAX_OK; ++k)
       if (outputs[k]) std::memcpy(outputs[k], s->slab_h + r.out_off[k], size_t(r.out_rows[k]) * r.B * 4);

@@ -190,10 +190,20 @@ def frax_crba(model: Model, q, M=None, LD=None, want_M=True, want_LD=False):
 
 
 def frax_aba(model: Model, q, qd, tau, qdd=None):
-    """qdd = M^-1 (tau - c - g) (Eq. 2) by the articulated-body algorithm."""
+    """qdd = M^-1 (tau - c - g) (Eq. 2): the articulated-body algorithm on
+    trees, a solve through the mass-matrix factor on 7-body chains."""
     B, ld = _prep(model, q, qd=(qd, model.nv), tau=(tau, model.nv), qdd=(qdd, model.nv))
     qdd = _out(model.nv, q, ld, B) if qdd is None else qdd
     _check(lib().frax_aba(model.handle, B, ld, _p(q), _p(qd), _p(tau), _p(qdd), _stream(q)))
+    return qdd
+
+
+def frax_aba_articulated(model: Model, q, qd, tau, qdd=None):
+    """qdd (Eq. 2) always by the O(n) articulated-body sweeps (for 7-body
+    chains frax_aba solves through the mass-matrix factor instead)."""
+    B, ld = _prep(model, q, qd=(qd, model.nv), tau=(tau, model.nv), qdd=(qdd, model.nv))
+    qdd = _out(model.nv, q, ld, B) if qdd is None else qdd
+    _check(lib().frax_aba_articulated(model.handle, B, ld, _p(q), _p(qd), _p(tau), _p(qdd), _stream(q)))
     return qdd
 
 
@@ -354,6 +364,17 @@ def frax_serve_batch_noalloc(requests):
         stream = stream or _stream(inputs[0])
     _check(lib().frax_serve_batch_noalloc(ctypes.cast(arr, ctypes.c_void_p), n,
                                           stream if stream is not None else ctypes.c_void_p(0)))
+
+
+def frax_fp32_probe(packed: bool, blocks: int, iters: int, sink) -> float:
+    """Launches the FP32 peak probe (independent FMA chains; packed = the
+    two-lane form) on sink's stream; returns the FP32 operations it performs."""
+    if sink.dtype != torch.float32 or not sink.is_cuda or sink.numel() < blocks * 256:
+        raise FraxError(1, "frax_fp32_probe: sink must be a CUDA float32 tensor of blocks * 256 elements")
+    flops = ctypes.c_double()
+    _check(lib().frax_fp32_probe(int(bool(packed)), int(blocks), int(iters), ctypes.c_void_p(sink.data_ptr()),
+                                 ctypes.byref(flops), _stream(sink)))
+    return flops.value
 
 
 # ------------------------------------------------------------- autograd wrappers

@@ -88,7 +88,9 @@ class Server:
 
     def replay(self, trace, arrival_us, keep_outputs=False, timeout_ms=120000.0):
         """Replays [(model_id, op, inputs)] with arrival times (us from now)
-        natively; returns (latency_us array, outputs or None)."""
+        natively; returns (latency_us array, outputs or None). keep_outputs:
+        False (no outputs copied back), True (all), or a set of trace
+        positions whose outputs are copied back (None elsewhere)."""
         n = len(trace)
         mids = (ctypes.c_int * n)(*[t[0] for t in trace])
         ops = (ctypes.c_int * n)(*[OPS[t[1]] for t in trace])
@@ -105,6 +107,9 @@ class Server:
             outs = []
             outp = (ctypes.c_void_p * (3 * n))()
             for k, t in enumerate(trace):
+                if keep_outputs is not True and k not in keep_outputs:
+                    outs.append(None)
+                    continue
                 m = self.models[t[0]]
                 _, rows = op_rows(t[1], m.nq, m.nv)
                 o = [np.empty((r, Bs[k]), dtype=np.float32) for r in rows]

@@ -36,6 +36,13 @@ def test_cpu_baseline_child_and_reference_arm():
                         "0.5"], capture_output=True, text=True, cwd=ROOT, timeout=300)
     d = json.loads(r.stdout.strip().splitlines()[-1])
     assert d["kind"] == "oracle" and d["cores"] == 1 and d["value"] > 0
+    assert set(d["per_op"]) == set(bench.OPS)
+    # the aggregate is the six-op rate: 6 / sum of 1 / per-op rates
+    assert abs(d["value"] - 6 / sum(1 / v for v in d["per_op"].values())) < 1e-9 * d["value"]
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-baseline-child", "--cpu-robot",
+                        "humanoid", "--cpu-seconds", "0.5"], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert set(d["per_op"]) == set(bench.HUMANOID_OPS) and all(v > 0 for v in d["per_op"].values())
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0", "--cpu-seconds", "0.5"], capture_output=True, text=True, cwd=ROOT,
                        timeout=300)

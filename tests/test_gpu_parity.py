@@ -90,6 +90,40 @@ def test_aba(fxm, name):
     assert normwise(host(qdd), rbd.aba(m, s.q, s.qd, s.tau)) < _aba_tol(name)
 
 
+def test_chain7_config0_every_instance(fxm):
+    """The 7-revolute chain from model seed 0 with its batch of 1024 states
+    drawn from seed 1000 (q U[-pi, pi], qd U[-2, 2], qdd and tau U[-5, 5]):
+    FK, RNEA, CRBA and ABA on the GPU in FP32 against the FP64 oracle, every
+    instance and every element compared."""
+    m, h = MODELS["chain7"], fxm["chain7"]
+    B = 1024
+    s, d = states(m, B, 1000)
+    pose = fx.frax_fk(h, d["q"])
+    tau = fx.frax_rnea(h, d["q"], d["qd"], d["qdd"])
+    M, LD = fx.frax_crba(h, d["q"], want_M=True, want_LD=True)
+    qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+    qdd_sweep = fx.frax_aba_articulated(h, d["q"], d["qd"], d["tau"])
+    Mref = rbd.crba(m, s.q)
+    assert normwise(host(pose), rbd.fk_flat(m, s.q)) < TOL
+    assert normwise(host(tau), rbd.rnea(m, s.q, s.qd, s.qdd)) < TOL
+    assert normwise(host(M), Mref.reshape(B, -1)) < TOL
+    assert normwise(host(LD), rbd.pack_ltdl(*rbd.ltdl(Mref))) < TOL
+    qref = rbd.aba(m, s.q, s.qd, s.tau)
+    assert normwise(host(qdd), qref) < TOL
+    assert normwise(host(qdd_sweep), qref) < TOL
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_aba_articulated(fxm, name):
+    """frax_aba_articulated always runs the O(n) articulated-body sweeps (the
+    7-body chain's frax_aba solves through the mass-matrix factor instead)."""
+    m, h = MODELS[name], fxm[name]
+    B = 300
+    s, d = states(m, B, 32)
+    qdd = fx.frax_aba_articulated(h, d["q"], d["qd"], d["tau"])
+    assert normwise(host(qdd), rbd.aba(m, s.q, s.qd, s.tau)) < _aba_tol(name)
+
+
 @pytest.mark.parametrize("name", ["chain7", "humanoid", "tree101", "tree_big"])
 def test_rnea_vjp(fxm, name):
     m, h = MODELS[name], fxm[name]

@@ -230,3 +230,49 @@ def test_native_replay(server):
         for a, b in zip(o, alone):
             assert np.array_equal(a, b)
     assert srv.info()["in_flight"] == 0
+
+
+def test_long_mixed_replay_with_relaunches():
+    """20 000 mixed requests (four robots, four ops, 1-4096 instances
+    log-uniform) in four bursts separated by pauses longer than the idle
+    limit, so the persistent kernel both runs for long stretches and exits
+    and is relaunched between bursts. Every request completes, no device
+    error is recorded, and sampled results match the FP64 oracle."""
+    srv = Server(budget_bytes=1 << 30, idle_exit_ms=100.0)
+    ids = [srv.add_model(fx.Model.from_robot(r)) for r in ROBOTS]
+    rng = np.random.default_rng(77)
+    pool = {}  # a few input sets per (robot, op, size class), reused across the trace
+    trace, meta = [], []
+    n, bursts = 20000, 4
+    sizes = np.array([1, 2, 5, 13, 33, 90, 250, 700, 1900, 4096])
+    for j in range(n):
+        k = int(rng.integers(len(ROBOTS)))
+        op = ["rnea", "crba", "aba", "rnea_grad"][int(rng.integers(4))]
+        # log-uniform size, snapped to one of ten classes so a small pool of
+        # input sets serves the whole trace
+        Bj = int(sizes[np.abs(np.log(sizes) - rng.uniform(0, np.log(4096))).argmin()])
+        if ROBOTS[k].n_bodies >= 64:
+            Bj = min(Bj, 512)
+        key = (k, op, Bj, j % 2)
+        if key not in pool:
+            pool[key] = _inputs(ROBOTS[k], op, Bj, 9000 + len(pool))
+        trace.append((ids[k], op, pool[key][2]))
+        meta.append(key)
+    per = n // bursts
+    gaps = rng.exponential(1e6 / 20000.0, size=n)  # about 20 000 requests/s inside a burst
+    for b in range(1, bursts):
+        gaps[b * per] += 250e3  # 250 ms pauses: longer than idle_exit_ms
+    arrival = np.cumsum(gaps)
+    keep = set(int(x) for x in rng.choice(n, 24, replace=False))
+    lat, outs = srv.replay(trace, arrival, keep_outputs=keep, timeout_ms=300000.0)
+    info = srv.info()
+    assert info["device_status"] == 0
+    assert info["completed"] == n and info["in_flight"] == 0 and info["bytes_in_use"] == 0
+    assert info["kernel_launches"] >= bursts
+    assert np.all(np.isfinite(lat)) and np.all(lat > 0)
+    for j in sorted(keep):
+        k, op, Bj, _ = meta[j]
+        s_, g_, _ = pool[meta[j]]
+        for o, ref in zip(outs[j], _oracle(ROBOTS[k], op, s_, g_)):
+            assert normwise(gen.from_soa(o, Bj), ref) < _tol(ROBOTS[k], op)
+    srv.close()

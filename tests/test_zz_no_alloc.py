@@ -1,9 +1,10 @@
 """frax_serve_batch_noalloc, the allocation-free batch entry point, against
-the regular entry points (frax_rnea, frax_crba, frax_aba, frax_rnea_vjp) on
-the same inputs, within the parity tolerances, on two calls in a row. The
-entry point keeps its scratch in a fixed device array shared by all calls;
-the second call uses other inputs and another request order, so results
-left in that array by the first call would show up as mismatches.
+the regular entry points (frax_rnea, frax_crba, frax_aba, frax_rnea_vjp) and
+against the FP64 oracle on the same inputs, within the parity tolerances, on
+two calls in a row. The entry point keeps its scratch in a fixed device array
+shared by all calls; the second call uses other inputs and another request
+order, so results left in that array by the first call would show up as
+mismatches. A call made while its stream is being captured is refused.
 
 Kept in a file that pytest collects last, so a run that stops at the first
 failure has already run every other test."""
@@ -14,6 +15,8 @@ import torch
 
 import gen
 import paper_2604_04310_gb300 as fx
+from oracle import derivatives as dv
+from oracle import rbd
 from tests.gpu_util import dev, host
 from tests.pins import normwise
 
@@ -33,20 +36,25 @@ def _request(models, name, op, B, seed):
     if B == 0:  # an empty request rides along; there is nothing to compare
         nin, rows = {"rnea": (3, [m.nv]), "crba": (1, [m.nv * m.nv]), "aba": (3, [m.nv]),
                      "rnea_grad": (4, [m.nq, m.nv, m.nv])}[op]
-        return (m, op, [q, qd, qdd, gb][:nin], [e(r) for r in rows]), [], tol
+        return (m, op, [q, qd, qdd, gb][:nin], [e(r) for r in rows]), ([], []), tol
+    gq = g.astype(np.float32).astype(np.float64)
     if op == "rnea":
         ins, outs = [q, qd, qdd], [e(m.nv)]
         ref = [fx.frax_rnea(m, q, qd, qdd)]
+        oref = [rbd.rnea(robot, s.q, s.qd, s.qdd)]
     elif op == "crba":
         ins, outs = [q], [e(m.nv * m.nv)]
         ref = [fx.frax_crba(m, q)[0]]
+        oref = [rbd.crba(robot, s.q).reshape(B, -1)]
     elif op == "aba":
         ins, outs = [q, qd, tau], [e(m.nv)]
         ref = [fx.frax_aba(m, q, qd, tau)]
+        oref = [rbd.aba(robot, s.q, s.qd, s.tau)]
     else:
         ins, outs = [q, qd, qdd, gb], [e(m.nq), e(m.nv), e(m.nv)]
         ref = list(fx.frax_rnea_vjp(m, q, qd, qdd, gb))
-    return (m, op, ins, outs), ref, tol
+        oref = list(dv.rnea_vjp(robot, s.q, s.qd, s.qdd, gq))
+    return (m, op, ins, outs), (ref, oref), tol
 
 
 def _check(models, mix, seed0):
@@ -57,10 +65,13 @@ def _check(models, mix, seed0):
         refs.append((ref, tol, B))
     fx.frax_serve_batch_noalloc(reqs)
     torch.cuda.synchronize()
-    for (m, op, ins, outs), (ref, tol, B) in zip(reqs, refs):
-        for o, rf in zip(outs, ref):
-            if B:
-                assert normwise(host(o), host(rf)) < tol, (op, B)
+    for (m, op, ins, outs), ((ref, oref), tol, B) in zip(reqs, refs):
+        if not B:
+            continue
+        for o, rf in zip(outs, ref):  # the regular GPU entry points
+            assert normwise(host(o), host(rf)) < tol, (op, B)
+        for o, rf in zip(outs, oref):  # the FP64 oracle
+            assert normwise(host(o), rf) < tol, (op, B, "oracle")
 
 
 def test_noalloc_batch_matches_regular_entry_points():
@@ -82,3 +93,30 @@ def test_noalloc_batch_limits():
         fx.frax_serve_batch_noalloc(reqs)
     assert "256" in str(e.value)
     fx.frax_serve_batch_noalloc([])
+
+
+def test_noalloc_batch_refused_while_capturing():
+    """Under stream capture the call returns FRAX_EINVAL and enqueues nothing,
+    so the capture stays valid and ends as an empty graph."""
+    m = fx.Model.from_robot(ROBOTS["chain7"])
+    q = torch.zeros((7, 4), device="cuda")
+    out = torch.zeros((49, 4), device="cuda")
+    reqs = [(m, "crba", [q], [out])]
+    fx.frax_serve_batch_noalloc(reqs)  # the per-device set-up, before any capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        q2 = torch.zeros((7, 4), device="cuda")
+        out2 = torch.zeros((49, 4), device="cuda")
+    torch.cuda.synchronize()
+    refused = None
+    with torch.cuda.graph(g, stream=s):
+        try:
+            fx.frax_serve_batch_noalloc([(m, "crba", [q2], [out2])])
+        except fx.FraxError as e:
+            refused = e
+    assert refused is not None and refused.status == 1 and "captur" in str(refused)
+    torch.cuda.synchronize()
+    fx.frax_serve_batch_noalloc(reqs)  # still usable after the refusal
+    torch.cuda.synchronize()
