@@ -209,20 +209,25 @@ class Step:
     """The whole hot path over one resident batch; output buffers are
     allocated once (torch), the kernels write into them."""
 
-    def __init__(self, fx, model, robot, dev, device, ops, task=None):
+    def __init__(self, fx, model, robot, dev, device, ops, task=None, flat=False):
         import torch
         self.fx, self.m, self.d, self.ops = fx, model, dev, ops
         B = dev["q"].shape[1]
         nv, nb = model.nv, model.n_bodies
-        e = lambda k: torch.empty((k, B), dtype=torch.float32, device=device)
         self.frames = list(robot.end_frames)
-        self.out = {
-            "pose": e(12 * nb), "J": e(len(self.frames) * 6 * nv), "tau": e(nv), "M": e(nv * nv),
-            "LD": e(nv * (nv + 1) // 2), "qdd": e(nv), "rq": e(model.nq), "rqd": e(nv), "rqdd": e(nv),
-            "aq": e(model.nq), "aqd": e(nv), "at": e(nv),
-        }
+        rows = {"pose": 12 * nb, "J": len(self.frames) * 6 * nv, "tau": nv, "M": nv * nv,
+                "LD": nv * (nv + 1) // 2, "qdd": nv, "rq": model.nq, "rqd": nv, "rqdd": nv,
+                "aq": model.nq, "aqd": nv, "at": nv}
+        if flat:  # every output a [rows][B] view of one buffer (one copy brings them all back)
+            self.flat_out = torch.empty(sum(rows.values()) * B, dtype=torch.float32, device=device)
+            self.out, off = {}, 0
+            for k, r in rows.items():
+                self.out[k] = self.flat_out[off:off + r * B].view(r, B)
+                off += r * B
+        else:
+            self.out = {k: torch.empty((r, B), dtype=torch.float32, device=device) for k, r in rows.items()}
         if "fk_jvp" in ops:
-            self.out["dpose"] = e(6 * len(self.frames))
+            self.out["dpose"] = torch.empty((6 * len(self.frames), B), dtype=torch.float32, device=device)
         fx_, m, d, o = fx, model, dev, self.out
         table = {
             "fk_jac": lambda: fx_.frax_jacobian(m, d["q"], self.frames, pose=o["pose"], J=o["J"]),
@@ -602,9 +607,10 @@ def batch_sweep(fx, device, flush):
     calls captured once as a CUDA graph and replayed, CUDA events, L2 flushed
     between replays), the calls issued one by one (CUDA events between them),
     the host time to issue one public call (Python binding + C ABI + launch,
-    no synchronisation), and end to end through the public API (pinned inputs
-    copied in, the six calls, every output copied back, synchronised; host
-    clock). Medians over the repetitions."""
+    no synchronisation), and end to end through the public API (the inputs,
+    one pinned [rows][B] block, copied in with one copy; the six calls; the
+    outputs, views of one device buffer, copied back with one copy;
+    synchronised; host clock). Medians over the repetitions."""
     import torch
 
     import gen
@@ -616,8 +622,18 @@ def batch_sweep(fx, device, flush):
         model = fx.Model.from_robot(robot)
         rows = []
         for B in [b for b in SWEEP_B if b <= bmax]:
-            host, dev = make_inputs(robot, B, 4004, device)
-            step = Step(fx, model, robot, dev, device, ops)
+            host, dev0 = make_inputs(robot, B, 4004, device)
+            # inputs and outputs each one [rows][B] block: one copy in, one copy out
+            keys = list(host)
+            nrow = [host[k].shape[0] for k in keys]
+            hin = torch.cat([host[k] for k in keys]).pin_memory()
+            din = hin.to(device)
+            dev, r0 = {}, 0
+            for k, r in zip(keys, nrow):
+                dev[k] = din[r0:r0 + r]
+                r0 += r
+            del dev0
+            step = Step(fx, model, robot, dev, device, ops, flat=True)
             reps = 200 if B <= 4096 else (40 if B <= (1 << 16) else 12)
             g_ms, g_l, _, _, why = time_graph(step, reps, 3, flush, 1, None)
             e_ms, _, e_l, _, _ = time_step(step, reps, 3, flush, 1, None)
@@ -630,18 +646,20 @@ def batch_sweep(fx, device, flush):
                 host_us.append((time.perf_counter() - t0) * 1e6 / len(ops))
                 torch.cuda.synchronize()
             res["launches"] += reps * step.kernels
-            pin = {k: v.pin_memory() for k, v in host.items()}
-            keys = [k for n in ops for k in OUT_OF[n]]
-            outh = {k: torch.empty(step.out[k].shape, dtype=torch.float32).pin_memory() for k in keys}
+            # the outputs of the step's ops lie in one span of the flat buffer
+            outk = [k for n in ops for k in OUT_OF[n]]
+            spans = [(step.out[k].data_ptr() - step.flat_out.data_ptr()) // 4 for k in outk]
+            lo = min(spans)
+            hi = max(sp + step.out[k].numel() for sp, k in zip(spans, outk))
+            dspan = step.flat_out[lo:hi]
+            hout = torch.empty(hi - lo, dtype=torch.float32).pin_memory()
             e2e_us = []
             for _ in range(reps):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                for k in dev:
-                    dev[k].copy_(pin[k], non_blocking=True)
+                din.copy_(hin, non_blocking=True)
                 step.run()
-                for k in keys:
-                    outh[k].copy_(step.out[k], non_blocking=True)
+                hout.copy_(dspan, non_blocking=True)
                 torch.cuda.synchronize()
                 e2e_us.append((time.perf_counter() - t0) * 1e6)
             res["launches"] += reps * step.kernels
@@ -654,11 +672,44 @@ def batch_sweep(fx, device, flush):
                          "eager_us": e_ms * 1e3, "eager_evals_per_s": ev / (e_ms / 1e3),
                          "host_us_per_call": statistics.median(host_us),
                          "e2e_us": e2e, "e2e_evals_per_s": ev / (e2e / 1e6),
-                         "h2d_bytes": sum(v.numel() * 4 for v in pin.values()),
-                         "d2h_bytes": sum(v.numel() * 4 for v in outh.values())})
-            del step, dev, host, pin, outh
+                         "h2d_bytes": hin.numel() * 4, "d2h_bytes": hout.numel() * 4})
+            del step, dev, host, hin, din, hout, dspan
         res[name] = rows
     return res
+
+
+TREE_PATH_B = [64, 512, 4096, 1 << 15, 1 << 18]
+
+
+def tree_paths(fx, device, flush):
+    """The humanoid's RNEA, bias forces and ABA on both tree paths, one thread
+    per instance and four lanes per instance (lane groups), at batch sizes
+    from 64 to 2^18: each op captured alone as a CUDA graph and replayed
+    (kernel time only, CUDA events, L2 flushed between replays), median."""
+    import gen
+    robot = gen.humanoid(0)
+    model = fx.Model.from_robot(robot)
+    rows, launches = [], 0
+    try:
+        for B in TREE_PATH_B:
+            _, dev = make_inputs(robot, B, 4005, device)
+            reps = 100 if B <= 4096 else 30
+            for op in ("rnea", "bias", "aba"):
+                row = {"B": B, "op": op}
+                for path in ("thread", "lane_group"):
+                    model.set_tree_path(path)
+                    step = Step(fx, model, robot, dev, device, [op])
+                    ms, n, _, _, why = time_graph(step, reps, 3, flush, 1, None)
+                    launches += n or 0
+                    row[f"{path}_us"] = ms * 1e3 if ms is not None else None
+                    row[f"{path}_evals_per_s"] = B / (ms / 1e3) if ms is not None else None
+                    del step
+                rows.append(row)
+            del dev
+    finally:
+        model.set_tree_path("auto")
+    return {"workload": "humanoid (root + 29 revolute), RNEA / bias / ABA at each batch size on both tree paths",
+            "rows": rows, "launches": launches}
 
 
 def fp32_probe(fx, device, phys):
@@ -890,10 +941,12 @@ def frax_arm(args, rank, world, local_rank):
             nxt["fk_scan"][f"B{sB}"] = {"fk_us": sper["fk"] * 1e3, "fk_scan_us": sper["fk_scan"] * 1e3}
             del sstep, sdev
 
-    sweep = None
+    sweep = paths = None
     if not args.no_sweep:
         sweep = batch_sweep(fx, device, flush)
         launches += sweep.pop("launches")
+        paths = tree_paths(fx, device, flush)
+        launches += paths.pop("launches")
 
     # the FP32 rate a kernel of independent FMA chains attains: each ALU-bound
     # op's rate is also given as a fraction of it (scalar and packed)
@@ -932,7 +985,7 @@ def frax_arm(args, rank, world, local_rank):
                            "global_batch": B * world, "parallelism": f"replicas x{world}",
                            "l2": "256 MB buffer written between steps (L2 flush)", "launch": launch_mode},
                 "clocks": clk, "gpu_launches": launches, "wall_s": wall, "per_op": per_op, "roofline": roofline,
-                "e2e": e2e, "humanoid": humanoid, "next_rows": nxt, "batch_sweep": sweep,
+                "e2e": e2e, "humanoid": humanoid, "next_rows": nxt, "batch_sweep": sweep, "tree_paths": paths,
                 "fp32_peak_measured": probe, "cpu_baseline": cpu,
                 "cpu_baseline_all_cores": cpu_all, "serving": serve}
         print(json.dumps(line))

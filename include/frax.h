@@ -89,6 +89,20 @@ FRAX_API frax_status frax_model_dims(frax_model_t model, int* nq, int* nv, int* 
  * per instance, topology compiled in), 1 = general tree (thread per
  * instance, segment sweeps). */
 FRAX_API frax_status frax_model_kind(frax_model_t model, int* kind);
+/* How the kernels of a general tree of up to 32 bodies spread one instance
+ * over threads (the 7-body chain and larger trees always run one thread per
+ * instance). FRAX_TREE_PATH_THREAD: one thread per instance, the segment
+ * sweeps. FRAX_TREE_PATH_LANE_GROUP: four lanes of a warp per instance, each
+ * walking its own branches of the tree (Sec. III-A's parallelism within one
+ * instance), for the ops that have such kernels (frax_rnea, frax_aba,
+ * frax_aba_articulated); other ops run one thread per instance.
+ * FRAX_TREE_PATH_AUTO (the default): the lane groups for batches of up to
+ * 8192 instances, where one thread per instance leaves most of the GPU idle,
+ * one thread per instance above. Results agree within FP32 rounding (sums
+ * at a branch body are added in another order). FRAX_EINVAL for another
+ * value. Not thread-safe against concurrent calls on the same model. */
+enum { FRAX_TREE_PATH_AUTO = 0, FRAX_TREE_PATH_THREAD = 1, FRAX_TREE_PATH_LANE_GROUP = 2 };
+FRAX_API frax_status frax_model_set_tree_path(frax_model_t model, int path);
 
 /*
  * frax_fk — forward kinematics (Sec. II): ^0T_i(q) of every body.

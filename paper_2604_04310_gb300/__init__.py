@@ -8,13 +8,13 @@ frax_aba_jvp, plus the autograd wrappers RneaFn / AbaFn.
 
 from .frax import (AbaFn, FraxError, Model, RneaFn, aba, frax_aba, frax_aba_articulated, frax_aba_vjp, frax_crba, frax_fk,
                    frax_jacobian, frax_last_error, frax_ltdl_inverse, frax_ltdl_solve, frax_model_create, frax_osc, frax_rnea_ext, frax_aba_ext,
-                   frax_fk_jvp, frax_rnea_jvp, frax_aba_jvp, frax_fk_scan, frax_rnea, frax_rnea_vjp, frax_serve_batch_noalloc,
-                   frax_version, lib, rnea)
+                   frax_fk_jvp, frax_rnea_jvp, frax_aba_jvp, frax_fk_scan, frax_fp32_probe, frax_rnea, frax_rnea_vjp,
+                   frax_serve_batch_noalloc, frax_version, lib, rnea)
 
 __all__ = [
     "AbaFn", "FraxError", "Model", "RneaFn", "aba", "frax_aba", "frax_aba_articulated", "frax_aba_vjp", "frax_crba", "frax_fk",
     "frax_jacobian", "frax_last_error", "frax_ltdl_inverse", "frax_ltdl_solve", "frax_model_create", "frax_osc", "frax_rnea_ext", "frax_aba_ext",
     "frax_fk_jvp", "frax_rnea_jvp", "frax_aba_jvp", "frax_fk_scan", "frax_rnea", "frax_rnea_vjp",
-    "frax_serve_batch_noalloc", "frax_version",
+    "frax_fp32_probe", "frax_serve_batch_noalloc", "frax_version",
     "lib", "rnea",
 ]

@@ -23,6 +23,7 @@ SIGNATURES = {
     "frax_model_destroy": (c_int, [c_vp]),
     "frax_model_dims": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "frax_model_kind": (c_int, [c_vp, ctypes.POINTER(c_int)]),
+    "frax_model_set_tree_path": (c_int, [c_vp, c_int]),
     "frax_fk": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp]),
     "frax_jacobian": (c_int, [c_vp, c_i64, c_i64, c_vp, c_int, c_i32, c_vp, c_vp, c_vp]),
     "frax_rnea": (c_int, [c_vp, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),

@@ -64,8 +64,15 @@ frax_status need(const void* p, const char* fn, const char* name) {
   return FRAX_OK;
 }
 
-frax_status dispatch(frax_model_t model, frax::Op op, const frax::OpArgs& a, const char* fn) {
+// Batches up to this size run the lane-group kernels (several lanes per
+// instance) where a tree has them; larger ones one thread per instance.
+constexpr int64_t kLaneGroupMaxBatch = 8192;
+
+frax_status dispatch(frax_model_t model, frax::Op op, const frax::OpArgs& args, const char* fn) {
   const frax::HostModel& m = model->m;
+  frax::OpArgs a = args;
+  a.lane_group = model->tree_path == FRAX_TREE_PATH_LANE_GROUP ||
+                 (model->tree_path == FRAX_TREE_PATH_AUTO && a.B <= kLaneGroupMaxBatch);
   cudaError_t e;
   if (m.kind == frax::kKindChain)
     e = frax::launch_chain7(m, op, a);
@@ -155,6 +162,14 @@ frax_status frax_model_dims(frax_model_t model, int* nq, int* nv, int* n_bodies)
   if (nq) *nq = model->m.nq;
   if (nv) *nv = model->m.nv;
   if (n_bodies) *n_bodies = model->m.nb;
+  return ok();
+}
+
+frax_status frax_model_set_tree_path(frax_model_t model, int path) {
+  if (!model) return fail(FRAX_EINVAL, "frax_model_set_tree_path: model is NULL");
+  if (path < FRAX_TREE_PATH_AUTO || path > FRAX_TREE_PATH_LANE_GROUP)
+    return fail(FRAX_EINVAL, "frax_model_set_tree_path: unknown path");
+  model->tree_path = path;
   return ok();
 }
 

@@ -14,6 +14,7 @@ struct frax_model_s {
   // Trees: the structural zeros the CRBA kernel writes, per requested output
   // (index 1: M only, 2: the factor only, 3: both), listed once at creation.
   std::unique_ptr<frax::ZeroRows> crba_zeros[4];
+  int tree_path = 0;  // FRAX_TREE_PATH_*: how tree kernels spread an instance over threads
 };
 
 namespace frax {

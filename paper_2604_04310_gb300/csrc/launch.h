@@ -45,6 +45,7 @@ struct OpArgs {
   float* out2 = nullptr;  // qddbar / taubar
   FramesArg frames{0, {0}};  // kOpOsc: body[0] is the task body
   const ZeroRows* zeros = nullptr;  // kOpCrba on trees: structural zeros the kernel writes
+  bool lane_group = false;  // trees of up to 32 bodies: the lane-group kernels where they exist
   cudaStream_t stream = nullptr;
 };
 

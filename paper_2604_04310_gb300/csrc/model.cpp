@@ -4,6 +4,7 @@
 #include <memory>
 #include <type_traits>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -83,6 +84,92 @@ std::string fmt(const char* f, int i) {
   char buf[256];
   std::snprintf(buf, sizeof(buf), f, i);
   return buf;
+}
+
+// The lane-group schedule of LanePlan: heavy paths (each body continues
+// into its child with the deepest subtree), list-scheduled onto kLgLanes
+// lanes in order of the step at which each path can start (one step after
+// its head's parent), longest path first on ties; then the flags and slots
+// that carry state across lanes.
+void build_lane_plan(HostModel* mp) {
+  HostModel& m = *mp;
+  LanePlan& P = m.lane_plan;
+  P = LanePlan{};
+  const int n = m.nb;
+  std::vector<std::vector<int>> kids(n);
+  for (int i = 0; i < n; ++i)
+    if (m.parent[i] >= 0) kids[m.parent[i]].push_back(i);
+  std::vector<int> height(n, 1), heavy(n, -1);  // bodies on the longest path down; its first child
+  for (int i = n - 1; i >= 0; --i)  // children come after their parents
+    for (int c : kids[i]) {
+      if (heavy[i] < 0 || height[c] > height[heavy[i]]) heavy[i] = c;
+      height[i] = std::max(height[i], 1 + height[c]);
+    }
+  std::vector<int> step(n, -1), lane(n, -1);
+  std::vector<int> lane_free(kLgLanes, 0);
+  // pending path heads with the step they can start at
+  std::vector<std::pair<int, int>> pend;
+  for (int i = 0; i < n; ++i)
+    if (m.parent[i] < 0) pend.push_back({0, i});
+  int T = 0;
+  while (!pend.empty()) {
+    size_t best = 0;
+    for (size_t k = 1; k < pend.size(); ++k) {
+      const auto& a = pend[k];
+      const auto& b = pend[best];
+      if (a.first < b.first || (a.first == b.first && height[a.second] > height[b.second])) best = k;
+    }
+    const int ready = pend[best].first, head = pend[best].second;
+    pend.erase(pend.begin() + static_cast<long>(best));
+    int l = 0;
+    for (int k = 1; k < kLgLanes; ++k)
+      if (std::max(lane_free[k], ready) < std::max(lane_free[l], ready)) l = k;
+    int t = std::max(lane_free[l], ready);
+    for (int i = head; i >= 0; i = heavy[i], ++t) {
+      step[i] = t;
+      lane[i] = l;
+      for (int c : kids[i])
+        if (c != heavy[i]) pend.push_back({t + 1, c});
+    }
+    lane_free[l] = t;
+    T = std::max(T, t);
+  }
+  if (T > kMaxBodies) return;  // cannot happen: at most one body per step and lane
+  P.T = T;
+  for (int t = 0; t < kMaxBodies; ++t)
+    for (int l = 0; l < kLgLanes; ++l) {
+      P.body[t][l] = -1;
+      P.flag[t][l] = 0;
+    }
+  for (int i = 0; i < kMaxBodies; ++i) P.oslot[i] = P.islot[i] = -1, P.rc_first[i] = P.rc_count[i] = 0;
+  for (int i = 0; i < n; ++i) P.body[step[i]][lane[i]] = static_cast<int8_t>(i);
+  auto at = [&](int t, int l) { return (t >= 0 && t < T) ? static_cast<int>(P.body[t][l]) : -1; };
+  // outward: a parent processed at the previous step on the same lane hands
+  // its state over in registers; any other parent stores it in a slot
+  for (int i = 0; i < n; ++i) {
+    const int p = m.parent[i];
+    if (p < 0 || at(step[i] - 1, lane[i]) == p) continue;
+    P.flag[step[i]][lane[i]] |= kLgLoad;
+    if (P.oslot[p] < 0) {
+      P.oslot[p] = static_cast<int8_t>(P.n_oslot++);
+      P.flag[step[p]][lane[p]] |= kLgStoreOut;
+    }
+  }
+  // inward (the table read backwards): the lane's carry is a child's when
+  // the next step on the lane is that child; other children are remote
+  int nrc = 0;
+  for (int i = 0; i < n; ++i) {
+    const int cnext = at(step[i] + 1, lane[i]);
+    if (cnext >= 0 && m.parent[cnext] == i) P.flag[step[i]][lane[i]] |= kLgCarry;
+    P.rc_first[i] = static_cast<int8_t>(nrc);
+    for (int c : kids[i]) {
+      if (c == cnext) continue;
+      P.rc_list[nrc++] = static_cast<int8_t>(c);
+      P.islot[c] = static_cast<int8_t>(P.n_islot++);
+      P.flag[step[c]][lane[c]] |= kLgStoreIn;
+    }
+    P.rc_count[i] = static_cast<int8_t>(nrc - P.rc_first[i]);
+  }
 }
 
 }  // namespace
@@ -335,6 +422,7 @@ std::string build_model(int n, const int32_t* parent, const int32_t* joint_type,
   // the segment's first: each such body is the only child of a revolute body
   for (int i = 0; i < n; ++i)
     if (m.pos_of[i] > 0 && !m.bodies[i].dh) return fmt("body %d: segment body without a Rot_x frame", i);
+  build_lane_plan(&m);
   auto packed = [&](auto* tag) {
     using Img = std::remove_pointer_t<decltype(tag)>;
     auto p = std::make_shared<Img>();

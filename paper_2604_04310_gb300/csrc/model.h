@@ -29,6 +29,7 @@ struct HostModel {
   std::vector<uint16_t> zero_LD;    // and of the packed factor (r (r + 1) / 2 + c)
   double gravity[3] = {0, 0, 0};
   std::vector<BodyImage> bodies;  // FP32 internal-frame image
+  LanePlan lane_plan{};            // lockstep lane schedule (model_image.h)
 
   template <int NB>
   void pack(ModelImage<NB>* img) const;

@@ -63,4 +63,30 @@ struct alignas(16) ModelImage {
   BodyImage body[NB];
 };
 
+// Lane-group schedule: one instance spread over kLgLanes lanes of a warp,
+// each lane walking its own root-to-leaf paths of the tree (a heavy-path
+// decomposition). An outward sweep runs steps t = 0 .. T-1, lane l handling
+// body[t][l] (or idling), all lanes in lockstep; an inward sweep runs the
+// same table backwards, so a parent always comes after its children. State
+// crosses lanes only where a path starts: the parent's outward state sits in
+// its outward slot, a path head's inward contribution in its inward slot.
+constexpr int kLgLanes = 4;
+enum LgFlag {
+  kLgLoad = 1,      // outward: the parent's state comes from its outward slot
+  kLgStoreOut = 2,  // outward: this body's state goes to its outward slot
+  kLgCarry = 4,     // inward: the lane's carried contribution is a child's
+  kLgStoreIn = 8,   // inward: this body's contribution goes to its inward slot
+};
+struct LanePlan {
+  int32_t T;                         // steps of one sweep (0: no plan)
+  int32_t n_oslot, n_islot;          // slots used
+  int8_t body[kMaxBodies][kLgLanes];  // body at (step, lane), -1 idle
+  uint8_t flag[kMaxBodies][kLgLanes];
+  int8_t oslot[kMaxBodies];          // per body: outward slot, -1 none
+  int8_t islot[kMaxBodies];          // per body: inward slot, -1 none
+  int8_t rc_first[kMaxBodies];       // per body: its children whose contributions
+  int8_t rc_count[kMaxBodies];       //   sit in inward slots, rc_list[first ..]
+  int8_t rc_list[kMaxBodies];
+};
+
 }  // namespace frax

@@ -75,6 +75,13 @@ class Model:
         _check(L.frax_model_kind(h, ctypes.byref(kind)))
         self.nq, self.nv, self.n_bodies, self.kind = nq.value, nv.value, nb.value, kind.value
 
+    TREE_PATHS = {"auto": 0, "thread": 1, "lane_group": 2}
+
+    def set_tree_path(self, path: str):
+        """'auto' (default), 'thread' (one thread per instance) or
+        'lane_group' (four lanes per instance) for trees of up to 32 bodies."""
+        _check(lib().frax_model_set_tree_path(self.handle, self.TREE_PATHS[path]))
+
     @classmethod
     def from_robot(cls, robot):
         """From any object with parent, joint_type, axis, placement, inertia,
@@ -98,21 +105,28 @@ def frax_model_create(parent, joint_type, axis, placement, inertia, gravity=(0.0
 
 # ----------------------------------------------------------------- marshalling
 
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(t):
-    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    """The current CUDA stream of t's device, as the ABI's void* (an int)."""
+    if _raw_stream is not None:
+        return _raw_stream(t.get_device())
+    return torch.cuda.current_stream(t.device).cuda_stream
 
 
 def _soa(t, rows, name, ld=None, B=None):
     if t is None:
         return None
-    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
+    if not isinstance(t, torch.Tensor) or t.dtype is not torch.float32 or not t.is_cuda:
         raise FraxError(1, f"{name} must be a float32 CUDA tensor")
-    if t.dim() != 2 or t.shape[0] != rows or (rows > 0 and t.shape[1] > 1 and t.stride(1) != 1):
+    shape, stride = t.shape, t.stride()
+    if len(shape) != 2 or shape[0] != rows or (rows > 0 and shape[1] > 1 and stride[1] != 1):
         raise FraxError(1, f"{name} must have shape ({rows}, B) with unit stride along B")
-    if ld is not None and rows > 1 and t.shape[1] > 0 and t.stride(0) != ld:
+    if ld is not None and rows > 1 and shape[1] > 0 and stride[0] != ld:
         raise FraxError(1, f"{name}: every tensor of one call must share the same leading dimension")
-    if B is not None and t.shape[1] != B:
-        raise FraxError(1, f"{name}: batch size {t.shape[1]} != {B}")
+    if B is not None and shape[1] != B:
+        raise FraxError(1, f"{name}: batch size {shape[1]} != {B}")
     return t
 
 
@@ -127,7 +141,7 @@ def _out(rows, like, ld, B):
 
 
 def _p(t):
-    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+    return t.data_ptr() if t is not None else None
 
 
 def _prep(model, q, **others):

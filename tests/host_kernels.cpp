@@ -24,6 +24,7 @@ static inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 #include "paper_2604_04310_gb300/csrc/osc.cuh"
 #include "paper_2604_04310_gb300/csrc/ext.cuh"
 #include "paper_2604_04310_gb300/csrc/jvp.cuh"
+#include "paper_2604_04310_gb300/csrc/lg.cuh"
 
 using namespace frax;
 
@@ -112,6 +113,81 @@ void run_all(const HostModel& hm, int B, int nf, const int* frames, const float*
   }
 }
 
+// The lane-group sweeps (lg.cuh) for trees of up to 32 bodies: the lanes of
+// one instance run one after another within each step, the dataflow of the
+// lockstep kernel; the plan's invariants are checked first.
+std::string check_plan(const HostModel& hm) {
+  const LanePlan& P = hm.lane_plan;
+  const int n = hm.nb;
+  std::vector<int> step(n, -1), lane(n, -1);
+  if (P.T < 1 || P.T > n) return "plan: bad step count";
+  for (int t = 0; t < P.T; ++t)
+    for (int l = 0; l < kLgLanes; ++l) {
+      const int i = P.body[t][l];
+      if (i < -1 || i >= n) return "plan: bad body";
+      if (i >= 0) {
+        if (step[i] >= 0) return "plan: body scheduled twice";
+        step[i] = t;
+        lane[i] = l;
+      }
+    }
+  for (int i = 0; i < n; ++i) {
+    if (step[i] < 0) return "plan: body not scheduled";
+    if (P.flag[step[i]][lane[i]] & kLgCarry) {  // the next step on the lane is a child
+      const int c = step[i] + 1 < P.T ? P.body[step[i] + 1][lane[i]] : -1;
+      if (c < 0 || hm.parent[c] != i) return "plan: carry without a child";
+    }
+    const int p = hm.parent[i];
+    if (p < 0) continue;
+    if (step[p] >= step[i]) return "plan: child before parent";
+    const bool reg = lane[p] == lane[i] && step[p] == step[i] - 1;
+    const int fl = P.flag[step[i]][lane[i]];
+    if (reg == bool(fl & kLgLoad)) return "plan: outward load flag";
+    if (!reg && (P.oslot[p] < 0 || !(P.flag[step[p]][lane[p]] & kLgStoreOut))) return "plan: missing outward slot";
+    if (reg == bool(fl & kLgStoreIn)) return "plan: inward store flag";
+    if (reg && !(P.flag[step[p]][lane[p]] & kLgCarry)) return "plan: carry flag";
+    bool listed = false;
+    for (int r = 0; r < P.rc_count[p]; ++r) listed = listed || P.rc_list[P.rc_first[p] + r] == i;
+    if (listed == reg) return "plan: remote child list";
+  }
+  return "";
+}
+
+template <bool FREE>
+void run_lane_groups(const HostModel& hm, int B, const float* q, const float* qd, const float* qdd,
+                     const float* tau, Out& o) {
+  ModelImage<32> img;
+  hm.pack(&img);
+  const LanePlan& P = hm.lane_plan;
+  auto& tau_r = o.add("rnea_lg", hm.nv, B);
+  auto& bias = o.add("bias_lg", hm.nv, B);
+  auto& qdd_a = o.add("aba_lg", hm.nv, B);
+  std::vector<float> sr(lg_rnea_floats(hm.nb, P.n_oslot, P.n_islot), 0.f);
+  std::vector<float> sa(lg_aba_floats(hm.nb, P.n_oslot, P.n_islot), 0.f);
+  for (int b = 0; b < B; ++b) {
+    const Col col{B, b};
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<RneaLg<FREE, Col>> L;
+      for (int l = 0; l < kLgLanes; ++l)
+        L.push_back(RneaLg<FREE, Col>{img, P, LgScratch{sr.data(), 1}, col, l, true, q, qd, pass ? nullptr : qdd,
+                                      pass ? bias.data() : tau_r.data()});
+      for (int t = 0; t < P.T; ++t)
+        for (auto& x : L) x.out_step(t);
+      for (int t = P.T - 1; t >= 0; --t)
+        for (auto& x : L) x.in_step(t);
+    }
+    std::vector<AbaLg<FREE, Col>> L;
+    for (int l = 0; l < kLgLanes; ++l)
+      L.push_back(AbaLg<FREE, Col>{img, P, LgScratch{sa.data(), 1}, col, l, true, q, qd, tau, qdd_a.data()});
+    for (int t = 0; t < P.T; ++t)
+      for (auto& x : L) x.vel_step(t);
+    for (int t = P.T - 1; t >= 0; --t)
+      for (auto& x : L) x.inward_step(t);
+    for (int t = 0; t < P.T; ++t)
+      for (auto& x : L) x.acc_step(t);
+  }
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
@@ -158,6 +234,14 @@ int main(int argc, char** argv) {
     else
       run_all<SegTopo<64, false>, 64>(hm, B, nf, frames.data(), q.data(), qd.data(), qdd.data(), tau.data(),
                                       gbar.data(), dq.data(), dqd.data(), dx.data(), fext.data(), o, false);
+    if (n <= 32) {
+      const std::string perr = check_plan(hm);
+      if (!perr.empty()) throw perr;
+      if (hm.free_root)
+        run_lane_groups<true>(hm, B, q.data(), qd.data(), qdd.data(), tau.data(), o);
+      else
+        run_lane_groups<false>(hm, B, q.data(), qd.data(), qdd.data(), tau.data(), o);
+    }
     FILE* g = std::fopen(argv[2], "wb");
     if (!g) throw std::string("cannot open output");
     const int32_t count = static_cast<int32_t>(o.arrays.size());

@@ -156,3 +156,13 @@ def test_fk_scan_requires_a_serial_chain():
     assert b"serial chain" in L.frax_last_error()
     ch = fx.Model.from_robot(gen.serial_chain(1, 64, free_root=True))
     assert L.frax_fk_scan(ch.handle, 0, 0, ctypes.c_void_p(0), ctypes.c_void_p(0), ctypes.c_void_p(0)) == 0
+
+
+def test_tree_path_setting_is_validated():
+    import gen
+    h = fx.Model.from_robot(gen.humanoid(0))
+    L = fx.lib()
+    assert L.frax_model_set_tree_path(h.handle, 2) == 0
+    assert L.frax_model_set_tree_path(h.handle, 3) == 1 and "unknown path" in L.frax_last_error().decode()
+    assert L.frax_model_set_tree_path(None, 0) == 1
+    h.set_tree_path("auto")

@@ -436,3 +436,51 @@ def test_chain_unrolled_kernels_edge_batches(fxm, B):
     Fb = F.reshape(B, 7, 6)
     assert normwise(host(v("te")), rbd.rnea(m, s.q, s.qd, s.qdd, fext=Fb)) < TOL
     assert normwise(host(v("ae")), rbd.aba(m, s.q, s.qd, s.tau, fext=Fb)) < TOL
+
+
+LG_MODELS = ["humanoid", "tree101", "tree117"]
+
+
+@pytest.mark.parametrize("name", LG_MODELS)
+@pytest.mark.parametrize("B", [1, 15, 16, 17, 300])
+def test_lane_group_paths(fxm, name, B):
+    """Trees of up to 32 bodies: the lane-group kernels (four lanes per
+    instance) against the oracle, forced on and off, on ragged batches
+    (16 instances per block)."""
+    m, h = MODELS[name], fxm[name]
+    s, d = states(m, B, 33)
+    try:
+        h.set_tree_path("lane_group")
+        tau = fx.frax_rnea(h, d["q"], d["qd"], d["qdd"])
+        bias = fx.frax_rnea(h, d["q"], d["qd"], None)
+        qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+        qdd2 = fx.frax_aba_articulated(h, d["q"], d["qd"], d["tau"])
+        h.set_tree_path("thread")
+        tau_t = fx.frax_rnea(h, d["q"], d["qd"], d["qdd"])
+        qdd_t = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+    finally:
+        h.set_tree_path("auto")
+    assert normwise(host(tau), rbd.rnea(m, s.q, s.qd, s.qdd)) < TOL
+    assert normwise(host(bias), rbd.rnea(m, s.q, s.qd, np.zeros_like(s.qd))) < TOL
+    qref = rbd.aba(m, s.q, s.qd, s.tau)
+    assert normwise(host(qdd), qref) < TOL_ABA_TREE
+    assert torch.equal(qdd, qdd2)
+    # the two paths agree to FP32 rounding of the branch sums
+    assert normwise(host(tau), host(tau_t)) < 1e-5
+    assert normwise(host(qdd), host(qdd_t)) < TOL_ABA_TREE
+
+
+def test_lane_group_auto_dispatch_and_padding(fxm):
+    """The default path picks the lane groups at small batches and one thread
+    per instance above 8192; ld > B padding columns are never written."""
+    m, h = MODELS["humanoid"], fxm["humanoid"]
+    for B in (4096, 8193):
+        ld = B + 5
+        s = gen.draw_states(m, B, 34).as_f32()
+        q, qd, tau = (dev(x, ld) for x in (s.q, s.qd, s.tau))
+        out = torch.full((m.nv, ld), 7.0, device="cuda")
+        fx.frax_aba(h, q, qd, tau, qdd=out[:, :B])
+        idx = np.arange(0, B, 97)
+        assert normwise(host(out[:, :B])[idx], rbd.aba(m, s.q[idx], s.qd[idx], s.tau[idx])) < TOL_ABA_TREE
+        assert torch.all(out[:, B:] == 7.0)
+    assert fx.lib().frax_model_set_tree_path(h.handle, 7) == 1  # FRAX_EINVAL

@@ -22,7 +22,8 @@ TOL = 1e-4
 TOL_TREE = 1e-3  # tree ABA and every derivative
 CUDA_INCLUDE = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
 
-MODELS = {"chain7": gen.chain7(0), "humanoid": gen.humanoid(0), "tree101": gen.random_tree(101)}
+MODELS = {"chain7": gen.chain7(0), "humanoid": gen.humanoid(0), "tree101": gen.random_tree(101),
+          "tree117": gen.random_tree(117), "star": gen.random_tree(3, 12)}
 
 
 @pytest.fixture(scope="module")
@@ -93,3 +94,7 @@ def test_host_compiled_kernels_match_the_oracle(harness, tmp_path, name):
     assert normwise(o["fk_jvp"], dv.fk_jvp(m, s.q, extra["dq"], frames).reshape(B, -1)) < TOL
     assert normwise(o["rnea_ext"], rbd.rnea(m, s.q, s.qd, s.qdd, fext=extra["F"])) < TOL
     assert normwise(o["aba_ext"], rbd.aba(m, s.q, s.qd, s.tau, fext=extra["F"])) < tol_aba
+    if m.n_bodies <= 32:  # the lane-group sweeps, lanes run one after another in each step
+        assert normwise(o["rnea_lg"], rbd.rnea(m, s.q, s.qd, s.qdd)) < TOL
+        assert normwise(o["bias_lg"], rbd.rnea(m, s.q, s.qd, np.zeros_like(s.qd))) < TOL
+        assert normwise(o["aba_lg"], rbd.aba(m, s.q, s.qd, s.tau)) < tol_aba
