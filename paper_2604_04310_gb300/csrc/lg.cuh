@@ -26,8 +26,18 @@ constexpr int kLgPlanBytes = (int(sizeof(LanePlan)) + 15) / 16 * 16;
 // factors of its outward step, velocity + acceleration slots, articulated
 // inertia + bias slots. RNEA: per body cos, sin and net force, velocity +
 // acceleration slots, force slots.
-inline int lg_aba_floats(int nb, int no, int ni) { return 14 * nb + 12 * no + 27 * ni; }
-inline int lg_rnea_floats(int nb, int no, int ni) { return 8 * nb + 12 * no + 6 * ni; }
+FD int lg_aba_floats(int nb, int no, int ni) { return 14 * nb + 12 * no + 27 * ni; }
+FD int lg_rnea_floats(int nb, int no, int ni) { return 8 * nb + 12 * no + 6 * ni; }
+
+// Column accessor of the lane-group kernels: inputs are read from the
+// block's staged copy in shared memory ([row][kLgInst], this instance's
+// column), outputs written to the caller's global arrays.
+struct LgCol {
+  int64_t ld, b;  // global output column
+  int inst;       // staged input column
+  FD float in(const float* __restrict__ p, int k) const { return p[k * kLgInst + inst]; }
+  FD void out(float* __restrict__ p, int k, float v) const { st_cs(p + k * ld + b, v); }
+};
 
 // One instance's scratch, field f at base[f * stride] (instance-major in
 // shared memory: stride = instances per block).
@@ -137,8 +147,10 @@ struct RneaLg {
 
 // ABA (Eq. 2, f = 0) for one lane: velocities outward, articulated inertias
 // inward (each body's outward-step factors kept in the scratch), then
-// accelerations outward.
-template <bool FREE, class C>
+// accelerations outward. rhs(i) / rhs.root() give the joint forces, out(i, x)
+// / out.root(a) take the accelerations. Without VEL: zero velocity and no
+// gravity, i.e. x = M^-1 rhs (the solve of the ABA adjoint).
+template <bool FREE, bool VEL, class C, class Rhs, class Out>
 struct AbaLg {
   using T = SegTopo<32, FREE>;
   const ModelImage<32>& M;
@@ -147,8 +159,9 @@ struct AbaLg {
   C col;
   int lane;
   bool valid;
-  const float *q, *qd, *tau;
-  float* qdd;
+  const float *q, *qd;
+  Rhs rhs;
+  Out out;
   SV v, a, pa, a0;  // carried from this lane's previous step; a0: the free root's acceleration
   AI Ia;
   V3 gam;           // free root: gravity in root coordinates
@@ -158,15 +171,22 @@ struct AbaLg {
   FD int P0() const { return 8 * M.nb; }
   FD int OS() const { return 14 * M.nb; }
   FD int IS() const { return 14 * M.nb + 12 * P.n_oslot; }
+  FD SV ag() const { return VEL ? gravity_acc(M.g) : szero(); }
 
+  // velocities (and each joint's cos, sin)
   FD void vel_step(int t) {
     const int i = P.body[t][lane];
     if (!valid || i < 0) return;
     const int fl = P.flag[t][lane];
     if (FREE && i == 0) {
-      const RootPose RP = root_pose(M, q, col);
-      gam = rotT(RP.E, gravity_acc(M.g).v);
-      v = load6(qd, 0, col);
+      if (VEL) {
+        const RootPose RP = root_pose(M, q, col);
+        gam = rotT(RP.E, ag().v);
+        v = load6(qd, 0, col);
+      } else {
+        gam = mk(0, 0, 0);
+        v = szero();
+      }
     } else {
       const BodyImage& bi = M.body[i];
       const int p = M.parent[i];
@@ -176,8 +196,10 @@ struct AbaLg {
       joint_sincos(col.in(q, iq_of<T>(i)) + bi.th0, &sn, &cs);
       S[CS() + i] = cs;
       S[SN() + i] = sn;
-      with_dh(bi.dh, [&](auto dh) { v = mot_in(bi, cs, sn, v, dh); });
-      v.w.z += col.in(qd, iv_of<T>(i));
+      if (VEL) {
+        with_dh(bi.dh, [&](auto dh) { v = mot_in(bi, cs, sn, v, dh); });
+        v.w.z += col.in(qd, iv_of<T>(i));
+      }
     }
     S.put6(V0() + 6 * i, v);
     if (fl & kLgStoreOut) S.put6(OS() + 12 * P.oslot[i], v);
@@ -190,7 +212,7 @@ struct AbaLg {
     const RBI Ib = rbi_of(bi);
     const SV vi = S.get6(V0() + 6 * i);
     AI IA = ai_of(Ib);
-    SV pA = crf(vi, rbi_mul(Ib, vi));
+    SV pA = VEL ? crf(vi, rbi_mul(Ib, vi)) : szero();
     if (fl & kLgCarry) {
       ai_add(IA, Ia);
       pA = pA + pa;
@@ -201,14 +223,13 @@ struct AbaLg {
       pA = pA + S.get6(f + 21);
     }
     if (FREE && i == 0) {
-      a0 = spd6_solve(IA, load6(tau, 0, col) - pA);
+      a0 = spd6_solve(IA, rhs.root() - pA);
       return;
     }
     const float cs = S[CS() + i], sn = S[SN() + i];
-    const SV cb = ez_velprod(vi, col.in(qd, iv_of<T>(i)));
     const SV U = ai_col_z(IA);
     const float dinv = rcp(U.w.z);
-    const float ud = (col.in(tau, iv_of<T>(i)) - pA.w.z) * dinv;
+    const float ud = (rhs(i) - pA.w.z) * dinv;
     SV Ud = dinv * U;
     Ud.w.z = 1.f;
     S[P0() + 6 * i] = Ud.w.x;
@@ -219,7 +240,8 @@ struct AbaLg {
     S[P0() + 6 * i + 5] = ud;
     Ia = IA;
     ai_rank1_sub_d(Ia, Ud, U);
-    pa = pA + ai_mul(Ia, cb) + ud * U;
+    if (VEL) pa = pA + ai_mul(Ia, ez_velprod(vi, col.in(qd, iv_of<T>(i)))) + ud * U;
+    else pa = pA + ud * U;  // children's bias contributions, no velocity products
     with_dh(bi.dh, [&](auto dh) {
       ai_out(bi, cs, sn, Ia, dh);
       pa = frc_out(bi, cs, sn, pa, dh);
@@ -236,24 +258,186 @@ struct AbaLg {
     const int fl = P.flag[t][lane];
     if (FREE && i == 0) {
       a = a0;
-      store6(qdd, 0, col, a0 - SV{mk(0, 0, 0), gam});
+      out.root(a0 - SV{mk(0, 0, 0), gam});
     } else {
       const BodyImage& bi = M.body[i];
       const int p = M.parent[i];
-      if (p < 0) a = gravity_acc(M.g);
+      if (p < 0) a = ag();
       else if (fl & kLgLoad) a = S.get6(OS() + 12 * P.oslot[p] + 6);
       const float cs = S[CS() + i], sn = S[SN() + i];
-      const SV cb = ez_velprod(S.get6(V0() + 6 * i), col.in(qd, iv_of<T>(i)));
+      const SV cb = VEL ? ez_velprod(S.get6(V0() + 6 * i), col.in(qd, iv_of<T>(i))) : szero();
       with_dh(bi.dh, [&](auto dh) { a = mot_in(bi, cs, sn, a, dh) + cb; });
       const int f = P0() + 6 * i;
       const float x = S[f + 5] - (fmaf(S[f], a.w.x, fmaf(S[f + 1], a.w.y, a.w.z)) +
                                   fmaf(S[f + 2], a.v.x, fmaf(S[f + 3], a.v.y, S[f + 4] * a.v.z)));
       a.w.z += x;
-      col.out(qdd, iv_of<T>(i), x);
+      out(i, x);
     }
     if (fl & kLgStoreOut) S.put6(OS() + 12 * P.oslot[i] + 6, a);
   }
 };
+
+// A per-dof vector in the scratch (the ABA adjoint's w), optionally copied
+// to a global array too.
+template <class T>
+struct LgVec {
+  LgScratch S;
+  int f0;
+  FD float operator()(int i) const { return S[f0 + iv_of<T>(i)]; }
+  FD SV root() const { return S.get6(f0); }
+};
+template <class T, class C>
+struct OutToLgVec {
+  LgScratch S;
+  int f0;
+  float* also;  // global copy or nullptr
+  C col;
+  FD void operator()(int i, float x) const {
+    S[f0 + iv_of<T>(i)] = x;
+    if (also) col.out(also, iv_of<T>(i), x);
+  }
+  FD void root(const SV& x) const {
+    S.put6(f0, x);
+    if (also) store6(also, 0, col, x);
+  }
+};
+
+// The RNEA adjoint (reverse mode of Eq. 1) for one lane: the forward state
+// and the seed's propagation outward (each body's v, a and Fb kept in the
+// scratch), then the adjoint sweep inward. gb(i) / gb.root() seed it, sink
+// takes (qbar, qdbar, qddbar) per body. The arithmetic is rnea_vjp_seg's.
+template <bool FREE, class C, class Seed, class Sink>
+struct RneaVjpLg {
+  using T = SegTopo<32, FREE>;
+  const ModelImage<32>& M;
+  const LanePlan& P;
+  LgScratch S;
+  C col;
+  int lane;
+  bool valid;
+  const float *q, *qd, *qdd;
+  Seed gb;
+  Sink sink;
+  SV v, a, Fb;      // outward carry
+  SV Fc, abc, vbc;  // inward carry (contributions to the parent, in its frame)
+  V3 gam;
+  FD int CS() const { return 0; }
+  FD int SN() const { return M.nb; }
+  FD int V0() const { return 2 * M.nb; }
+  FD int A0() const { return 8 * M.nb; }
+  FD int B0() const { return 14 * M.nb; }
+  FD int OS() const { return 20 * M.nb; }
+  FD int IS() const { return 20 * M.nb + 18 * P.n_oslot; }
+
+  FD void out_step(int t) {
+    const int i = P.body[t][lane];
+    if (!valid || i < 0) return;
+    const int fl = P.flag[t][lane];
+    const SV ag = gravity_acc(M.g);
+    if (FREE && i == 0) {
+      const RootPose RP = root_pose(M, q, col);
+      gam = rotT(RP.E, ag.v);
+      v = load6(qd, 0, col);
+      a = SV{mk(0, 0, 0), gam} + load6(qdd, 0, col);
+      Fb = gb.root();
+    } else {
+      const BodyImage& bi = M.body[i];
+      const int p = M.parent[i];
+      if (p < 0) {
+        v = szero();
+        a = ag;
+        Fb = szero();
+      } else if (fl & kLgLoad) {
+        const int f = OS() + 18 * P.oslot[p];
+        v = S.get6(f);
+        a = S.get6(f + 6);
+        Fb = S.get6(f + 12);
+      }
+      float sn, cs;
+      joint_sincos(col.in(q, iq_of<T>(i)) + bi.th0, &sn, &cs);
+      S[CS() + i] = cs;
+      S[SN() + i] = sn;
+      const float qdi = col.in(qd, iv_of<T>(i));
+      with_dh(bi.dh, [&](auto dh) {
+        v = mot_in(bi, cs, sn, v, dh);
+        a = mot_in(bi, cs, sn, a, dh);
+        Fb = mot_in(bi, cs, sn, Fb, dh);
+      });
+      v.w.z += qdi;
+      a.w.z += col.in(qdd, iv_of<T>(i));
+      a = a + ez_velprod(v, qdi);
+      Fb.w.z += gb(i);
+    }
+    S.put6(V0() + 6 * i, v);
+    S.put6(A0() + 6 * i, a);
+    S.put6(B0() + 6 * i, Fb);
+    if (fl & kLgStoreOut) {
+      const int f = OS() + 18 * P.oslot[i];
+      S.put6(f, v);
+      S.put6(f + 6, a);
+      S.put6(f + 12, Fb);
+    }
+  }
+  FD void in_step(int t) {
+    const int i = P.body[t][lane];
+    if (!valid || i < 0) return;
+    const int fl = P.flag[t][lane];
+    SV Fs = szero(), abs_ = szero(), vbs = szero();  // children's contributions, this body's frame
+    if (fl & kLgCarry) {
+      Fs = Fc;
+      abs_ = abc;
+      vbs = vbc;
+    }
+    for (int r = 0; r < P.rc_count[i]; ++r) {
+      const int f = IS() + 18 * P.islot[P.rc_list[P.rc_first[i] + r]];
+      Fs = Fs + S.get6(f);
+      abs_ = abs_ + S.get6(f + 6);
+      vbs = vbs + S.get6(f + 12);
+    }
+    const BodyImage& bi = M.body[i];
+    const RBI I = rbi_of(bi);
+    const SV vi = S.get6(V0() + 6 * i), ai = S.get6(A0() + 6 * i), Fbi = S.get6(B0() + 6 * i);
+    if (FREE && i == 0) {
+      const SV ab = rbi_mul_add(abs_, I, Fbi);
+      const SV vb = rbi_mul_sub(crf_sub(vbs, Fbi, rbi_mul(I, vi)), I, crm(vi, Fbi));
+      sink.root(cross(ab.v, gam), vb, ab);
+      return;
+    }
+    const float cs = S[CS() + i], sn = S[SN() + i];
+    const float qdi = col.in(qd, iv_of<T>(i));
+    SV xa = ai - ez_velprod(vi, qdi);
+    xa.w.z -= col.in(qdd, iv_of<T>(i));
+    const SV Iv = rbi_mul(I, vi);
+    const SV F = crf_add(rbi_mul_add(Fs, I, ai), vi, Iv);
+    const SV ab = rbi_mul_add(abs_, I, Fbi);
+    const SV vb = rbi_mul_sub(crf_sub(vbs, Fbi, Iv), I, crm(vi, Fbi)) + qdi * ez_crf(ab);
+    const SV ef = ez_crf(F), ea = ez_crm(xa), ev = ez_crm(vi);
+    const float q1 = fmaf(Fbi.w.x, ef.w.x, fmaf(Fbi.w.y, ef.w.y, fmaf(Fbi.v.x, ef.v.x, Fbi.v.y * ef.v.y)));
+    const float q2 = fmaf(ab.w.x, ea.w.x, fmaf(ab.w.y, ea.w.y, fmaf(ab.v.x, ea.v.x, ab.v.y * ea.v.y)));
+    const float q3 = fmaf(vb.w.x, ev.w.x, fmaf(vb.w.y, ev.w.y, fmaf(vb.v.x, ev.v.x, vb.v.y * ev.v.y)));
+    const float qdb =
+        fmaf(-ab.w.x, ev.w.x, fmaf(-ab.w.y, ev.w.y, fmaf(-ab.v.x, ev.v.x, fmaf(-ab.v.y, ev.v.y, vb.w.z))));
+    sink(i, q1 - q2 - q3, qdb, ab.w.z);
+    with_dh(bi.dh, [&](auto dh) {
+      Fc = frc_out(bi, cs, sn, F, dh);
+      abc = frc_out(bi, cs, sn, ab, dh);
+      vbc = frc_out(bi, cs, sn, vb, dh);
+    });
+    if (fl & kLgStoreIn) {
+      const int f = IS() + 18 * P.islot[i];
+      S.put6(f, Fc);
+      S.put6(f + 6, abc);
+      S.put6(f + 12, vbc);
+    }
+  }
+};
+
+// Scratch floats of the adjoint sweep and of the ABA adjoint (its solve's
+// sweep, w, then the adjoint sweep over a second region).
+FD int lg_vjp_floats(int nb, int no, int ni) { return 20 * nb + 18 * no + 18 * ni; }
+FD int lg_aba_vjp_floats(int nb, int nv, int no, int ni) {
+  return lg_aba_floats(nb, no, ni) + nv + lg_vjp_floats(nb, no, ni);
+}
 
 #ifdef __CUDACC__
 // Stages the model image and the plan in shared memory (body constants are
@@ -268,7 +452,23 @@ __device__ __forceinline__ void lg_stage(const ModelImage<32>& Mg, const LanePla
   __syncthreads();
 }
 
-#define FRAX_LG_PROLOGUE()                                                                    \
+// Copies rows [0, rows) of this block's kLgInst instances of a global SoA
+// array into shared memory as [row][kLgInst] (consecutive threads read
+// consecutive instances: coalesced), zeros past the batch's end; returns the
+// next free float of the staging area.
+__device__ __forceinline__ float* lg_stage_rows(const float* __restrict__ src, int rows, int64_t ld, int64_t B,
+                                                float* dst) {
+  const int64_t b0 = int64_t(blockIdx.x) * kLgInst;
+  for (int k = threadIdx.x; k < rows * kLgInst; k += kLgBlock) {
+    const int r = k / kLgInst, j = k % kLgInst;
+    dst[k] = b0 + j < B ? __ldg(src + r * ld + b0 + j) : 0.f;
+  }
+  return dst + rows * kLgInst;
+}
+
+// Staged inputs first (fixed per kernel: `nin` arrays with their row counts),
+// then the per-instance scratch.
+#define FRAX_LG_PROLOGUE(NIN_FLOATS)                                                          \
   extern __shared__ __align__(16) char smem[];                                                \
   lg_stage(Mg, Pg, smem);                                                                     \
   const ModelImage<32>& M = *reinterpret_cast<const ModelImage<32>*>(smem);                   \
@@ -276,16 +476,22 @@ __device__ __forceinline__ void lg_stage(const ModelImage<32>& Mg, const LanePla
   const int lane = threadIdx.x % kLgLanes, inst = threadIdx.x / kLgLanes;                     \
   const int64_t b = int64_t(blockIdx.x) * kLgInst + inst;                                     \
   const bool valid = b < B;                                                                   \
-  const Col col{ld, valid ? b : 0};                                                           \
-  const LgScratch S{reinterpret_cast<float*>(smem + kLgImgBytes + kLgPlanBytes) + inst, kLgInst};
+  const LgCol col{ld, valid ? b : 0, inst};                                                   \
+  float* const stage = reinterpret_cast<float*>(smem + kLgImgBytes + kLgPlanBytes);           \
+  const LgScratch S{stage + (NIN_FLOATS) * kLgInst + inst, kLgInst};
 
 template <bool FREE>
 __global__ void __launch_bounds__(kLgBlock) k_rnea_lg(const __grid_constant__ ModelImage<32> Mg,
                                                       const __grid_constant__ LanePlan Pg, int64_t B, int64_t ld,
                                                       const float* __restrict__ q, const float* __restrict__ qd,
                                                       const float* __restrict__ qdd, float* __restrict__ tau) {
-  FRAX_LG_PROLOGUE();
-  RneaLg<FREE, Col> L{M, P, S, col, lane, valid, q, qd, qdd, tau};
+  FRAX_LG_PROLOGUE(M.nq + 2 * M.nv);
+  float* sq = stage;
+  float* sqd = lg_stage_rows(q, M.nq, ld, B, sq);
+  float* sqdd = lg_stage_rows(qd, M.nv, ld, B, sqd);
+  if (qdd) lg_stage_rows(qdd, M.nv, ld, B, sqdd);
+  __syncthreads();
+  RneaLg<FREE, LgCol> L{M, P, S, col, lane, valid, sq, sqd, qdd ? sqdd : nullptr, tau};
   for (int t = 0; t < P.T; ++t) {
     L.out_step(t);
     __syncwarp();
@@ -301,8 +507,15 @@ __global__ void __launch_bounds__(kLgBlock) k_aba_lg(const __grid_constant__ Mod
                                                      const __grid_constant__ LanePlan Pg, int64_t B, int64_t ld,
                                                      const float* __restrict__ q, const float* __restrict__ qd,
                                                      const float* __restrict__ tau, float* __restrict__ qdd) {
-  FRAX_LG_PROLOGUE();
-  AbaLg<FREE, Col> L{M, P, S, col, lane, valid, q, qd, tau, qdd};
+  FRAX_LG_PROLOGUE(M.nq + 2 * M.nv);
+  using T = SegTopo<32, FREE>;
+  float* sq = stage;
+  float* sqd = lg_stage_rows(q, M.nq, ld, B, sq);
+  float* stau = lg_stage_rows(qd, M.nv, ld, B, sqd);
+  lg_stage_rows(tau, M.nv, ld, B, stau);
+  __syncthreads();
+  AbaLg<FREE, true, LgCol, RhsFromGlobal<T, LgCol>, OutToGlobal<T, LgCol>> L{
+      M, P, S, col, lane, valid, sq, sqd, RhsFromGlobal<T, LgCol>{stau, col}, OutToGlobal<T, LgCol>{qdd, col}};
   for (int t = 0; t < P.T; ++t) {
     L.vel_step(t);
     __syncwarp();
@@ -313,6 +526,81 @@ __global__ void __launch_bounds__(kLgBlock) k_aba_lg(const __grid_constant__ Mod
   }
   for (int t = 0; t < P.T; ++t) {
     L.acc_step(t);
+    __syncwarp();
+  }
+}
+
+template <bool FREE>
+__global__ void __launch_bounds__(kLgBlock) k_rnea_vjp_lg(const __grid_constant__ ModelImage<32> Mg,
+                                                          const __grid_constant__ LanePlan Pg, int64_t B, int64_t ld,
+                                                          const float* __restrict__ q, const float* __restrict__ qd,
+                                                          const float* __restrict__ qdd, const float* __restrict__ gbar,
+                                                          float* qbar, float* qdbar, float* qddbar) {
+  FRAX_LG_PROLOGUE(M.nq + 3 * M.nv);
+  using T = SegTopo<32, FREE>;
+  float* sq = stage;
+  float* sqd = lg_stage_rows(q, M.nq, ld, B, sq);
+  float* sqdd = lg_stage_rows(qd, M.nv, ld, B, sqd);
+  float* sg = lg_stage_rows(qdd, M.nv, ld, B, sqdd);
+  lg_stage_rows(gbar, M.nv, ld, B, sg);
+  __syncthreads();
+  RneaVjpLg<FREE, LgCol, RhsFromGlobal<T, LgCol>, VjpToGlobal<T, LgCol>> L{
+      M, P, S, col, lane, valid, sq, sqd, sqdd, RhsFromGlobal<T, LgCol>{sg, col},
+      vjp_sink<T>(M, sq, qbar, qdbar, qddbar, 1.f, col)};
+  for (int t = 0; t < P.T; ++t) {
+    L.out_step(t);
+    __syncwarp();
+  }
+  for (int t = P.T - 1; t >= 0; --t) {
+    L.in_step(t);
+    __syncwarp();
+  }
+}
+
+// The ABA adjoint at qdd = ABA(q, qd, tau): w = M^-1 gbar by the
+// zero-velocity sweeps (into taubar when asked), then the RNEA adjoint
+// seeded with w, negated.
+template <bool FREE>
+__global__ void __launch_bounds__(kLgBlock) k_aba_vjp_lg(const __grid_constant__ ModelImage<32> Mg,
+                                                         const __grid_constant__ LanePlan Pg, int64_t B, int64_t ld,
+                                                         const float* __restrict__ q, const float* __restrict__ qd,
+                                                         const float* __restrict__ qdd, const float* __restrict__ gbar,
+                                                         float* qbar, float* qdbar, float* taubar) {
+  FRAX_LG_PROLOGUE(M.nq + 3 * M.nv);
+  using T = SegTopo<32, FREE>;
+  float* sq = stage;
+  float* sqd = lg_stage_rows(q, M.nq, ld, B, sq);
+  float* sqdd = lg_stage_rows(qd, M.nv, ld, B, sqd);
+  float* sg = lg_stage_rows(qdd, M.nv, ld, B, sqdd);
+  lg_stage_rows(gbar, M.nv, ld, B, sg);
+  __syncthreads();
+  const int W0 = lg_aba_floats(M.nb, P.n_oslot, P.n_islot);
+  const LgScratch S2{&S[W0 + M.nv], kLgInst};
+  {
+    AbaLg<FREE, false, LgCol, RhsFromGlobal<T, LgCol>, OutToLgVec<T, LgCol>> L{
+        M, P, S, col, lane, valid, sq, sqd, RhsFromGlobal<T, LgCol>{sg, col},
+        OutToLgVec<T, LgCol>{S, W0, taubar, col}};
+    for (int t = 0; t < P.T; ++t) {
+      L.vel_step(t);
+      __syncwarp();
+    }
+    for (int t = P.T - 1; t >= 0; --t) {
+      L.inward_step(t);
+      __syncwarp();
+    }
+    for (int t = 0; t < P.T; ++t) {
+      L.acc_step(t);
+      __syncwarp();
+    }
+  }
+  RneaVjpLg<FREE, LgCol, LgVec<T>, VjpToGlobal<T, LgCol>> L{
+      M, P, S2, col, lane, valid, sq, sqd, sqdd, LgVec<T>{S, W0}, vjp_sink<T>(M, sq, qbar, qdbar, nullptr, -1.f, col)};
+  for (int t = 0; t < P.T; ++t) {
+    L.out_step(t);
+    __syncwarp();
+  }
+  for (int t = P.T - 1; t >= 0; --t) {
+    L.in_step(t);
     __syncwarp();
   }
 }

@@ -155,15 +155,24 @@ std::string check_plan(const HostModel& hm) {
 
 template <bool FREE>
 void run_lane_groups(const HostModel& hm, int B, const float* q, const float* qd, const float* qdd,
-                     const float* tau, Out& o) {
+                     const float* tau, const float* gbar, Out& o) {
   ModelImage<32> img;
   hm.pack(&img);
   const LanePlan& P = hm.lane_plan;
   auto& tau_r = o.add("rnea_lg", hm.nv, B);
   auto& bias = o.add("bias_lg", hm.nv, B);
   auto& qdd_a = o.add("aba_lg", hm.nv, B);
+  auto& rq = o.add("rnea_vjp_lg_q", hm.nq, B);
+  auto& rqd = o.add("rnea_vjp_lg_qd", hm.nv, B);
+  auto& rqdd = o.add("rnea_vjp_lg_qdd", hm.nv, B);
+  auto& aq = o.add("aba_vjp_lg_q", hm.nq, B);
+  auto& aqd = o.add("aba_vjp_lg_qd", hm.nv, B);
+  auto& at = o.add("aba_vjp_lg_tau", hm.nv, B);
   std::vector<float> sr(lg_rnea_floats(hm.nb, P.n_oslot, P.n_islot), 0.f);
   std::vector<float> sa(lg_aba_floats(hm.nb, P.n_oslot, P.n_islot), 0.f);
+  std::vector<float> sv(lg_vjp_floats(hm.nb, P.n_oslot, P.n_islot), 0.f);
+  std::vector<float> sav(lg_aba_vjp_floats(hm.nb, hm.nv, P.n_oslot, P.n_islot), 0.f);
+  using T = SegTopo<32, FREE>;
   for (int b = 0; b < B; ++b) {
     const Col col{B, b};
     for (int pass = 0; pass < 2; ++pass) {
@@ -176,15 +185,50 @@ void run_lane_groups(const HostModel& hm, int B, const float* q, const float* qd
       for (int t = P.T - 1; t >= 0; --t)
         for (auto& x : L) x.in_step(t);
     }
-    std::vector<AbaLg<FREE, Col>> L;
+    using AbaL = AbaLg<FREE, true, Col, RhsFromGlobal<T, Col>, OutToGlobal<T, Col>>;
+    std::vector<AbaL> L;
     for (int l = 0; l < kLgLanes; ++l)
-      L.push_back(AbaLg<FREE, Col>{img, P, LgScratch{sa.data(), 1}, col, l, true, q, qd, tau, qdd_a.data()});
+      L.push_back(AbaL{img, P, LgScratch{sa.data(), 1}, col, l, true, q, qd, RhsFromGlobal<T, Col>{tau, col},
+                       OutToGlobal<T, Col>{qdd_a.data(), col}});
     for (int t = 0; t < P.T; ++t)
       for (auto& x : L) x.vel_step(t);
     for (int t = P.T - 1; t >= 0; --t)
       for (auto& x : L) x.inward_step(t);
     for (int t = 0; t < P.T; ++t)
       for (auto& x : L) x.acc_step(t);
+    // the RNEA adjoint
+    using VjpL = RneaVjpLg<FREE, Col, RhsFromGlobal<T, Col>, VjpToGlobal<T, Col>>;
+    std::vector<VjpL> V;
+    for (int l = 0; l < kLgLanes; ++l)
+      V.push_back(VjpL{img, P, LgScratch{sv.data(), 1}, col, l, true, q, qd, qdd, RhsFromGlobal<T, Col>{gbar, col},
+                       vjp_sink<T>(img, q, rq.data(), rqd.data(), rqdd.data(), 1.f, col)});
+    for (int t = 0; t < P.T; ++t)
+      for (auto& x : V) x.out_step(t);
+    for (int t = P.T - 1; t >= 0; --t)
+      for (auto& x : V) x.in_step(t);
+    // the ABA adjoint at this instance's own forward result, as the kernel is run
+    const int W0 = lg_aba_floats(hm.nb, P.n_oslot, P.n_islot);
+    const LgScratch S{sav.data(), 1};
+    using WL = AbaLg<FREE, false, Col, RhsFromGlobal<T, Col>, OutToLgVec<T, Col>>;
+    std::vector<WL> W;
+    for (int l = 0; l < kLgLanes; ++l)
+      W.push_back(WL{img, P, S, col, l, true, q, qd, RhsFromGlobal<T, Col>{gbar, col},
+                     OutToLgVec<T, Col>{S, W0, at.data(), col}});
+    for (int t = 0; t < P.T; ++t)
+      for (auto& x : W) x.vel_step(t);
+    for (int t = P.T - 1; t >= 0; --t)
+      for (auto& x : W) x.inward_step(t);
+    for (int t = 0; t < P.T; ++t)
+      for (auto& x : W) x.acc_step(t);
+    using AVL = RneaVjpLg<FREE, Col, LgVec<T>, VjpToGlobal<T, Col>>;
+    std::vector<AVL> A;
+    for (int l = 0; l < kLgLanes; ++l)
+      A.push_back(AVL{img, P, LgScratch{sav.data() + W0 + hm.nv, 1}, col, l, true, q, qd, qdd_a.data(),
+                      LgVec<T>{S, W0}, vjp_sink<T>(img, q, aq.data(), aqd.data(), nullptr, -1.f, col)});
+    for (int t = 0; t < P.T; ++t)
+      for (auto& x : A) x.out_step(t);
+    for (int t = P.T - 1; t >= 0; --t)
+      for (auto& x : A) x.in_step(t);
   }
 }
 
@@ -238,9 +282,9 @@ int main(int argc, char** argv) {
       const std::string perr = check_plan(hm);
       if (!perr.empty()) throw perr;
       if (hm.free_root)
-        run_lane_groups<true>(hm, B, q.data(), qd.data(), qdd.data(), tau.data(), o);
+        run_lane_groups<true>(hm, B, q.data(), qd.data(), qdd.data(), tau.data(), gbar.data(), o);
       else
-        run_lane_groups<false>(hm, B, q.data(), qd.data(), qdd.data(), tau.data(), o);
+        run_lane_groups<false>(hm, B, q.data(), qd.data(), qdd.data(), tau.data(), gbar.data(), o);
     }
     FILE* g = std::fopen(argv[2], "wb");
     if (!g) throw std::string("cannot open output");

@@ -470,6 +470,33 @@ def test_lane_group_paths(fxm, name, B):
     assert normwise(host(qdd), host(qdd_t)) < TOL_ABA_TREE
 
 
+@pytest.mark.parametrize("name", LG_MODELS)
+@pytest.mark.parametrize("B", [1, 17, 64])
+def test_lane_group_adjoints(fxm, name, B):
+    """The RNEA and ABA adjoints on the lane-group path against the oracle's
+    complex-step VJPs and against the one-thread path."""
+    m, h = MODELS[name], fxm[name]
+    s, d = states(m, B, 35)
+    g = gen.draw_gbar(m.nv, B, 36).astype(np.float32).astype(np.float64)
+    gb = dev(g)
+    try:
+        h.set_tree_path("lane_group")
+        qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
+        r_lg = fx.frax_rnea_vjp(h, d["q"], d["qd"], d["qdd"], gb)
+        a_lg = fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], qdd, gb)
+        h.set_tree_path("thread")
+        r_t = fx.frax_rnea_vjp(h, d["q"], d["qd"], d["qdd"], gb)
+        a_t = fx.frax_aba_vjp(h, d["q"], d["qd"], d["tau"], qdd, gb)
+    finally:
+        h.set_tree_path("auto")
+    for x, ref in zip(r_lg, dv.rnea_vjp(m, s.q, s.qd, s.qdd, g)):
+        assert normwise(host(x), ref) < TOL_GRAD
+    for x, ref in zip(a_lg, dv.aba_vjp(m, s.q, s.qd, s.tau, g)):
+        assert normwise(host(x), ref) < TOL_GRAD
+    for x, y in zip(r_lg + a_lg, r_t + a_t):
+        assert normwise(host(x), host(y)) < TOL_GRAD
+
+
 def test_lane_group_auto_dispatch_and_padding(fxm):
     """The default path picks the lane groups at small batches and one thread
     per instance above 8192; ld > B padding columns are never written."""

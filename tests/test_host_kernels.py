@@ -98,3 +98,9 @@ def test_host_compiled_kernels_match_the_oracle(harness, tmp_path, name):
         assert normwise(o["rnea_lg"], rbd.rnea(m, s.q, s.qd, s.qdd)) < TOL
         assert normwise(o["bias_lg"], rbd.rnea(m, s.q, s.qd, np.zeros_like(s.qd))) < TOL
         assert normwise(o["aba_lg"], rbd.aba(m, s.q, s.qd, s.tau)) < tol_aba
+        for got, ref in zip(("rnea_vjp_lg_q", "rnea_vjp_lg_qd", "rnea_vjp_lg_qdd"),
+                            dv.rnea_vjp(m, s.q, s.qd, s.qdd, extra["g"])):
+            assert normwise(o[got], ref) < TOL_TREE, got
+        for got, ref in zip(("aba_vjp_lg_q", "aba_vjp_lg_qd", "aba_vjp_lg_tau"),
+                            dv.aba_vjp(m, s.q, s.qd, s.tau, extra["g"])):
+            assert normwise(o[got], ref) < TOL_TREE, got
