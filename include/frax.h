@@ -95,12 +95,15 @@ FRAX_API frax_status frax_model_kind(frax_model_t model, int* kind);
  * sweeps. FRAX_TREE_PATH_LANE_GROUP: four lanes of a warp per instance, each
  * walking its own branches of the tree (Sec. III-A's parallelism within one
  * instance), for the ops that have such kernels (frax_rnea, frax_aba,
- * frax_aba_articulated); other ops run one thread per instance.
- * FRAX_TREE_PATH_AUTO (the default): the lane groups for batches of up to
- * 8192 instances, where one thread per instance leaves most of the GPU idle,
- * one thread per instance above. Results agree within FP32 rounding (sums
- * at a branch body are added in another order). FRAX_EINVAL for another
- * value. Not thread-safe against concurrent calls on the same model. */
+ * frax_aba_articulated, frax_rnea_vjp, frax_aba_vjp); other ops run one
+ * thread per instance.
+ * FRAX_TREE_PATH_AUTO (the default): the lane groups while the batch fits
+ * one resident wave of the op's lane-group kernel on the current device (a
+ * few thousand instances, fewer for ops with more state per instance), where
+ * one thread per instance would leave most of the GPU idle; one thread per
+ * instance above. Results agree within FP32 rounding (sums at a branch body
+ * are added in another order). FRAX_EINVAL for another value. Not
+ * thread-safe against concurrent calls on the same model. */
 enum { FRAX_TREE_PATH_AUTO = 0, FRAX_TREE_PATH_THREAD = 1, FRAX_TREE_PATH_LANE_GROUP = 2 };
 FRAX_API frax_status frax_model_set_tree_path(frax_model_t model, int path);
 

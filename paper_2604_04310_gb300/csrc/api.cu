@@ -64,15 +64,10 @@ frax_status need(const void* p, const char* fn, const char* name) {
   return FRAX_OK;
 }
 
-// Batches up to this size run the lane-group kernels (several lanes per
-// instance) where a tree has them; larger ones one thread per instance.
-constexpr int64_t kLaneGroupMaxBatch = 8192;
-
 frax_status dispatch(frax_model_t model, frax::Op op, const frax::OpArgs& args, const char* fn) {
   const frax::HostModel& m = model->m;
   frax::OpArgs a = args;
-  a.lane_group = model->tree_path == FRAX_TREE_PATH_LANE_GROUP ||
-                 (model->tree_path == FRAX_TREE_PATH_AUTO && a.B <= kLaneGroupMaxBatch);
+  a.tree_path = model->tree_path;
   cudaError_t e;
   if (m.kind == frax::kKindChain)
     e = frax::launch_chain7(m, op, a);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/frax.h"
 #include "model.h"
 
 namespace frax {
@@ -45,7 +46,7 @@ struct OpArgs {
   float* out2 = nullptr;  // qddbar / taubar
   FramesArg frames{0, {0}};  // kOpOsc: body[0] is the task body
   const ZeroRows* zeros = nullptr;  // kOpCrba on trees: structural zeros the kernel writes
-  bool lane_group = false;  // trees of up to 32 bodies: the lane-group kernels where they exist
+  int tree_path = 0;  // FRAX_TREE_PATH_*: trees of up to 32 bodies, the lane-group kernels or not
   cudaStream_t stream = nullptr;
 };
 

@@ -498,10 +498,11 @@ def test_lane_group_adjoints(fxm, name, B):
 
 
 def test_lane_group_auto_dispatch_and_padding(fxm):
-    """The default path picks the lane groups at small batches and one thread
-    per instance above 8192; ld > B padding columns are never written."""
+    """The default path picks the lane groups while the batch fits one resident
+    wave of the lane-group kernel (4096 here) and one thread per instance
+    beyond (2^17 + 1); ld > B padding columns are never written."""
     m, h = MODELS["humanoid"], fxm["humanoid"]
-    for B in (4096, 8193):
+    for B in (4096, (1 << 17) + 1):
         ld = B + 5
         s = gen.draw_states(m, B, 34).as_f32()
         q, qd, tau = (dev(x, ld) for x in (s.q, s.qd, s.tau))
