@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "ABA/RNEA evals/sec at 1 GB300 vs roofline; served p50/p99 latency at 1e-4 rel err"
 UNIT = "evals/s"
 OPS = ["fk_jac", "rnea", "crba_ltdl", "aba", "rnea_vjp", "aba_vjp"]
+HBM_OPS = ("fk_jac", "crba_ltdl")  # bound by their output writes; the other four by FP32 arithmetic
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -264,6 +265,23 @@ class Step:
                 events[name][1].record()
         return self.kernels
 
+    def run_split(self, side, side_ops):
+        """The same calls, those in side_ops issued on the stream `side`
+        (forked from and joined back into the current stream), the rest on
+        the current stream: independent ops overlap on the GPU."""
+        import torch
+        cur = torch.cuda.current_stream()
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            for name, fn in self.launches:
+                if name in side_ops:
+                    fn()
+        for name, fn in self.launches:
+            if name not in side_ops:
+                fn()
+        cur.wait_stream(side)
+        return self.kernels
+
 
 def time_step(step, steps, warmup, flush, world, dist, clocks=None):
     """Times `steps` passes of the step with CUDA events (per step and per
@@ -301,12 +319,14 @@ def time_step(step, steps, warmup, flush, world, dist, clocks=None):
     return step_ms, per_op_ms, launches, wall, clk
 
 
-def time_graph(step, steps, warmup, flush, world, dist, clocks=None):
+def time_graph(step, steps, warmup, flush, world, dist, clocks=None, side_ops=()):
     """The same step captured once as a CUDA graph (the same calls, the same
     kernels; replaying it trims the host's launch gaps between them) and
     replayed `steps` times, L2 flushed between replays outside the events.
-    Returns (median step ms, launches, wall, clocks, None), or five Nones but
-    the last, the reason, when the capture fails."""
+    With side_ops, those calls go on a second stream inside the capture (the
+    graph then runs them beside the others). Returns (median step ms,
+    launches, wall, clocks, None), or five Nones but the last, the reason,
+    when the capture fails."""
     import torch
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -316,9 +336,13 @@ def time_graph(step, steps, warmup, flush, world, dist, clocks=None):
     torch.cuda.current_stream().wait_stream(side)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
+    fork = torch.cuda.Stream()
     try:
         with torch.cuda.graph(g):
-            step.run()
+            if side_ops:
+                step.run_split(fork, set(side_ops))
+            else:
+                step.run()
     except Exception as e:  # noqa: BLE001 - reported in the bench line
         torch.cuda.synchronize()
         return None, None, None, None, str(e).splitlines()[0][:200]
@@ -847,11 +871,23 @@ def frax_arm(args, rank, world, local_rank):
     step_ms, per_op_ms, launches, wall, clk = time_step(step, args.steps, args.warmup, flush, world, dist,
                                                         clocks if args.eager else None)
     launch_mode = "eager: one public call per op"
+    graph_one_stream = None
     if not args.eager:
-        g_ms, g_launches, g_wall, g_clk, why = time_graph(step, args.steps, args.warmup, flush, world, dist, clocks)
+        # the step's calls as one CUDA graph; the memory-bound ops (FK+J, CRBA)
+        # on a second stream beside the ALU-bound ones unless --one-stream
+        side_ops = () if args.one_stream else HBM_OPS
+        g_ms, g_launches, g_wall, g_clk, why = time_graph(step, args.steps, args.warmup, flush, world, dist, clocks,
+                                                          side_ops)
         if g_ms is not None:
             step_ms, launches, wall, clk = g_ms, g_launches, g_wall, g_clk
-            launch_mode = "the step's public calls captured once as a CUDA graph and replayed"
+            launch_mode = "the step's public calls captured once as a CUDA graph and replayed" + (
+                "; FK+J and CRBA+LTDL (memory-bound) on a second stream beside the four ALU-bound ops"
+                if side_ops else "")
+            if side_ops:
+                o_ms, o_l, _, _, _ = time_graph(step, args.steps, args.warmup, flush, world, dist, None)
+                launches += o_l or 0
+                graph_one_stream = {"ms_per_step": o_ms, "evals_per_s": len(OPS) * B / (o_ms / 1e3)} \
+                    if o_ms is not None else None
         else:
             launch_mode += f" (graph capture failed: {why})"
     ms_per_step, value = whole_job(step_ms, len(OPS) * B, world, dist, device)
@@ -987,6 +1023,7 @@ def frax_arm(args, rank, world, local_rank):
                            "global_batch": B * world, "parallelism": f"replicas x{world}",
                            "l2": "256 MB buffer written between steps (L2 flush)", "launch": launch_mode},
                 "clocks": clk, "gpu_launches": launches, "wall_s": wall, "per_op": per_op, "roofline": roofline,
+                "graph_one_stream": graph_one_stream,
                 "e2e": e2e, "humanoid": humanoid, "next_rows": nxt, "batch_sweep": sweep, "tree_paths": paths,
                 "fp32_peak_measured": probe, "cpu_baseline": cpu,
                 "cpu_baseline_all_cores": cpu_all, "serving": serve}
@@ -1007,6 +1044,7 @@ def main():
     ap.add_argument("--no-next", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time the step as separate calls, not a CUDA graph")
+    ap.add_argument("--one-stream", action="store_true", help="capture every call of the step on one stream")
     ap.add_argument("--humanoid-batch", type=int, default=1 << 18)
     ap.add_argument("--count-flops", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -1,5 +1,4 @@
-// Serial chains of 7 revolute bodies: topology compiled in, registers only
-// (OSC runs the segment code on the same chain).
+// Serial chains of 7 revolute bodies: topology compiled in, registers only.
 #include "kernels.cuh"
 
 namespace frax {
@@ -130,6 +129,14 @@ __global__ void __launch_bounds__(kBlock) k_rnea_vjp_chain7(const __grid_constan
                     vjp_sink<T>(M, q, qbar, qdbar, qddbar, 1.f, col), col);
 }
 
+// 7-body chains: operational-space control with every sweep unrolled.
+__global__ void __launch_bounds__(kBlock) k_osc_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
+                                                        int64_t ld, int task, const float* q, const float* qd,
+                                                        const float* xdd, float* tau, float* Lam) {
+  FRAX_TID();
+  osc_chain<7>(M, task, q, qd, xdd, tau, Lam, col);
+}
+
 cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
   if (op == kOpAbaVjp && a.out2) {
     const ModelImage<8>& img8 = m.image<8>();
@@ -194,9 +201,10 @@ cudaError_t launch_chain7(const HostModel& m, Op op, const OpArgs& a) {
     return cudaGetLastError();
   }
   if (op == kOpOsc) {
-    // OSC: the segment code (rolled loops)
-    const ModelImage<8>& img8 = m.image<8>();
-    return launch_topo<SegTopo<8, false>>(img8, op, a);
+    const dim3 grid(unsigned((a.B + kBlock - 1) / kBlock));
+    k_osc_chain7<<<grid, kBlock, 0, a.stream>>>(m.image<8>(), a.B, a.ld, a.frames.body[0], a.q, a.qd, a.in_xdd,
+                                                a.out0, a.out1);
+    return cudaGetLastError();
   }
   return launch_topo<ChainTopo<7>>(m.image<7>(), op, a);
 }

@@ -164,6 +164,36 @@ struct OscPath {
   float E[9];  // world rotation of the task body's (internal) frame
 };
 
+// One step of sweep 2 through revolute body b (cos, sin of its joint), with
+// u = U / D of its articulated inertia: Omega, v, the velocity-product
+// acceleration and the world rotation of the path so far.
+template <class DH>
+FD void osc_path_step(const BodyImage& b, float cs, float sn, float qdj, const SV& U, float dinv, OscPath& o,
+                      DH dh) {
+  ai_in(b, cs, sn, o.Om, dh);
+  const SV u = dinv * U;
+  const SV y = ai_mul(o.Om, SV{u.v, u.w});  // W u as [linear; angular]
+  const float uWu = dot(u.w, y.v) + dot(u.v, y.w);
+  o.Om.B[2] -= y.w.x;
+  o.Om.B[5] -= y.w.y;
+  o.Om.B[8] -= y.w.z;
+  o.Om.C[4] -= y.v.x;
+  o.Om.C[5] -= y.v.y;
+  o.Om.C[2] += fmaf(-2.f, y.v.z, uWu + dinv);
+  o.v = mot_in(b, cs, sn, o.v, dh);
+  o.v.w.z += qdj;
+  o.a = mot_in(b, cs, sn, o.a, dh) + ez_velprod(o.v, qdj);
+  float ER[9];
+  mat_mul_b(o.E, b, ER, dh);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float x = ER[3 * r], z = ER[3 * r + 1];
+    o.E[3 * r] = fmaf(cs, x, sn * z);
+    o.E[3 * r + 1] = fmaf(-sn, x, cs * z);
+    o.E[3 * r + 2] = ER[3 * r + 2];
+  }
+}
+
 // Sweep 2: outward along the path to the task body.
 template <class T, class Img, class C, class PL>
 FD OscPath osc_path(const Img& M, const float* __restrict__ q, const float* __restrict__ qd, uint64_t path,
@@ -201,58 +231,22 @@ FD OscPath osc_path(const Img& M, const float* __restrict__ q, const float* __re
     const BodyImage& b = M.body[j];
     float sn, cs;
     joint_sincos(col.in(q, iq_of<T>(j)) + b.th0, &sn, &cs);
-    const float qdj = col.in(qd, iv_of<T>(j));
-    with_dh(b.dh, [&](auto dh) {
-      // W = X Omega_p X^T
-      ai_in(b, cs, sn, o.Om, dh);
-      // Omega = P W P^T + e_z e_z^T / D, P = 1 - e_z u^T, u = U / D
-      const float dinv = P.at(j, 6);
-      const SV u{dinv * mk(P.at(j, 0), P.at(j, 1), P.at(j, 2)), dinv * mk(P.at(j, 3), P.at(j, 4), P.at(j, 5))};
-      const SV y = ai_mul(o.Om, SV{u.v, u.w});  // W u as [linear; angular]
-      const float uWu = dot(u.w, y.v) + dot(u.v, y.w);
-      o.Om.B[2] -= y.w.x;
-      o.Om.B[5] -= y.w.y;
-      o.Om.B[8] -= y.w.z;
-      o.Om.C[4] -= y.v.x;
-      o.Om.C[5] -= y.v.y;
-      o.Om.C[2] += fmaf(-2.f, y.v.z, uWu + dinv);
-      // velocity and velocity-product acceleration
-      o.v = mot_in(b, cs, sn, o.v, dh);
-      o.v.w.z += qdj;
-      o.a = mot_in(b, cs, sn, o.a, dh) + ez_velprod(o.v, qdj);
-      // E <- E R Rot_z(q)
-      float ER[9];
-      mat_mul_b(o.E, b, ER, dh);
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float x = ER[3 * r], z = ER[3 * r + 1];
-        o.E[3 * r] = fmaf(cs, x, sn * z);
-        o.E[3 * r + 1] = fmaf(-sn, x, cs * z);
-        o.E[3 * r + 2] = ER[3 * r + 2];
-      }
-    });
+    const SV U{mk(P.at(j, 0), P.at(j, 1), P.at(j, 2)), mk(P.at(j, 3), P.at(j, 4), P.at(j, 5))};
+    with_dh(b.dh, [&](auto dh) { osc_path_step(b, cs, sn, col.in(qd, iv_of<T>(j)), U, P.at(j, 6), o, dh); });
   }
   return o;
 }
 
-// Whole controller for one instance. xdd: task acceleration [omega_dot;
-// p_ddot] of the task body's origin in world coordinates (6 rows); tau: nv
-// rows; Lam (optional): 36 rows, Lambda row-major in world-aligned
-// coordinates.
-template <class T, class Img, class C>
-FD void osc_seg(const Img& M, int task, const float* __restrict__ q, const float* __restrict__ qd,
-                const float* __restrict__ xdd, float* __restrict__ tau, float* __restrict__ Lam, const C& col) {
-  const uint64_t path = M.anc[task];
-  PathLocal<T::NBMAX> P;
-  const AI IA0 = osc_inertias<T>(M, q, path, P, col);
-  const OscPath o = osc_path<T>(M, q, qd, path, IA0, P, col);
+// Sweep 3: the task wrench f = Lambda r in task-body coordinates, with
+// r = E^T xdd - Jdot qd, and (optionally) Lambda written world-aligned.
+template <class C>
+FD SV osc_task_wrench(const OscPath& o, const float* __restrict__ xdd, float* __restrict__ Lam, const C& col) {
   // r = E^T xdd - Jdot qd in body coordinates; Jdot qd = [a_w; a_v + w x v]
   const SV xw = load6(xdd, 0, col);
   const V3 rw = rotT(o.E, xw.w) - o.a.w;
   const V3 rv = rotT(o.E, xw.v) - (o.a.v + cross(o.v.w, o.v.v));
   // f = Omega^-1 r; in the swapped halves the solution is [f_lin; f_ang]
   const SV fs = spd6_solve(o.Om, SV{rv, rw});
-  const SV f{fs.v, fs.w};
   if (Lam) {
     float A[6][6];
     ai_dense(o.Om, A);
@@ -281,7 +275,89 @@ FD void osc_seg(const Img& M, int task, const float* __restrict__ q, const float
                     fmaf(T1[3 * r], o.E[3 * c], fmaf(T1[3 * r + 1], o.E[3 * c + 1], T1[3 * r + 2] * o.E[3 * c + 2])));
       }
   }
+  return SV{fs.v, fs.w};
+}
+
+// Whole controller for one instance. xdd: task acceleration [omega_dot;
+// p_ddot] of the task body's origin in world coordinates (6 rows); tau: nv
+// rows; Lam (optional): 36 rows, Lambda row-major in world-aligned
+// coordinates.
+template <class T, class Img, class C>
+FD void osc_seg(const Img& M, int task, const float* __restrict__ q, const float* __restrict__ qd,
+                const float* __restrict__ xdd, float* __restrict__ tau, float* __restrict__ Lam, const C& col) {
+  const uint64_t path = M.anc[task];
+  PathLocal<T::NBMAX> P;
+  const AI IA0 = osc_inertias<T>(M, q, path, P, col);
+  const OscPath o = osc_path<T>(M, q, qd, path, IA0, P, col);
+  const SV f = osc_task_wrench(o, xdd, Lam, col);
   rnea_seg<T, Img, C, true>(M, q, qd, nullptr, tau, col, task, f);
+}
+
+// The same controller on a fixed-base serial chain of N revolute bodies with
+// every sweep unrolled: body indices, and with them each model constant's
+// offset in the parameter image and each joint's frame form (Rot_x after
+// the first body), are known at compile time, and the per-body state (joint
+// cos/sin, U, 1/D, the RNEA sweep) lives in registers. The path to the task
+// body is bodies 0 .. task.
+template <int N, class Img, class C>
+FD void osc_chain(const Img& M, int task, const float* __restrict__ q, const float* __restrict__ qd,
+                  const float* __restrict__ xdd, float* __restrict__ tau, float* __restrict__ Lam, const C& col) {
+  using T = ChainTopo<N>;
+  float cs[N], sn[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) joint_sincos(col.in(q, k) + M.body[k].th0, &sn[k], &cs[k]);
+  // sweep 1: articulated inertias at zero velocity, tip to base
+  SV U[N];
+  float dinv[N];
+  AI IA;
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    const BodyImage& b = M.body[k];
+    AI Ik = ai_of(rbi_of(b));
+    if (k < N - 1) ai_add(Ik, IA);
+    IA = Ik;
+    U[k] = ai_col_z(IA);
+    dinv[k] = rcp(U[k].w.z);
+    ai_rank1_sub(IA, U[k], dinv[k]);
+    ai_out(b, cs[k], sn[k], IA, k > 0);
+  }
+  // sweep 2: outward along bodies 0 .. task
+  OscPath o;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) { o.Om.A[k] = 0.f; o.Om.C[k] = 0.f; }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) { o.Om.B[k] = 0.f; o.E[k] = (k % 4 == 0) ? 1.f : 0.f; }
+  o.v = szero();
+  o.a = szero();
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (k > task) break;
+    if (k > 0) osc_path_step(M.body[k], cs[k], sn[k], col.in(qd, k), U[k], dinv[k], o, DhOn{});
+    else osc_path_step(M.body[k], cs[k], sn[k], col.in(qd, k), U[k], dinv[k], o, DhOff{});
+  }
+  // sweep 3: the task wrench
+  const SV fext = osc_task_wrench(o, xdd, Lam, col);
+  // sweep 4: RNEA at qdd = 0 with f added to the task body's force
+  SV v = szero(), a = gravity_acc(M.g), F[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const BodyImage& b = M.body[k];
+    const float qdk = col.in(qd, k);
+    v = mot_in(b, cs[k], sn[k], v, k > 0);
+    v.w.z += qdk;
+    a = mot_in(b, cs[k], sn[k], a, k > 0) + ez_velprod(v, qdk);
+    const RBI I = rbi_of(b);
+    F[k] = crf_add(rbi_mul(I, a), v, rbi_mul(I, v));
+    if (k == task) F[k] = F[k] + fext;
+  }
+  SV Fs = szero();
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    Fs = Fs + F[k];
+    col.out(tau, k, Fs.w.z);
+    if (k > 0) Fs = frc_out(M.body[k], cs[k], sn[k], Fs, true);
+  }
+  (void)sizeof(T);
 }
 
 }  // namespace frax

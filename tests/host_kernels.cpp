@@ -76,6 +76,9 @@ void run_all(const HostModel& hm, int B, int nf, const int* frames, const float*
   auto& dpose = o.add("fk_jvp", size_t(6) * nf, B);
   auto& tau_e = o.add("rnea_ext", nv, B);
   auto& qdd_e = o.add("aba_ext", nv, B);
+  auto& osc_t = o.add("osc", nv, B);
+  auto& osc_l = o.add("osc_lambda", 36, B);
+  const int task = frames[nf - 1];
   for (int b = 0; b < B; ++b) {
     const Col col{B, b};
     fk_seg<T, ModelImage<NBI>, Col, true>(img, q, pose.data(), fr, J.data(), col);
@@ -103,6 +106,12 @@ void run_all(const HostModel& hm, int B, int nf, const int* frames, const float*
       rnea_seg<T>(img, q, qd, qdd, tau_e.data(), col);
       ext_tau<T>(img, q, fext, col, SubFromGlobal<T>{tau_e.data(), ColT<false>{B, b}});
     }
+    // operational-space control of the last frame, task accelerations = the
+    // first six rows of dx
+    if (chain7)
+      osc_chain<7>(img, task, q, qd, dx, osc_t.data(), osc_l.data(), col);
+    else
+      osc_seg<T>(img, task, q, qd, dx, osc_t.data(), osc_l.data(), col);
     {  // ABA with external forces: right-hand side tau + tau_ext
       LocalVec<T> w;
       ext_tau<T>(img, q, fext, col, OutToLocal<T>{&w});

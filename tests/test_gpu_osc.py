@@ -25,7 +25,7 @@ MODELS = {
     "humanoid": gen.humanoid(0),
     "tree_big": gen.random_tree(7, 64),
 }
-TASKS = [("chain7", 6), ("humanoid", 6), ("humanoid", 12), ("humanoid", 22), ("humanoid", 29), ("humanoid", 0),
+TASKS = [("chain7", 6), ("chain7", 5), ("humanoid", 6), ("humanoid", 12), ("humanoid", 22), ("humanoid", 29), ("humanoid", 0),
          ("tree_big", 34)]
 
 

@@ -14,7 +14,7 @@ import pytest
 
 import gen
 from oracle import derivatives as dv
-from oracle import rbd
+from oracle import rbd, task_space
 from tests.pins import normwise
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -94,6 +94,18 @@ def test_host_compiled_kernels_match_the_oracle(harness, tmp_path, name):
     assert normwise(o["fk_jvp"], dv.fk_jvp(m, s.q, extra["dq"], frames).reshape(B, -1)) < TOL
     assert normwise(o["rnea_ext"], rbd.rnea(m, s.q, s.qd, s.qdd, fext=extra["F"])) < TOL
     assert normwise(o["aba_ext"], rbd.aba(m, s.q, s.qd, s.tau, fext=extra["F"])) < tol_aba
+    # operational-space control of the last frame (the chain through its unrolled code), task accelerations
+    # = the first six rows of dx; the FP32 bound of a solve with Lambda^-1 (cond(Lambda) * 2^-24)
+    path_dofs, j = 0, frames[-1]
+    while j >= 0:
+        path_dofs += 6 if m.joint_type[j] == 1 else 1
+        j = int(m.parent[j])
+    if path_dofs >= 6:  # fewer dofs leave Lambda^-1 singular
+        rt, rL = task_space.osc(m, s.q, s.qd, frames[-1], extra["dx"][:, :6])
+        bound = 1e-5 + np.linalg.cond(rL) * 2.0 ** -24
+        rel = lambda a, r: np.max(np.abs(a - r).reshape(B, -1), 1) / np.max(np.abs(r).reshape(B, -1), 1)
+        assert np.all(rel(o["osc"], rt) <= bound)
+        assert np.all(rel(o["osc_lambda"], rL.reshape(B, -1)) <= bound)
     if m.n_bodies <= 32:  # the lane-group sweeps, lanes run one after another in each step
         assert normwise(o["rnea_lg"], rbd.rnea(m, s.q, s.qd, s.qdd)) < TOL
         assert normwise(o["bias_lg"], rbd.rnea(m, s.q, s.qd, np.zeros_like(s.qd))) < TOL
