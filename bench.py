@@ -893,6 +893,9 @@ def frax_arm(args, rank, world, local_rank):
     ms_per_step, value = whole_job(step_ms, len(OPS) * B, world, dist, device)
     hbm, hbm_src = measured_hbm_gbs()
     per_op = roofline_of(per_op_ms, FLOPS["chain7"], B, peak, hbm, robot)
+    per_op["aba"]["method"] = ("forward dynamics through the mass-matrix factor (RNEA bias + CRBA + L^T D L solves), "
+                               "what frax_aba runs on the 7-body chain; next_rows.chain7.aba_sweep times the O(n) "
+                               "articulated-body sweeps")
     dom = max(OPS, key=lambda n: per_op_ms[n])
     d = per_op[dom]
     if d["bound"] == "alu":

@@ -103,8 +103,11 @@ void run_all(const HostModel& hm, int B, int nf, const int* frames, const float*
       aba_vjp_seg_one<T>(img, q, qd, tau, qdd_a.data(), gbar, aq.data(), aqd.data(), at.data(), col);
       aba_jvp_seg_one<T>(img, q, qd, qdd_a.data(), dq, dqd, dx, dqdd.data(), col);
       fk_jvp_seg<T>(img, q, dq, fr, dpose.data(), col);
-      rnea_seg<T>(img, q, qd, qdd, tau_e.data(), col);
-      ext_tau<T>(img, q, fext, col, SubFromGlobal<T>{tau_e.data(), ColT<false>{B, b}});
+      {  // as k_rnea_ext: tau_ext first, then RNEA writing tau - tau_ext
+        LocalVec<T> w;
+        ext_tau<T>(img, q, fext, col, OutToLocal<T>{&w});
+        rnea_seg<T>(img, q, qd, qdd, tau_e.data(), ColMinusLocal<T, Col>{col, &w, B, b});
+      }
     }
     // operational-space control of the last frame, task accelerations = the
     // first six rows of dx
