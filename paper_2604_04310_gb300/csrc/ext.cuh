@@ -177,18 +177,6 @@ struct SubFromGlobal {
   FD void root(const SV& x) const { store6(p, 0, col, load6(p, 0, col) - x); }
 };
 
-// Column accessor that writes x - w[k] for output entry k: RNEA's own output
-// sink becomes RNEA - tau_ext with tau_ext already in a thread-local vector,
-// so nothing is read back from global memory.
-template <class T, class C>
-struct ColMinusLocal {
-  C base;
-  const LocalVec<T>* w;
-  int64_t ld, b;  // as the other column accessors (unused here)
-  FD float in(const float* __restrict__ p, int k) const { return base.in(p, k); }
-  FD void out(float* __restrict__ p, int k, float v) const { base.out(p, k, v - w->x[k]); }
-};
-
 // tau + tau_ext as the right-hand side of ABA.
 template <class T, class C>
 struct RhsPlusLocal {

@@ -61,30 +61,36 @@ cudaError_t launch_lg(const HostModel& m, const ModelImage<32>& img, Op op, cons
   auto go = [&](auto k, int sm, auto&&... args) -> cudaError_t {
     if (decide && a.B > lg_wave(k, sm)) return cudaErrorNotSupported;
     if ((e = lg_smem(k, sm)) != cudaSuccess) return e;
-    k<<<grid, kLgBlock, sm, a.stream>>>(img, P, a.B, a.ld, args...);
+    k<<<grid, kLgBlock, sm, a.stream>>>(img, P, args...);
     return cudaGetLastError();
   };
   switch (op) {
     case kOpRnea:
-      return go(m.free_root ? k_rnea_lg<true> : k_rnea_lg<false>, bytes(lg_rnea_floats(m.nb, no, ni), r3), a.q,
-                a.qd, a.qdd, a.out0);
+      return go(m.free_root ? k_rnea_lg<true> : k_rnea_lg<false>, bytes(lg_rnea_floats(m.nb, no, ni), r3), a.B,
+                a.ld, a.q, a.qd, a.qdd, a.out0);
     case kOpAba:
     case kOpAbaSweep:
-      return go(m.free_root ? k_aba_lg<true> : k_aba_lg<false>, bytes(lg_aba_floats(m.nb, no, ni), r3), a.q, a.qd,
-                a.tau, a.out0);
+      return go(m.free_root ? k_aba_lg<true> : k_aba_lg<false>, bytes(lg_aba_floats(m.nb, no, ni), r3), a.B,
+                a.ld, a.q, a.qd, a.tau, a.out0);
     case kOpRneaVjp:
       return go(m.free_root ? k_rnea_vjp_lg<true> : k_rnea_vjp_lg<false>, bytes(lg_vjp_floats(m.nb, no, ni), r4),
-                a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1, a.out2);
+                a.B, a.ld, a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1, a.out2);
+    case kOpCrba: {
+      static const ZeroRows kNone{};
+      return go(m.free_root ? k_crba_lg<true> : k_crba_lg<false>, bytes(lg_crba_floats(m.nb, ni), m.nq),
+                a.zeros ? *a.zeros : kNone, a.B, a.ld, a.q, a.out0, a.out1);
+    }
     case kOpAbaVjp:
       return go(m.free_root ? k_aba_vjp_lg<true> : k_aba_vjp_lg<false>,
-                bytes(lg_aba_vjp_floats(m.nb, m.nv, no, ni), r4), a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1, a.out2);
+                bytes(lg_aba_vjp_floats(m.nb, m.nv, no, ni), r4), a.B, a.ld, a.q, a.qd, a.qdd, a.gbar, a.out0,
+                a.out1, a.out2);
     default:
       return cudaErrorInvalidValue;
   }
 }
 
 bool has_lg(Op op) {
-  return op == kOpRnea || op == kOpAba || op == kOpAbaSweep || op == kOpRneaVjp || op == kOpAbaVjp;
+  return op == kOpRnea || op == kOpAba || op == kOpAbaSweep || op == kOpRneaVjp || op == kOpAbaVjp || op == kOpCrba;
 }
 
 }  // namespace

@@ -148,15 +148,9 @@ __global__ void __launch_bounds__(kBlock, 8) k_rnea_ext(const __grid_constant__ 
                                                          int64_t ld, const float* q, const float* qd,
                                                          const float* qdd, const float* fext, float* tau) {
   FRAX_TID();
-  if constexpr (T::kSeg) {
-    // tau_ext first (thread-local), then RNEA writing tau - tau_ext directly
-    LocalVec<T> w;
-    ext_tau<T>(M, q, fext, col, OutToLocal<T>{&w});
-    rnea_seg<T>(M, q, qd, qdd, tau, ColMinusLocal<T, Col>{col, &w, ld, b});
-  } else {
-    rnea_one<T>(M, q, qd, qdd, tau, col);
-    ext_tau<T>(M, q, fext, col, SubFromGlobal<T>{tau, ColT<false>{ld, b}});
-  }
+  if constexpr (T::kSeg) rnea_seg<T>(M, q, qd, qdd, tau, col);
+  else rnea_one<T>(M, q, qd, qdd, tau, col);
+  ext_tau<T>(M, q, fext, col, SubFromGlobal<T>{tau, ColT<false>{ld, b}});
 }
 template <class T>
 __global__ void __launch_bounds__(kBlock, 8) k_aba_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,

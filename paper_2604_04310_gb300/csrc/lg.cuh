@@ -432,6 +432,101 @@ struct RneaVjpLg {
   }
 };
 
+// CRBA + L^T D L (Algorithm 2's M and its factor) for one lane: joint
+// cos/sin outward, then inward the composite inertia (M) and the articulated
+// inertia at rest (the factor) of every subtree; each body emits its rows by
+// the ancestor walk of crba_seg (structural zeros written separately).
+template <bool FREE, class C>
+struct CrbaLg {
+  using T = SegTopo<32, FREE>;
+  const ModelImage<32>& M;
+  const LanePlan& P;
+  LgScratch S;
+  C col;
+  int lane;
+  bool valid;
+  const float* q;
+  float *Mout, *LD;
+  RBI Cc;  // carried contributions to the parent, in its frame
+  AI Ia;
+  FD int CS() const { return 0; }
+  FD int SN() const { return M.nb; }
+  FD int IS() const { return 2 * M.nb; }
+  struct SinCos {
+    LgScratch S;
+    int cs, sn;
+    FD float cos(int j) const { return S[cs + j]; }
+    FD float sin(int j) const { return S[sn + j]; }
+  };
+
+  FD void sincos_step(int t) {
+    const int i = P.body[t][lane];
+    if (!valid || i < 0 || (FREE && i == 0)) return;
+    float sn, cs;
+    joint_sincos(col.in(q, iq_of<T>(i)) + M.body[i].th0, &sn, &cs);
+    S[CS() + i] = cs;
+    S[SN() + i] = sn;
+  }
+  FD void in_step(int t) {
+    const int i = P.body[t][lane];
+    if (!valid || i < 0) return;
+    const int fl = P.flag[t][lane];
+    const BodyImage& b = M.body[i];
+    RBI Ci = rbi_of(b);
+    AI IAi = ai_of(Ci);
+    if (fl & kLgCarry) {
+      Ci = rbi_add(Ci, Cc);
+      ai_add(IAi, Ia);
+    }
+    for (int r = 0; r < P.rc_count[i]; ++r) {
+      const int f = IS() + 31 * P.islot[P.rc_list[P.rc_first[i] + r]];
+      Ci = rbi_add(Ci, RBI{S[f], mk(S[f + 1], S[f + 2], S[f + 3]), S[f + 4], S[f + 5], S[f + 6], S[f + 7],
+                           S[f + 8], S[f + 9]});
+      S.add_ai(f + 10, IAi);
+    }
+    const int nv = FREE ? M.nb + 5 : M.nb;
+    auto putM = [&](int r, int c, float x) {  // r >= c
+      col.out(Mout, r * nv + c, x);
+      if (r != c) col.out(Mout, c * nv + r, x);
+    };
+    auto putL = [&](int r, int c, float x) { col.out(LD, MSink::tri(r, c), x); };
+    if (FREE && i == 0) {
+      if (Mout) crba_root_block(Ci, putM);
+      if (LD) crba_root_factor(IAi, putL);
+      return;
+    }
+    const int di = iv_of<T>(i);
+    const SV FM{mk(Ci.xz, Ci.yz, Ci.zz), mk(-Ci.h.y, Ci.h.x, 0.f)};  // I^c_i e_z
+    if (Mout) col.out(Mout, di * nv + di, FM.w.z);
+    const SV U = ai_col_z(IAi);
+    const float dinv = rcp(U.w.z);
+    if (LD) putL(di, di, U.w.z);
+    crba_emit_row<T, ModelImage<32>, C, false, 3>(M, i, FM, dinv * U, Mout, LD, SinCos{S, CS(), SN()}, col);
+    ai_rank1_sub(IAi, U, dinv);
+    const float cs = S[CS() + i], sn = S[SN() + i];
+    with_dh(b.dh, [&](auto dh) {
+      Cc = rbi_out(b, cs, sn, Ci, dh);
+      ai_out(b, cs, sn, IAi, dh);
+    });
+    Ia = IAi;
+    if (fl & kLgStoreIn) {
+      const int f = IS() + 31 * P.islot[i];
+      S[f] = Cc.m;
+      S[f + 1] = Cc.h.x;
+      S[f + 2] = Cc.h.y;
+      S[f + 3] = Cc.h.z;
+      S[f + 4] = Cc.xx;
+      S[f + 5] = Cc.yy;
+      S[f + 6] = Cc.zz;
+      S[f + 7] = Cc.xy;
+      S[f + 8] = Cc.xz;
+      S[f + 9] = Cc.yz;
+      S.put_ai(f + 10, Ia);
+    }
+  }
+};
+FD int lg_crba_floats(int nb, int ni) { return 2 * nb + 31 * ni; }
+
 // Scratch floats of the adjoint sweep and of the ABA adjoint (its solve's
 // sweep, w, then the adjoint sweep over a second region).
 FD int lg_vjp_floats(int nb, int no, int ni) { return 20 * nb + 18 * no + 18 * ni; }
@@ -602,6 +697,31 @@ __global__ void __launch_bounds__(kLgBlock) k_aba_vjp_lg(const __grid_constant__
   for (int t = P.T - 1; t >= 0; --t) {
     L.in_step(t);
     __syncwarp();
+  }
+}
+// CRBA + L^T D L; each lane writes its share of the structural zeros (rows
+// lane, lane + 4, ... of the list Z).
+template <bool FREE>
+__global__ void __launch_bounds__(kLgBlock) k_crba_lg(const __grid_constant__ ModelImage<32> Mg,
+                                                      const __grid_constant__ LanePlan Pg,
+                                                      const __grid_constant__ ZeroRows Z, int64_t B, int64_t ld,
+                                                      const float* __restrict__ q, float* Mout, float* LD) {
+  FRAX_LG_PROLOGUE(M.nq);
+  float* sq = stage;
+  lg_stage_rows(q, M.nq, ld, B, sq);
+  __syncthreads();
+  CrbaLg<FREE, LgCol> L{M, P, S, col, lane, valid, sq, Mout, LD};
+  for (int t = 0; t < P.T; ++t) {
+    L.sincos_step(t);
+    __syncwarp();
+  }
+  for (int t = P.T - 1; t >= 0; --t) {
+    L.in_step(t);
+    __syncwarp();
+  }
+  if (valid) {
+    for (int r = lane; r < Z.n0; r += kLgLanes) col.out(Mout, Z.row[r], 0.f);
+    for (int r = Z.n0 + lane; r < Z.n; r += kLgLanes) col.out(LD, Z.row[r], 0.f);
   }
 }
 #undef FRAX_LG_PROLOGUE

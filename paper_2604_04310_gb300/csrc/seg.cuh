@@ -333,9 +333,17 @@ FD void aba_seg(const Img& M, const float* __restrict__ q, const float* __restri
 // dofs of non-ancestors.
 // With ZEROS false the structural zeros (non-ancestor pairs) are left to the
 // caller (a separate fill of those rows, the same for every instance).
-template <class T, class Img, class C, bool ZEROS, int OUT>
+// Joint cos/sin of every body, from per-thread arrays.
+struct SinCosArrays {
+  const float* c;
+  const float* s;
+  FD float cos(int j) const { return c[j]; }
+  FD float sin(int j) const { return s[j]; }
+};
+
+template <class T, class Img, class C, bool ZEROS, int OUT, class SC>
 FD void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mout,
-                                           float* __restrict__ LD, const float* sc, const float* ss, C col) {
+                                           float* __restrict__ LD, const SC& scs, C col) {
   const int nv = T::kFree ? M.nb + 5 : M.nb;
   const int di = iv_of<T>(i);
   const bool wM = (OUT & 1) && Mout != nullptr, wL = (OUT & 2) && LD != nullptr;
@@ -357,9 +365,10 @@ FD void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mou
     const int k = M.parent[j];
     if (k < 0) break;
     const BodyImage& b = M.body[j];
+    const float cj = scs.cos(j), sj = scs.sin(j);
     with_dh(b.dh, [&](auto dh) {
-      if (wM) FM = frc_out(b, sc[j], ss[j], FM, dh);
-      if (wL) FL = frc_out(b, sc[j], ss[j], FL, dh);
+      if (wM) FM = frc_out(b, cj, sj, FM, dh);
+      if (wL) FL = frc_out(b, cj, sj, FL, dh);
     });
     j = k;
     if (T::kFree && j == 0) {
@@ -379,6 +388,51 @@ FD void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mou
       put(iv_of<T>(jj), 0.f, 0.f);
     }
   }
+}
+
+// A free-flyer root's 6x6 block of M from its composite inertia Cc
+// (put(r, c, x) for c <= r).
+template <class Put>
+FD void crba_root_block(const RBI& Cc, const Put& put) {
+  const float blk[6][6] = {{Cc.xx, Cc.xy, Cc.xz, 0.f, -Cc.h.z, Cc.h.y},
+                           {Cc.xy, Cc.yy, Cc.yz, Cc.h.z, 0.f, -Cc.h.x},
+                           {Cc.xz, Cc.yz, Cc.zz, -Cc.h.y, Cc.h.x, 0.f},
+                           {0.f, Cc.h.z, -Cc.h.y, Cc.m, 0.f, 0.f},
+                           {-Cc.h.z, 0.f, Cc.h.x, 0.f, Cc.m, 0.f},
+                           {Cc.h.y, -Cc.h.x, 0.f, 0.f, 0.f, Cc.m}};
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c) put(r, c, blk[r][c]);
+}
+
+// Its block of the factor: the dense L^T D L of the root's articulated
+// inertia A0, last dof first.
+template <class Put>
+FD void crba_root_factor(const AI& A0, const Put& put) {
+  const float* Af = A0.A;
+  const float* Cf = A0.C;
+  float H[6][6] = {{Af[0], Af[3], Af[4], A0.B[0], A0.B[1], A0.B[2]},
+                   {Af[3], Af[1], Af[5], A0.B[3], A0.B[4], A0.B[5]},
+                   {Af[4], Af[5], Af[2], A0.B[6], A0.B[7], A0.B[8]},
+                   {A0.B[0], A0.B[3], A0.B[6], Cf[0], Cf[3], Cf[4]},
+                   {A0.B[1], A0.B[4], A0.B[7], Cf[3], Cf[1], Cf[5]},
+                   {A0.B[2], A0.B[5], A0.B[8], Cf[4], Cf[5], Cf[2]}};
+#pragma unroll
+  for (int k = 5; k >= 0; --k) {
+    const float rk = rcp(H[k][k]);
+#pragma unroll
+    for (int i = k - 1; i >= 0; --i) {
+      const float a = H[k][i] * rk;
+#pragma unroll
+      for (int j = i; j >= 0; --j) H[i][j] = fmaf(-a, H[k][j], H[i][j]);
+      H[k][i] = a;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c) put(r, c, H[r][c]);
 }
 
 // OUT selects at compile time what the kernel can produce (1: M, 2: the
@@ -417,46 +471,11 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
         if constexpr (kL) IAa[0] = azero;
       }
       if (kind == kActOpen) continue;
-      if constexpr (kM) if (wantM) {
-        const RBI Cc = rbi_add(rbi_of(M.body[0]), ICa[0]);
-        const float blk[6][6] = {{Cc.xx, Cc.xy, Cc.xz, 0.f, -Cc.h.z, Cc.h.y},
-                                 {Cc.xy, Cc.yy, Cc.yz, Cc.h.z, 0.f, -Cc.h.x},
-                                 {Cc.xz, Cc.yz, Cc.zz, -Cc.h.y, Cc.h.x, 0.f},
-                                 {0.f, Cc.h.z, -Cc.h.y, Cc.m, 0.f, 0.f},
-                                 {-Cc.h.z, 0.f, Cc.h.x, 0.f, Cc.m, 0.f},
-                                 {Cc.h.y, -Cc.h.x, 0.f, 0.f, 0.f, Cc.m}};
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-          for (int c = 0; c <= r; ++c) putM(r, c, blk[r][c]);
-      }
+      if constexpr (kM) if (wantM) crba_root_block(rbi_add(rbi_of(M.body[0]), ICa[0]), putM);
       if constexpr (kL) if (wantL) {
         AI A0 = ai_of(rbi_of(M.body[0]));
         ai_add(A0, IAa[0]);
-        const float* Af = A0.A;
-        const float* Cf = A0.C;
-        float H[6][6] = {{Af[0], Af[3], Af[4], A0.B[0], A0.B[1], A0.B[2]},
-                         {Af[3], Af[1], Af[5], A0.B[3], A0.B[4], A0.B[5]},
-                         {Af[4], Af[5], Af[2], A0.B[6], A0.B[7], A0.B[8]},
-                         {A0.B[0], A0.B[3], A0.B[6], Cf[0], Cf[3], Cf[4]},
-                         {A0.B[1], A0.B[4], A0.B[7], Cf[3], Cf[1], Cf[5]},
-                         {A0.B[2], A0.B[5], A0.B[8], Cf[4], Cf[5], Cf[2]}};
-        // dense L^T D L of the root block, last dof first
-#pragma unroll
-        for (int k = 5; k >= 0; --k) {
-          const float rk = rcp(H[k][k]);
-#pragma unroll
-          for (int i = k - 1; i >= 0; --i) {
-            const float a = H[k][i] * rk;
-#pragma unroll
-            for (int j = i; j >= 0; --j) H[i][j] = fmaf(-a, H[k][j], H[i][j]);
-            H[k][i] = a;
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-          for (int c = 0; c <= r; ++c) putL(r, c, H[r][c]);
+        crba_root_factor(A0, putL);
       }
       continue;
     }
@@ -501,7 +520,7 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
           ai_rank1_sub(Ia, U, dinv);
           ai_out(b, sc[i], ss[i], Ia);
         }
-        crba_emit_row<T, Img, C, ZEROS, OUT>(M, i, FM, FL, Mout, LD, sc, ss, col);
+        crba_emit_row<T, Img, C, ZEROS, OUT>(M, i, FM, FL, Mout, LD, SinCosArrays{sc, ss}, col);
         const RBI Ip = rbi_of(M.body[M.order[st + (k > 0 ? k - 1 : 0)]]);
         if constexpr (kM) {
           const RBI up = rbi_out(b, sc[i], ss[i], Cc);

@@ -103,11 +103,8 @@ void run_all(const HostModel& hm, int B, int nf, const int* frames, const float*
       aba_vjp_seg_one<T>(img, q, qd, tau, qdd_a.data(), gbar, aq.data(), aqd.data(), at.data(), col);
       aba_jvp_seg_one<T>(img, q, qd, qdd_a.data(), dq, dqd, dx, dqdd.data(), col);
       fk_jvp_seg<T>(img, q, dq, fr, dpose.data(), col);
-      {  // as k_rnea_ext: tau_ext first, then RNEA writing tau - tau_ext
-        LocalVec<T> w;
-        ext_tau<T>(img, q, fext, col, OutToLocal<T>{&w});
-        rnea_seg<T>(img, q, qd, qdd, tau_e.data(), ColMinusLocal<T, Col>{col, &w, B, b});
-      }
+      rnea_seg<T>(img, q, qd, qdd, tau_e.data(), col);
+      ext_tau<T>(img, q, fext, col, SubFromGlobal<T>{tau_e.data(), ColT<false>{B, b}});
     }
     // operational-space control of the last frame, task accelerations = the
     // first six rows of dx
@@ -174,6 +171,9 @@ void run_lane_groups(const HostModel& hm, int B, const float* q, const float* qd
   auto& tau_r = o.add("rnea_lg", hm.nv, B);
   auto& bias = o.add("bias_lg", hm.nv, B);
   auto& qdd_a = o.add("aba_lg", hm.nv, B);
+  auto& Mlg = o.add("crba_lg_M", size_t(hm.nv) * hm.nv, B);
+  auto& LDlg = o.add("crba_lg_LD", size_t(hm.nv) * (hm.nv + 1) / 2, B);
+  std::vector<float> sc(lg_crba_floats(hm.nb, P.n_islot), 0.f);
   auto& rq = o.add("rnea_vjp_lg_q", hm.nq, B);
   auto& rqd = o.add("rnea_vjp_lg_qd", hm.nv, B);
   auto& rqdd = o.add("rnea_vjp_lg_qdd", hm.nv, B);
@@ -208,6 +208,15 @@ void run_lane_groups(const HostModel& hm, int B, const float* q, const float* qd
       for (auto& x : L) x.inward_step(t);
     for (int t = 0; t < P.T; ++t)
       for (auto& x : L) x.acc_step(t);
+    // CRBA + L^T D L (the structural zeros stay as the output was cleared)
+    using CL = CrbaLg<FREE, Col>;
+    std::vector<CL> Cg;
+    for (int l = 0; l < kLgLanes; ++l)
+      Cg.push_back(CL{img, P, LgScratch{sc.data(), 1}, col, l, true, q, Mlg.data(), LDlg.data()});
+    for (int t = 0; t < P.T; ++t)
+      for (auto& x : Cg) x.sincos_step(t);
+    for (int t = P.T - 1; t >= 0; --t)
+      for (auto& x : Cg) x.in_step(t);
     // the RNEA adjoint
     using VjpL = RneaVjpLg<FREE, Col, RhsFromGlobal<T, Col>, VjpToGlobal<T, Col>>;
     std::vector<VjpL> V;

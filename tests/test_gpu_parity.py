@@ -455,6 +455,11 @@ def test_lane_group_paths(fxm, name, B):
         bias = fx.frax_rnea(h, d["q"], d["qd"], None)
         qdd = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
         qdd2 = fx.frax_aba_articulated(h, d["q"], d["qd"], d["tau"])
+        # CRBA into NaN-filled outputs: every entry, structural zeros included, is written
+        Mn = torch.full((m.nv * m.nv, B), float("nan"), device="cuda")
+        LDn = torch.full((m.nv * (m.nv + 1) // 2, B), float("nan"), device="cuda")
+        fx.frax_crba(h, d["q"], M=Mn, LD=LDn)
+        M_only, _ = fx.frax_crba(h, d["q"], want_M=True, want_LD=False)
         h.set_tree_path("thread")
         tau_t = fx.frax_rnea(h, d["q"], d["qd"], d["qdd"])
         qdd_t = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
@@ -465,6 +470,11 @@ def test_lane_group_paths(fxm, name, B):
     qref = rbd.aba(m, s.q, s.qd, s.tau)
     assert normwise(host(qdd), qref) < TOL_ABA_TREE
     assert torch.equal(qdd, qdd2)
+    Mref = rbd.crba(m, s.q)
+    assert not torch.isnan(Mn).any() and not torch.isnan(LDn).any()
+    assert normwise(host(Mn), Mref.reshape(B, -1)) < TOL
+    assert normwise(host(LDn), rbd.pack_ltdl(*rbd.ltdl(Mref))) < TOL
+    assert torch.equal(M_only, Mn)
     # the two paths agree to FP32 rounding of the branch sums
     assert normwise(host(tau), host(tau_t)) < 1e-5
     assert normwise(host(qdd), host(qdd_t)) < TOL_ABA_TREE

@@ -110,6 +110,8 @@ def test_host_compiled_kernels_match_the_oracle(harness, tmp_path, name):
         assert normwise(o["rnea_lg"], rbd.rnea(m, s.q, s.qd, s.qdd)) < TOL
         assert normwise(o["bias_lg"], rbd.rnea(m, s.q, s.qd, np.zeros_like(s.qd))) < TOL
         assert normwise(o["aba_lg"], rbd.aba(m, s.q, s.qd, s.tau)) < tol_aba
+        assert normwise(o["crba_lg_M"], Mref.reshape(B, -1)) < TOL
+        assert normwise(o["crba_lg_LD"], rbd.pack_ltdl(*rbd.ltdl(Mref))) < TOL
         for got, ref in zip(("rnea_vjp_lg_q", "rnea_vjp_lg_qd", "rnea_vjp_lg_qdd"),
                             dv.rnea_vjp(m, s.q, s.qd, s.qdd, extra["g"])):
             assert normwise(o[got], ref) < TOL_TREE, got
