@@ -706,7 +706,7 @@ TREE_PATH_B = [64, 512, 4096, 8192, 16384, 1 << 15, 1 << 18]
 
 
 def tree_paths(fx, device, flush):
-    """The humanoid's RNEA, bias forces, CRBA + LTDL, ABA and both adjoints on both tree
+    """The humanoid's FK + Jacobians, RNEA, bias forces, CRBA + LTDL, ABA and both adjoints on both tree
     paths, one thread per instance and four lanes per instance (lane groups),
     at batch sizes from 64 to 2^18: each op captured alone as a CUDA graph and
     replayed (kernel time only, CUDA events, L2 flushed between replays),
@@ -719,7 +719,7 @@ def tree_paths(fx, device, flush):
         for B in TREE_PATH_B:
             _, dev = make_inputs(robot, B, 4005, device)
             reps = 100 if B <= 4096 else 30
-            for op in ("rnea", "bias", "crba_ltdl", "aba", "rnea_vjp", "aba_vjp"):
+            for op in ("fk_jac", "rnea", "bias", "crba_ltdl", "aba", "rnea_vjp", "aba_vjp"):
                 row = {"B": B, "op": op}
                 for path in ("thread", "lane_group"):
                     model.set_tree_path(path)
@@ -733,7 +733,7 @@ def tree_paths(fx, device, flush):
             del dev
     finally:
         model.set_tree_path("auto")
-    return {"workload": "humanoid (root + 29 revolute), RNEA / bias / CRBA+LTDL / ABA / RNEA-VJP / ABA-VJP at each batch size "
+    return {"workload": "humanoid (root + 29 revolute), FK+J / RNEA / bias / CRBA+LTDL / ABA / RNEA-VJP / ABA-VJP at each batch size "
                         "on both tree paths",
             "rows": rows, "launches": launches}
 

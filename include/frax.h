@@ -94,9 +94,9 @@ FRAX_API frax_status frax_model_kind(frax_model_t model, int* kind);
  * instance). FRAX_TREE_PATH_THREAD: one thread per instance, the segment
  * sweeps. FRAX_TREE_PATH_LANE_GROUP: four lanes of a warp per instance, each
  * walking its own branches of the tree (Sec. III-A's parallelism within one
- * instance), for the ops that have such kernels (frax_rnea, frax_crba,
- * frax_aba, frax_aba_articulated, frax_rnea_vjp, frax_aba_vjp); other ops
- * run one thread per instance.
+ * instance), for the ops that have such kernels (frax_fk, frax_jacobian,
+ * frax_rnea, frax_crba, frax_aba, frax_aba_articulated, frax_rnea_vjp,
+ * frax_aba_vjp); other ops run one thread per instance.
  * FRAX_TREE_PATH_AUTO (the default): the lane groups while the batch fits
  * one resident wave of the op's lane-group kernel on the current device (a
  * few thousand instances, fewer for ops with more state per instance), where

@@ -75,6 +75,13 @@ cudaError_t launch_lg(const HostModel& m, const ModelImage<32>& img, Op op, cons
     case kOpRneaVjp:
       return go(m.free_root ? k_rnea_vjp_lg<true> : k_rnea_vjp_lg<false>, bytes(lg_vjp_floats(m.nb, no, ni), r4),
                 a.B, a.ld, a.q, a.qd, a.qdd, a.gbar, a.out0, a.out1, a.out2);
+    case kOpFk:
+    case kOpJac: {
+      Frames fr{a.frames.n, {0}};
+      for (int k = 0; k < 8; ++k) fr.body[k] = a.frames.body[k];
+      return go(m.free_root ? k_fk_lg<true> : k_fk_lg<false>, bytes(lg_fk_floats(m.nb, no), m.nq), a.B, a.ld, a.q,
+                a.out0, fr, a.out1);
+    }
     case kOpCrba: {
       static const ZeroRows kNone{};
       return go(m.free_root ? k_crba_lg<true> : k_crba_lg<false>, bytes(lg_crba_floats(m.nb, ni), m.nq),
@@ -90,7 +97,8 @@ cudaError_t launch_lg(const HostModel& m, const ModelImage<32>& img, Op op, cons
 }
 
 bool has_lg(Op op) {
-  return op == kOpRnea || op == kOpAba || op == kOpAbaSweep || op == kOpRneaVjp || op == kOpAbaVjp || op == kOpCrba;
+  return op == kOpRnea || op == kOpAba || op == kOpAbaSweep || op == kOpRneaVjp || op == kOpAbaVjp || op == kOpCrba ||
+         op == kOpFk || op == kOpJac;
 }
 
 }  // namespace

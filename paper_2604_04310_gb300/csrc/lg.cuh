@@ -527,6 +527,130 @@ struct CrbaLg {
 };
 FD int lg_crba_floats(int nb, int ni) { return 2 * nb + 31 * ni; }
 
+// FK and frame Jacobians for one lane: world rotations and origins outward
+// (each body's pose written, its world axis and origin kept in the scratch),
+// then each lane builds the Jacobians of the frames lane, lane + 4, ...:
+// column j of frame k is [z_j; z_j x (p_k - p_j)] for every ancestor j (the
+// structural zeros are left to the caller's fill, as for fk_seg).
+template <bool FREE, class C>
+struct FkLg {
+  using T = SegTopo<32, FREE>;
+  const ModelImage<32>& M;
+  const LanePlan& P;
+  LgScratch S;
+  C col;
+  int lane;
+  bool valid;
+  const float* q;
+  float* pose;
+  const Frames& fr;
+  float* J;
+  float R[9];  // carried: world rotation and origin of the previous body
+  V3 p;
+  FD int Z0() const { return 0; }
+  FD int PO() const { return 3 * M.nb; }
+  FD int R0() const { return 6 * M.nb; }
+  FD int OS() const { return 6 * M.nb + 9; }
+
+  FD void pose_out(int i) const {
+    const BodyImage& b = M.body[i];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+        col.out(pose, 12 * i + 3 * r + cc,
+                fmaf(R[3 * r], b.Q[3 * cc], fmaf(R[3 * r + 1], b.Q[3 * cc + 1], R[3 * r + 2] * b.Q[3 * cc + 2])));
+    col.out(pose, 12 * i + 9, p.x);
+    col.out(pose, 12 * i + 10, p.y);
+    col.out(pose, 12 * i + 11, p.z);
+  }
+  FD void out_step(int t) {
+    const int i = P.body[t][lane];
+    if (!valid || i < 0) return;
+    const int fl = P.flag[t][lane];
+    if (FREE && i == 0) {
+      const RootPose RP = root_pose(M, q, col);
+#pragma unroll
+      for (int u = 0; u < 9; ++u) S[R0() + u] = R[u] = RP.E[u];
+      p = RP.r;
+    } else {
+      const BodyImage& b = M.body[i];
+      const int par = M.parent[i];
+      if (par < 0) {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) R[u] = (u % 4 == 0) ? 1.f : 0.f;
+        p = mk(0, 0, 0);
+      } else if (fl & kLgLoad) {
+        const int f = OS() + 12 * P.oslot[par];
+#pragma unroll
+        for (int u = 0; u < 9; ++u) R[u] = S[f + u];
+        p = mk(S[f + 9], S[f + 10], S[f + 11]);
+      }
+      float sn, cs;
+      joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
+      float A[9];
+      with_dh(b.dh, [&](auto dh) { mat_mul_b(R, b, A, dh); });
+      p = p + rot(R, mk(b.p[0], b.p[1], b.p[2]));
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        R[3 * r] = fmaf(cs, A[3 * r], sn * A[3 * r + 1]);
+        R[3 * r + 1] = fmaf(-sn, A[3 * r], cs * A[3 * r + 1]);
+        R[3 * r + 2] = A[3 * r + 2];
+      }
+    }
+    S[Z0() + 3 * i] = R[2];
+    S[Z0() + 3 * i + 1] = R[5];
+    S[Z0() + 3 * i + 2] = R[8];
+    S[PO() + 3 * i] = p.x;
+    S[PO() + 3 * i + 1] = p.y;
+    S[PO() + 3 * i + 2] = p.z;
+    if (pose) pose_out(i);
+    if (fl & kLgStoreOut) {
+      const int f = OS() + 12 * P.oslot[i];
+#pragma unroll
+      for (int u = 0; u < 9; ++u) S[f + u] = R[u];
+      S[f + 9] = p.x;
+      S[f + 10] = p.y;
+      S[f + 11] = p.z;
+    }
+  }
+  FD void jacobians() const {
+    if (!valid || !J) return;
+    const int nv = FREE ? M.nb + 5 : M.nb;
+    auto pos = [&](int j) { return mk(S[PO() + 3 * j], S[PO() + 3 * j + 1], S[PO() + 3 * j + 2]); };
+    auto jcol = [&](int base, int cj, V3 z, V3 lin) {
+      col.out(J, base + 0 * nv + cj, z.x);
+      col.out(J, base + 1 * nv + cj, z.y);
+      col.out(J, base + 2 * nv + cj, z.z);
+      col.out(J, base + 3 * nv + cj, lin.x);
+      col.out(J, base + 4 * nv + cj, lin.y);
+      col.out(J, base + 5 * nv + cj, lin.z);
+    };
+    for (int f = lane; f < fr.n; f += kLgLanes) {
+      const int kf = fr.body[f];
+      uint64_t rest = M.anc[kf];
+      const int base = f * 6 * nv;
+      const V3 pk = pos(kf);
+      if (FREE) {  // the root is an ancestor of every body
+        const V3 d = pk - pos(0);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const V3 zr = mk(S[R0() + m], S[R0() + 3 + m], S[R0() + 6 + m]);
+          jcol(base, m, zr, cross(zr, d));
+          jcol(base, 3 + m, mk(0, 0, 0), zr);
+        }
+        rest &= ~1ull;
+      }
+      for (; rest; rest &= rest - 1) {
+        const int j = low_bit(rest);
+        const V3 zj = mk(S[Z0() + 3 * j], S[Z0() + 3 * j + 1], S[Z0() + 3 * j + 2]);
+        jcol(base, iv_of<T>(j), zj, cross(zj, pk - pos(j)));
+      }
+    }
+  }
+};
+FD int lg_fk_floats(int nb, int no) { return 6 * nb + 9 + 12 * no; }
+
 // Scratch floats of the adjoint sweep and of the ABA adjoint (its solve's
 // sweep, w, then the adjoint sweep over a second region).
 FD int lg_vjp_floats(int nb, int no, int ni) { return 20 * nb + 18 * no + 18 * ni; }
@@ -723,6 +847,23 @@ __global__ void __launch_bounds__(kLgBlock) k_crba_lg(const __grid_constant__ Mo
     for (int r = lane; r < Z.n0; r += kLgLanes) col.out(Mout, Z.row[r], 0.f);
     for (int r = Z.n0 + lane; r < Z.n; r += kLgLanes) col.out(LD, Z.row[r], 0.f);
   }
+}
+// FK (every body's pose) and, when J is given, the frames' Jacobians.
+template <bool FREE>
+__global__ void __launch_bounds__(kLgBlock) k_fk_lg(const __grid_constant__ ModelImage<32> Mg,
+                                                    const __grid_constant__ LanePlan Pg, int64_t B, int64_t ld,
+                                                    const float* __restrict__ q, float* pose,
+                                                    const __grid_constant__ Frames fr, float* J) {
+  FRAX_LG_PROLOGUE(M.nq);
+  float* sq = stage;
+  lg_stage_rows(q, M.nq, ld, B, sq);
+  __syncthreads();
+  FkLg<FREE, LgCol> L{M, P, S, col, lane, valid, sq, pose, fr, J};
+  for (int t = 0; t < P.T; ++t) {
+    L.out_step(t);
+    __syncwarp();
+  }
+  L.jacobians();
 }
 #undef FRAX_LG_PROLOGUE
 #endif

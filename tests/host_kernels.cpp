@@ -163,14 +163,19 @@ std::string check_plan(const HostModel& hm) {
 }
 
 template <bool FREE>
-void run_lane_groups(const HostModel& hm, int B, const float* q, const float* qd, const float* qdd,
-                     const float* tau, const float* gbar, Out& o) {
+void run_lane_groups(const HostModel& hm, int B, int nf, const int* frames, const float* q, const float* qd,
+                     const float* qdd, const float* tau, const float* gbar, Out& o) {
   ModelImage<32> img;
   hm.pack(&img);
   const LanePlan& P = hm.lane_plan;
   auto& tau_r = o.add("rnea_lg", hm.nv, B);
   auto& bias = o.add("bias_lg", hm.nv, B);
   auto& qdd_a = o.add("aba_lg", hm.nv, B);
+  auto& pose_lg = o.add("fk_lg_pose", 12 * hm.nb, B);
+  auto& J_lg = o.add("fk_lg_J", size_t(nf) * 6 * hm.nv, B);
+  std::vector<float> sf(lg_fk_floats(hm.nb, P.n_oslot), 0.f);
+  Frames fr{nf, {0}};
+  for (int f = 0; f < nf; ++f) fr.body[f] = frames[f];
   auto& Mlg = o.add("crba_lg_M", size_t(hm.nv) * hm.nv, B);
   auto& LDlg = o.add("crba_lg_LD", size_t(hm.nv) * (hm.nv + 1) / 2, B);
   std::vector<float> sc(lg_crba_floats(hm.nb, P.n_islot), 0.f);
@@ -208,6 +213,14 @@ void run_lane_groups(const HostModel& hm, int B, const float* q, const float* qd
       for (auto& x : L) x.inward_step(t);
     for (int t = 0; t < P.T; ++t)
       for (auto& x : L) x.acc_step(t);
+    // FK and Jacobians (the structural zeros stay as the output was cleared)
+    using FL = FkLg<FREE, Col>;
+    std::vector<FL> Fk;
+    for (int l = 0; l < kLgLanes; ++l)
+      Fk.push_back(FL{img, P, LgScratch{sf.data(), 1}, col, l, true, q, pose_lg.data(), fr, J_lg.data()});
+    for (int t = 0; t < P.T; ++t)
+      for (auto& x : Fk) x.out_step(t);
+    for (auto& x : Fk) x.jacobians();
     // CRBA + L^T D L (the structural zeros stay as the output was cleared)
     using CL = CrbaLg<FREE, Col>;
     std::vector<CL> Cg;
@@ -303,9 +316,10 @@ int main(int argc, char** argv) {
       const std::string perr = check_plan(hm);
       if (!perr.empty()) throw perr;
       if (hm.free_root)
-        run_lane_groups<true>(hm, B, q.data(), qd.data(), qdd.data(), tau.data(), gbar.data(), o);
+        run_lane_groups<true>(hm, B, nf, frames.data(), q.data(), qd.data(), qdd.data(), tau.data(), gbar.data(), o);
       else
-        run_lane_groups<false>(hm, B, q.data(), qd.data(), qdd.data(), tau.data(), gbar.data(), o);
+        run_lane_groups<false>(hm, B, nf, frames.data(), q.data(), qd.data(), qdd.data(), tau.data(), gbar.data(),
+                               o);
     }
     FILE* g = std::fopen(argv[2], "wb");
     if (!g) throw std::string("cannot open output");

@@ -460,6 +460,12 @@ def test_lane_group_paths(fxm, name, B):
         LDn = torch.full((m.nv * (m.nv + 1) // 2, B), float("nan"), device="cuda")
         fx.frax_crba(h, d["q"], M=Mn, LD=LDn)
         M_only, _ = fx.frax_crba(h, d["q"], want_M=True, want_LD=False)
+        # FK and Jacobians into NaN-filled outputs (the structural zeros come from the row fill)
+        frames = list(m.end_frames)[:8]
+        pose_n = torch.full((12 * m.n_bodies, B), float("nan"), device="cuda")
+        J_n = torch.full((len(frames) * 6 * m.nv, B), float("nan"), device="cuda")
+        fx.frax_jacobian(h, d["q"], frames, pose=pose_n, J=J_n)
+        pose_fk = fx.frax_fk(h, d["q"])
         h.set_tree_path("thread")
         tau_t = fx.frax_rnea(h, d["q"], d["qd"], d["qdd"])
         qdd_t = fx.frax_aba(h, d["q"], d["qd"], d["tau"])
@@ -475,6 +481,10 @@ def test_lane_group_paths(fxm, name, B):
     assert normwise(host(Mn), Mref.reshape(B, -1)) < TOL
     assert normwise(host(LDn), rbd.pack_ltdl(*rbd.ltdl(Mref))) < TOL
     assert torch.equal(M_only, Mn)
+    assert not torch.isnan(pose_n).any() and not torch.isnan(J_n).any()
+    assert normwise(host(pose_n), rbd.fk_flat(m, s.q)) < TOL
+    assert normwise(host(J_n), rbd.jacobian(m, s.q, frames).reshape(B, -1)) < TOL
+    assert torch.equal(pose_fk, pose_n)
     # the two paths agree to FP32 rounding of the branch sums
     assert normwise(host(tau), host(tau_t)) < 1e-5
     assert normwise(host(qdd), host(qdd_t)) < TOL_ABA_TREE

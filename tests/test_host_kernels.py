@@ -110,6 +110,8 @@ def test_host_compiled_kernels_match_the_oracle(harness, tmp_path, name):
         assert normwise(o["rnea_lg"], rbd.rnea(m, s.q, s.qd, s.qdd)) < TOL
         assert normwise(o["bias_lg"], rbd.rnea(m, s.q, s.qd, np.zeros_like(s.qd))) < TOL
         assert normwise(o["aba_lg"], rbd.aba(m, s.q, s.qd, s.tau)) < tol_aba
+        assert normwise(o["fk_lg_pose"], rbd.fk_flat(m, s.q)) < TOL
+        assert normwise(o["fk_lg_J"], rbd.jacobian(m, s.q, frames).reshape(B, -1)) < TOL
         assert normwise(o["crba_lg_M"], Mref.reshape(B, -1)) < TOL
         assert normwise(o["crba_lg_LD"], rbd.pack_ltdl(*rbd.ltdl(Mref))) < TOL
         for got, ref in zip(("rnea_vjp_lg_q", "rnea_vjp_lg_qd", "rnea_vjp_lg_qdd"),
