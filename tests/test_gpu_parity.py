@@ -29,6 +29,7 @@ MODELS = {
     "tree101": gen.random_tree(101),
     "tree117": gen.random_tree(117),
     "tree_big": gen.random_tree(7, 64),
+    "tree32": gen.random_tree(9, 32),
 }
 
 
@@ -438,7 +439,7 @@ def test_chain_unrolled_kernels_edge_batches(fxm, B):
     assert normwise(host(v("ae")), rbd.aba(m, s.q, s.qd, s.tau, fext=Fb)) < TOL
 
 
-LG_MODELS = ["humanoid", "tree101", "tree117"]
+LG_MODELS = ["humanoid", "tree101", "tree117", "tree32"]
 
 
 @pytest.mark.parametrize("name", LG_MODELS)
