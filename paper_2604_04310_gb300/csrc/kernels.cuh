@@ -141,16 +141,22 @@ __global__ void __launch_bounds__(kBlock, 5) k_osc_seg(const __grid_constant__ M
   osc_seg<T>(M, task, q, qd, xdd, tau, Lam, col);
 }
 
-// External forces: the plain kernel's result, then tau_ext from one more
-// sweep (subtracted from RNEA's output, added to ABA's right-hand side).
+// External forces. Trees: RNEA takes them inside its own outward sweep;
+// ABA adds tau_ext from one more sweep to its right-hand side.
+// RNEA with external forces: 5 blocks per SM (the world pose it carries
+// spills at 64 registers; humanoid 2^18: 152 us against 156 at 8 blocks).
 template <class T>
-__global__ void __launch_bounds__(kBlock, 8) k_rnea_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 5) k_rnea_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                          int64_t ld, const float* q, const float* qd,
                                                          const float* qdd, const float* fext, float* tau) {
   FRAX_TID();
-  if constexpr (T::kSeg) rnea_seg<T>(M, q, qd, qdd, tau, col);
-  else rnea_one<T>(M, q, qd, qdd, tau, col);
-  ext_tau<T>(M, q, fext, col, SubFromGlobal<T>{tau, ColT<false>{ld, b}});
+  if constexpr (T::kSeg) {
+    // the forces enter RNEA's own outward sweep (Algorithm 1's -F_ext,i)
+    rnea_seg<T, ModelImage<T::NBMAX>, Col, false, true>(M, q, qd, qdd, tau, col, -1, SV{}, fext);
+  } else {
+    rnea_one<T>(M, q, qd, qdd, tau, col);
+    ext_tau<T>(M, q, fext, col, SubFromGlobal<T>{tau, ColT<false>{ld, b}});
+  }
 }
 template <class T>
 __global__ void __launch_bounds__(kBlock, 8) k_aba_ext(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,

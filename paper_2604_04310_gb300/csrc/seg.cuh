@@ -36,14 +36,27 @@ FD SV ez_velprod(const SV& v, float qd) { return qd * SV{mk(v.w.y, -v.w.x, 0.f),
 // ====================================================================== RNEA
 // With EXT, the spatial force fext (body coordinates) is added to the net
 // force of body ext_body, so tau gains J_ext^T fext.
-template <class T, class Img, class C, bool EXT = false>
+// With EXTW, fw holds every body's external spatial force in root-frame
+// Pluecker coordinates ([moment about the root origin; force], 6 rows per
+// body, Algorithm 1's ^0F_ext,i): the outward sweep also carries each body's
+// world rotation R and origin p, and subtracts the force in body coordinates,
+// [R^T (n - p x f); R^T f], from the body's net force, so tau loses
+// sum_i J_i^T F_ext,i in the same sweep.
+template <class T, class Img, class C, bool EXT = false, bool EXTW = false>
 FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restrict__ qd,
                  const float* __restrict__ qdd, float* __restrict__ tau, const C& col, int ext_body = -1,
-                 SV fext = SV{}) {
+                 SV fext = SV{}, const float* __restrict__ fw = nullptr) {
   constexpr int NB = T::NBMAX;
   SV bv[NB], ba[NB], Fa[NB], sf[NB];
   float sc[NB], ss[NB];
+  float bR[EXTW ? NB : 1][9];  // world rotation and origin of bodies with child segments
+  V3 bp[EXTW ? NB : 1];
   const SV ag = gravity_acc(M.g);
+  // body-frame form of an external force given in root-frame coordinates
+  auto ext_in = [&](const float* R, V3 o, int i) {
+    const SV F = load6(fw, 6 * i, col);
+    return SV{rotT(R, F.w - cross(o, F.v)), rotT(R, F.v)};
+  };
 #pragma unroll 1
   for (int t = 0; t < M.n_act; ++t) {
     const int act = M.act[t];
@@ -59,6 +72,14 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
         SV f0 = crf_add(rbi_mul(I, a0), v0, rbi_mul(I, v0));
         if constexpr (EXT) {
           if (ext_body == 0) f0 = f0 + fext;
+        }
+        if constexpr (EXTW) {
+          f0 = f0 - ext_in(P.E, P.r, 0);
+          if (kind == kActOpen) {
+#pragma unroll
+            for (int u = 0; u < 9; ++u) bR[0][u] = P.E[u];
+            bp[0] = P.r;
+          }
         }
         if (kind == kActLeaf) {
           store6(tau, 0, col, f0);
@@ -79,6 +100,13 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
       const int p = M.seg_parent[s];
       SV v = p < 0 ? szero() : bv[p];
       SV a = p < 0 ? ag : ba[p];
+      float R[EXTW ? 9 : 1];
+      V3 o = mk(0, 0, 0);
+      if constexpr (EXTW) {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) R[u] = p < 0 ? ((u % 4 == 0) ? 1.f : 0.f) : bR[p][u];
+        if (p >= 0) o = bp[p];
+      }
 #pragma unroll
       for (int k = 0; k < kMaxSeg; ++k) {
         if (k < len) {
@@ -97,12 +125,29 @@ FD void rnea_seg(const Img& M, const float* __restrict__ q, const float* __restr
           if constexpr (EXT) {
             if (i == ext_body) f[k] = f[k] + fext;
           }
+          if constexpr (EXTW) {  // world pose: R <- R R_b Rot_z(q), o <- o + R p_b
+            float A[9];
+            mat_mul_b(R, b, A, k > 0);
+            o = o + rot(R, mk(b.p[0], b.p[1], b.p[2]));
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              R[3 * r] = fmaf(cc[k], A[3 * r], sn[k] * A[3 * r + 1]);
+              R[3 * r + 1] = fmaf(-sn[k], A[3 * r], cc[k] * A[3 * r + 1]);
+              R[3 * r + 2] = A[3 * r + 2];
+            }
+            f[k] = f[k] - ext_in(R, o, i);
+          }
         }
       }
       if (kind == kActOpen) {
         const int last = M.order[st + len - 1];
         bv[last] = v;
         ba[last] = a;
+        if constexpr (EXTW) {
+#pragma unroll
+          for (int u = 0; u < 9; ++u) bR[last][u] = R[u];
+          bp[last] = o;
+        }
         Fa[last] = szero();
 #pragma unroll
         for (int k = 0; k < kMaxSeg; ++k)

@@ -103,8 +103,8 @@ void run_all(const HostModel& hm, int B, int nf, const int* frames, const float*
       aba_vjp_seg_one<T>(img, q, qd, tau, qdd_a.data(), gbar, aq.data(), aqd.data(), at.data(), col);
       aba_jvp_seg_one<T>(img, q, qd, qdd_a.data(), dq, dqd, dx, dqdd.data(), col);
       fk_jvp_seg<T>(img, q, dq, fr, dpose.data(), col);
-      rnea_seg<T>(img, q, qd, qdd, tau_e.data(), col);
-      ext_tau<T>(img, q, fext, col, SubFromGlobal<T>{tau_e.data(), ColT<false>{B, b}});
+      // as k_rnea_ext: the forces inside RNEA's outward sweep
+      rnea_seg<T, ModelImage<NBI>, Col, false, true>(img, q, qd, qdd, tau_e.data(), col, -1, SV{}, fext);
     }
     // operational-space control of the last frame, task accelerations = the
     // first six rows of dx
