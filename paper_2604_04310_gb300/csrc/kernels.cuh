@@ -141,8 +141,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_osc_seg(const __grid_constant__ M
   osc_seg<T>(M, task, q, qd, xdd, tau, Lam, col);
 }
 
-// External forces. Trees: RNEA takes them inside its own outward sweep;
-// ABA adds tau_ext from one more sweep to its right-hand side.
+// External forces. Trees: RNEA and ABA take them inside their own sweeps
+// (Algorithm 1's body-frame subtraction); per-body-array trees compute
+// tau_ext in one more sweep.
 // RNEA with external forces: 5 blocks per SM (the world pose it carries
 // spills at 64 registers; humanoid 2^18: 152 us against 156 at 8 blocks).
 template <class T>
@@ -163,13 +164,15 @@ __global__ void __launch_bounds__(kBlock, 8) k_aba_ext(const __grid_constant__ M
                                                         int64_t ld, const float* q, const float* qd,
                                                         const float* tau, const float* fext, float* qdd) {
   FRAX_TID();
-  LocalVec<T> w;
-  ext_tau<T>(M, q, fext, col, OutToLocal<T>{&w});
-  const RhsPlusLocal<T, Col> rhs{tau, col, &w};
   if constexpr (T::kSeg) {
+    // the forces enter the bias forces of ABA's own sweeps
     P3Local<T::NBMAX> P;
-    aba_seg_core<T, ModelImage<T::NBMAX>, true>(M, q, qd, rhs, OutToGlobal<T, Col>{qdd, col}, col, P);
+    aba_seg_core<T, ModelImage<T::NBMAX>, true, RhsFromGlobal<T, Col>, OutToGlobal<T, Col>, Col, P3Local<T::NBMAX>,
+                 true>(M, q, qd, RhsFromGlobal<T, Col>{tau, col}, OutToGlobal<T, Col>{qdd, col}, col, P, fext);
   } else {
+    LocalVec<T> w;
+    ext_tau<T>(M, q, fext, col, OutToLocal<T>{&w});
+    const RhsPlusLocal<T, Col> rhs{tau, col, &w};
     aba_core<T, ModelImage<T::NBMAX>, true>(M, q, qd, rhs, OutToGlobal<T, Col>{qdd, col}, col);
   }
 }

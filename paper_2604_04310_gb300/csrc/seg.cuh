@@ -200,12 +200,23 @@ struct P3Local {  // all in thread-local memory
 // occupancy that leaves, measured 22-36 % slower: the shared memory comes out
 // of the L1 that serves the thread-local arrays.)
 
-template <class T, class Img, bool VEL, class Rhs, class Out, class C, class P3>
+// With EXTW (and VEL), fw holds every body's external spatial force in
+// root-frame Pluecker coordinates (6 rows per body, Algorithm 1's ^0F_ext,i):
+// the velocity sweep also carries each body's world rotation and origin, the
+// inward sweep steps them back with the velocity and subtracts the body-frame
+// force from the body's bias force.
+template <class T, class Img, bool VEL, class Rhs, class Out, class C, class P3, bool EXTW = false>
 FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __restrict__ qd, const Rhs& rhs_at,
-                     const Out& out_at, const C& col, P3& P) {
+                     const Out& out_at, const C& col, P3& P, const float* __restrict__ fw = nullptr) {
   constexpr int NB = T::NBMAX;
   SV bv[NB], bA[NB], pAa[NB];
   AI IAa[NB];
+  float bR[EXTW ? NB : 1][9];  // world rotation and origin of segment tips with child segments
+  V3 bp[EXTW ? NB : 1];
+  auto ext_in = [&](const float* R, V3 o, int i) {
+    const SV F = load6(fw, 6 * i, col);
+    return SV{rotT(R, F.w - cross(o, F.v)), rotT(R, F.v)};
+  };
   const SV ag = VEL ? gravity_acc(M.g) : szero();
   V3 gam = mk(0, 0, 0);  // root: E^T (-g)
   AI azero;
@@ -228,11 +239,20 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         bv[0] = VEL ? load6(qd, 0, col) : szero();
         IAa[0] = azero;
         pAa[0] = szero();
+        if constexpr (EXTW) {
+#pragma unroll
+          for (int u = 0; u < 9; ++u) bR[0][u] = RP.E[u];
+          bp[0] = RP.r;
+        }
         if (kind == kActOpen) continue;
       }
       AI IA0 = ai_of(I0);
       ai_add(IA0, IAa[0]);
-      const SV pA0 = VEL ? crf(bv[0], rbi_mul(I0, bv[0])) : szero();
+      SV pA0 = VEL ? crf(bv[0], rbi_mul(I0, bv[0])) : szero();
+      if constexpr (EXTW) {
+        const RootPose RP = root_pose(M, q, col);
+        pA0 = pA0 - ext_in(RP.E, RP.r, 0);
+      }
       const SV a0 = spd6_solve(IA0, rhs_at.root() - (pA0 + pAa[0]));
       out_at.root(a0 - SV{mk(0, 0, 0), gam});
       bA[0] = a0;
@@ -240,9 +260,16 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
     }
     const int last = M.order[st + len - 1];
     SV vtip = szero();
+    float Rt[EXTW ? 9 : 1];  // world pose of the body the inward sweep is at
+    V3 ot = mk(0, 0, 0);
     if (kind != kActClose) {
       const int p = M.seg_parent[s];
       SV vv = (!VEL || p < 0) ? szero() : bv[p];
+      if constexpr (EXTW) {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) Rt[u] = p < 0 ? ((u % 4 == 0) ? 1.f : 0.f) : bR[p][u];
+        if (p >= 0) ot = bp[p];
+      }
       if (VEL) {
         seg_outward(len, M.body[M.order[st]].dh, [&](int k, auto dh) {
           const int i = M.order[st + k];
@@ -251,6 +278,17 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
           joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
           vv = mot_in(b, cs, sn, vv, dh);
           vv.w.z += col.in(qd, iv_of<T>(i));
+          if constexpr (EXTW) {  // R <- R R_b Rot_z(q), o <- o + R p_b
+            float A[9];
+            mat_mul_b(Rt, b, A, dh);
+            ot = ot + rot(Rt, mk(b.p[0], b.p[1], b.p[2]));
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              Rt[3 * r] = fmaf(cs, A[3 * r], sn * A[3 * r + 1]);
+              Rt[3 * r + 1] = fmaf(-sn, A[3 * r], cs * A[3 * r + 1]);
+              Rt[3 * r + 2] = A[3 * r + 2];
+            }
+          }
         });
       }
       vtip = vv;
@@ -258,10 +296,20 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         bv[last] = vv;
         pAa[last] = szero();
         IAa[last] = azero;
+        if constexpr (EXTW) {
+#pragma unroll
+          for (int u = 0; u < 9; ++u) bR[last][u] = Rt[u];
+          bp[last] = ot;
+        }
         continue;
       }
     } else {
       vtip = bv[last];
+      if constexpr (EXTW) {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) Rt[u] = bR[last][u];
+        ot = bp[last];
+      }
     }
     // inward sweep: articulated inertias and bias forces
     AI Ia;
@@ -283,6 +331,7 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
           cb = ez_velprod(vk, qdi);
           pAt = crf(vk, rbi_mul(Ib, vk));
         }
+        if constexpr (EXTW) pAt = pAt - ext_in(Rt, ot, i);
         if (k == len - 1) {
           if (closing) {
             ai_add(IA, IAa[last]);
@@ -312,6 +361,19 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
           SV vp = vk;
           vp.w.z -= col.in(qd, iv_of<T>(i));
           vtip = mot_out(b, ck, sk, vp, dh);
+        }
+        if constexpr (EXTW) {
+          if (k > 0) {  // back to the parent: R <- R Rot_z(q)^T R_b^T, o <- o - R p_b
+            float A[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              A[3 * r] = fmaf(ck, Rt[3 * r], -sk * Rt[3 * r + 1]);
+              A[3 * r + 1] = fmaf(sk, Rt[3 * r], ck * Rt[3 * r + 1]);
+              A[3 * r + 2] = Rt[3 * r + 2];
+            }
+            mat_mul_bT(A, b, Rt, dh);
+            ot = ot - rot(Rt, mk(b.p[0], b.p[1], b.p[2]));
+          }
         }
       }
     });

@@ -177,6 +177,25 @@ FD void mat_mul_b(const float* E, const BodyImage& b, float* C, bool dh = false)
   mat_mul(E, b.R, C);
 }
 
+// C = E R^T (E row-major): the inverse of mat_mul_b's step
+FD void mat_mul_bT(const float* E, const BodyImage& b, float* C, bool dh = false) {
+  if (dh) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float y = E[3 * r + 1], z = E[3 * r + 2];
+      C[3 * r] = E[3 * r];
+      C[3 * r + 1] = fmaf(b.ca, y, -b.sa * z);
+      C[3 * r + 2] = fmaf(b.sa, y, b.ca * z);
+    }
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      C[3 * r + c] = fmaf(E[3 * r], b.R[3 * c], fmaf(E[3 * r + 1], b.R[3 * c + 1], E[3 * r + 2] * b.R[3 * c + 2]));
+}
+
 // --- joint transforms (internal frames) -------------------------------------
 // A revolute body i sits at ^parent'T_i' = (R Rot_z(q + th0), p) with R, p
 // constant; (c, s) below are cos and sin of q + th0.

@@ -112,12 +112,11 @@ void run_all(const HostModel& hm, int B, int nf, const int* frames, const float*
       osc_chain<7>(img, task, q, qd, dx, osc_t.data(), osc_l.data(), col);
     else
       osc_seg<T>(img, task, q, qd, dx, osc_t.data(), osc_l.data(), col);
-    {  // ABA with external forces: right-hand side tau + tau_ext
-      LocalVec<T> w;
-      ext_tau<T>(img, q, fext, col, OutToLocal<T>{&w});
-      const RhsPlusLocal<T, Col> rhs{tau, col, &w};
+    {  // ABA with external forces, as k_aba_ext on trees: the forces in the bias forces of its sweeps
       P3Local<T::NBMAX> P;
-      aba_seg_core<T, ModelImage<NBI>, true>(img, q, qd, rhs, OutToGlobal<T, Col>{qdd_e.data(), col}, col, P);
+      aba_seg_core<T, ModelImage<NBI>, true, RhsFromGlobal<T, Col>, OutToGlobal<T, Col>, Col, P3Local<T::NBMAX>,
+                   true>(img, q, qd, RhsFromGlobal<T, Col>{tau, col}, OutToGlobal<T, Col>{qdd_e.data(), col}, col, P,
+                         fext);
     }
   }
 }
