@@ -254,7 +254,14 @@ FD void fk_jvp_seg(const Img& M, const float* __restrict__ q, const float* __res
   constexpr int NB = T::NBMAX;
   SV bv[NB];
   float bE[NB][9];
+  // bodies that are frames, and segments whose tips have child segments (only
+  // those tips' state is kept)
+  uint64_t frames = 0, opened = 0;
+  for (int f = 0; f < fr.n; ++f) frames |= 1ull << fr.body[f];
+  for (int s = 0; s < M.n_seg; ++s)
+    if (M.seg_parent[s] >= 0) opened |= 1ull << M.seg_of[M.seg_parent[s]];
   auto emit = [&](int i, const float* E, const SV& v) {
+    if (!((frames >> i) & 1ull)) return;
     for (int f = 0; f < fr.n; ++f)
       if (fr.body[f] == i) store6(out, 6 * f, col, SV{rot(E, v.w), rot(E, v.v)});
   };
@@ -275,17 +282,14 @@ FD void fk_jvp_seg(const Img& M, const float* __restrict__ q, const float* __res
     float E[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) E[k] = p < 0 ? ((k % 4 == 0) ? 1.f : 0.f) : bE[p][k];
-#pragma unroll 1
-    for (int k = 0; k < len; ++k) {
+    seg_outward(len, M.body[M.order[st]].dh, [&](int k, auto dh) {
       const int i = M.order[st + k];
       const BodyImage& b = M.body[i];
       float sn, cs;
       joint_sincos(col.in(q, iq_of<T>(i)) + b.th0, &sn, &cs);
       float ER[9];
-      with_dh(b.dh, [&](auto dh) {
-        v = mot_in(b, cs, sn, v, dh);
-        mat_mul_b(E, b, ER, dh);
-      });
+      v = mot_in(b, cs, sn, v, dh);
+      mat_mul_b(E, b, ER, dh);
       v.w.z += col.in(dq, iv_of<T>(i));
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
@@ -295,11 +299,13 @@ FD void fk_jvp_seg(const Img& M, const float* __restrict__ q, const float* __res
         E[3 * r + 2] = ER[3 * r + 2];
       }
       emit(i, E, v);
-    }
-    const int last = M.order[st + len - 1];
-    bv[last] = v;
+    });
+    if ((opened >> s) & 1ull) {
+      const int last = M.order[st + len - 1];
+      bv[last] = v;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) bE[last][k] = E[k];
+      for (int k = 0; k < 9; ++k) bE[last][k] = E[k];
+    }
   }
 }
 
