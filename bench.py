@@ -788,6 +788,28 @@ OUT_OF = {"fk_jac": ("pose", "J"), "rnea": ("tau",), "bias": ("tau",), "crba_ltd
           "rnea_vjp": ("rq", "rqd", "rqdd"), "aba_vjp": ("aq", "aqd", "at")}
 
 
+def copy_ceiling(device, nbytes=1 << 30):
+    """This box's pinned host <-> device copy rates (GB/s, best of three 1 GiB
+    copies each way, CUDA events): the ceiling of a copy-bound end-to-end
+    step."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    out = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        best = 0.0
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dst.copy_(src, non_blocking=True)
+            b.record()
+            torch.cuda.synchronize()
+            best = max(best, nbytes / (a.elapsed_time(b) / 1e3) / 1e9)
+        out[name] = best
+    del h, d
+    return out
+
+
 def e2e_pipeline(fx, model, robot, host, dev, step, device, steps, world, dist):
     import torch
     cs = torch.cuda.current_stream(device)
@@ -840,9 +862,14 @@ def e2e_pipeline(fx, model, robot, host, dev, step, device, steps, world, dist):
     tt = torch.tensor([el], dtype=torch.float64, device=device)
     if world > 1:
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    return {"value": world * len(step.ops) * step.B / float(tt.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    res = {"value": world * len(step.ops) * step.B / float(tt.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": float(tt.item()) * 1e3, "steps": n, "launches": launches,
             "pipelining": "H2D, kernels and per-op D2H on three streams, double-buffered"}
+    ceil = copy_ceiling(device)
+    res["copy_ceiling"] = ceil
+    # the step's D2H bytes at this box's D2H rate: the least time a step can take
+    res["frac_of_copy_ceiling"] = (d2h / (ceil["d2h_gbs"] * 1e9)) / float(tt.item())
+    return res
 
 
 def frax_arm(args, rank, world, local_rank):
