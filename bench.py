@@ -530,12 +530,15 @@ def run_cpu_baseline_all_cores(seconds, robot="chain7"):
 SERVE_OPS = ["rnea", "crba", "aba", "rnea_grad"]
 
 
+SERVE_LOADS = (0.25, 0.5, 0.75, 0.9)
+
+
 def serve_stream(fx, seconds, check_batched=True, repeats=3):
     """Served workload: requests for the 7-DoF chain, the humanoid and 32
     random trees (3-64 bodies), op uniform over rnea / crba / aba /
     rnea-gradient, instance count log-uniform in [1, 4096]. The request
     traces are replayed natively (frax_server_replay): first a burst that
-    gives the saturation rate, then Poisson arrivals at 50 % and 90 % of it,
+    gives the saturation rate, then Poisson arrivals at 25, 50, 75 and 90 % of it,
     each point repeated (p50/p99 per repeat and their medians); latency =
     completion seen by the host - arrival. The server's device error word
     and kernel launch count are reported with the results, and 64 small
@@ -574,7 +577,7 @@ def serve_stream(fx, seconds, check_batched=True, repeats=3):
     sat_req = len(tr) / el
     sat_inst = sum(pool[k][2] for k in ks) / el
     points = []
-    for frac in (0.5, 0.9):
+    for frac in SERVE_LOADS:
         rate = frac * sat_req
         n = int(max(200, rate * seconds))
         reps = []

@@ -14,6 +14,7 @@
 #include <cstddef>
 #include <chrono>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
@@ -265,7 +266,8 @@ struct frax_server_s {
     int64_t in_bytes = 0, out_begin = 0, out_bytes = 0;
     double latency_us = 0;
   };
-  std::mutex mu;
+  std::mutex mu;         // the request table, slab allocator and counters
+  std::mutex submit_mu;  // one submitter at a time (taken before mu)
   int device = 0;
   cudaStream_t kstream = nullptr, cstream = nullptr, dstream = nullptr;
   char* slab = nullptr;
@@ -288,6 +290,10 @@ struct frax_server_s {
   std::map<int64_t, int64_t> free_list;  // offset -> size
   std::map<int64_t, Req> inflight;
   int64_t slot_owner[kRing];
+  bool slot_done[kRing];           // the slot's request has been seen complete
+  int64_t scan_lo = 0;             // no request older than this is in flight and unseen
+  std::deque<int64_t> done_fifo;   // requests seen complete, in the order seen
+  std::chrono::steady_clock::time_point last_query{};  // wait_any's last kernel-state query
   int64_t next_seq = 0, tiles_total = 0;
   int64_t submitted = 0, completed = 0, launches = 0;
   int ctas = 0;
@@ -386,21 +392,61 @@ void release_all(frax_server_s* s) {
 }
 
 // Marks requests whose completion flag is up; returns how many were new.
-int scan_flags(frax_server_s* s, int64_t* first_done) {
+// Reads the completion flags of the requests in flight and not yet seen
+// complete. Those lie in the sequence window [scan_lo, next_seq), at most
+// kRing entries, read from flat per-slot arrays (no walk of the request map);
+// each newly completed request is appended to done_fifo. Returns how many
+// completed since the last scan.
+int scan_flags(frax_server_s* s) {
   int n = 0;
-  for (auto& kv : s->inflight) {
-    auto& r = kv.second;
-    if (r.done) continue;
-    volatile unsigned long long* f = s->flags_h + r.slot;
-    if (*f == static_cast<unsigned long long>(r.seq) + 1ull) {
-      r.done = true;
-      r.latency_us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - r.t0).count();
-      s->completed++;
-      if (n == 0 && first_done) *first_done = r.seq;
-      ++n;
+  const auto now = std::chrono::steady_clock::now();
+  for (int64_t q = s->scan_lo; q < s->next_seq; ++q) {
+    const int slot = static_cast<int>(q % kRing);
+    if (s->slot_owner[slot] != q || s->slot_done[slot]) continue;
+    const volatile unsigned long long* f = s->flags_h + slot;
+    if (*f != static_cast<unsigned long long>(q) + 1ull) continue;
+    s->slot_done[slot] = true;
+    auto it = s->inflight.find(q);
+    if (it != s->inflight.end()) {
+      it->second.done = true;
+      it->second.latency_us = std::chrono::duration<double, std::micro>(now - it->second.t0).count();
     }
+    s->done_fifo.push_back(q);
+    s->completed++;
+    ++n;
+  }
+  while (s->scan_lo < s->next_seq) {
+    const int slot = static_cast<int>(s->scan_lo % kRing);
+    if (s->slot_owner[slot] == s->scan_lo && !s->slot_done[slot]) break;
+    ++s->scan_lo;
   }
   return n;
+}
+
+// The oldest request seen complete and neither collected nor being
+// collected; entries at the front of done_fifo that were collected are
+// dropped on the way.
+bool first_uncollected(frax_server_s* s, int64_t* request) {
+  while (!s->done_fifo.empty()) {
+    auto it = s->inflight.find(s->done_fifo.front());
+    if (it == s->inflight.end()) {
+      s->done_fifo.pop_front();
+      continue;
+    }
+    if (!it->second.collecting) {
+      *request = it->first;
+      return true;
+    }
+    break;
+  }
+  for (int64_t q : s->done_fifo) {  // the front one is being collected
+    auto it = s->inflight.find(q);
+    if (it != s->inflight.end() && !it->second.collecting) {
+      *request = q;
+      return true;
+    }
+  }
+  return false;
 }
 
 }  // namespace
@@ -418,6 +464,7 @@ frax_status frax_server_create(int64_t budget_bytes, double idle_exit_ms, frax_s
   s->budget = round_up(budget_bytes);
   s->idle_ms = idle_exit_ms;
   for (auto& o : s->slot_owner) o = -1;
+  for (auto& d : s->slot_done) d = false;
   auto bail = [&](frax_status st) {
     release_all(s);
     delete s;
@@ -491,33 +538,47 @@ frax_status frax_server_submit(frax_server_t s, int model_id, int op, int64_t B,
                                int64_t* request) {
   if (!s || !request) return set_error(FRAX_EINVAL, "frax_server_submit: NULL argument");
   const auto t_arrive = std::chrono::steady_clock::now();
-  std::lock_guard<std::mutex> lk(s->mu);
-  if (model_id < 0 || model_id >= s->n_models) return set_error(FRAX_EINVAL, "frax_server_submit: bad model_id");
-  if (B < 1 || B > (int64_t(1) << 24)) return set_error(FRAX_EINVAL, "frax_server_submit: B must be in [1, 2^24]");
+  // Submitters run one at a time (requests are published in sequence
+  // order); the server lock is held only to reserve and to register, so the
+  // collecting thread keeps seeing completions while the inputs are copied.
+  std::lock_guard<std::mutex> sub(s->submit_mu);
   int in_rows[4], out_rows[3], nin, nout;
-  if (op_arrays(op, s->model_nq[model_id], s->model_nv[model_id], in_rows, out_rows, &nin, &nout) != 0)
-    return set_error(FRAX_EINVAL, "frax_server_submit: unknown op");
-  if (!inputs) return set_error(FRAX_EINVAL, "frax_server_submit: inputs is NULL");
-  for (int k = 0; k < nin; ++k)
-    if (!inputs[k]) return set_error(FRAX_EINVAL, "frax_server_submit: an input array is NULL");
-  int64_t in_bytes[4], out_bytes[3], total = 0;
-  for (int k = 0; k < nin; ++k) total += (in_bytes[k] = round_up(int64_t(in_rows[k]) * B * 4));
-  for (int k = 0; k < nout; ++k) total += (out_bytes[k] = round_up(int64_t(out_rows[k]) * B * 4));
-  if (total > s->budget) return set_error(FRAX_ENOMEM, "frax_server_submit: request exceeds the whole HBM budget");
-  const int64_t seq = s->next_seq;
+  int64_t in_bytes[4], out_bytes[3], total = 0, off = 0, seq = 0, tile0 = 0, oldest = 0;
+  int kind = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (model_id < 0 || model_id >= s->n_models) return set_error(FRAX_EINVAL, "frax_server_submit: bad model_id");
+    if (B < 1 || B > (int64_t(1) << 24)) return set_error(FRAX_EINVAL, "frax_server_submit: B must be in [1, 2^24]");
+    if (op_arrays(op, s->model_nq[model_id], s->model_nv[model_id], in_rows, out_rows, &nin, &nout) != 0)
+      return set_error(FRAX_EINVAL, "frax_server_submit: unknown op");
+    if (!inputs) return set_error(FRAX_EINVAL, "frax_server_submit: inputs is NULL");
+    for (int k = 0; k < nin; ++k)
+      if (!inputs[k]) return set_error(FRAX_EINVAL, "frax_server_submit: an input array is NULL");
+    for (int k = 0; k < nin; ++k) total += (in_bytes[k] = round_up(int64_t(in_rows[k]) * B * 4));
+    for (int k = 0; k < nout; ++k) total += (out_bytes[k] = round_up(int64_t(out_rows[k]) * B * 4));
+    if (total > s->budget) return set_error(FRAX_ENOMEM, "frax_server_submit: request exceeds the whole HBM budget");
+    seq = s->next_seq;
+    if (s->slot_owner[seq % kRing] >= 0) return set_error(FRAX_EBUSY, "frax_server_submit: request ring full");
+    if (!slab_alloc(s, total, &off)) return set_error(FRAX_EBUSY, "frax_server_submit: HBM budget in use");
+    tile0 = s->tiles_total;
+    kind = s->model_kind[model_id];
+    // the oldest request not yet collected (this one if none): a lower bound
+    // on the owner of any tile the kernel can still claim (requests collected
+    // before the count is published only make it more conservative)
+    oldest = s->inflight.empty() ? seq : std::min(seq, s->inflight.begin()->first);
+  }
+  // The slab range and the ring slot are this request's: no other submitter
+  // runs, and the slot stays free until the request is registered below.
   const int slot = static_cast<int>(seq % kRing);
-  if (s->slot_owner[slot] >= 0) return set_error(FRAX_EBUSY, "frax_server_submit: request ring full");
-  int64_t off;
-  if (!slab_alloc(s, total, &off)) return set_error(FRAX_EBUSY, "frax_server_submit: HBM budget in use");
-  ReqDesc& d = s->desc_stage[slot];
   const int64_t ntiles = (B + kTile - 1) / kTile;
-  d.tile_begin = s->tiles_total;
-  d.tile_end = s->tiles_total + ntiles;
+  ReqDesc& d = s->desc_stage[slot];
+  d.tile_begin = tile0;
+  d.tile_end = tile0 + ntiles;
   d.B = B;
   d.seq = seq;
   d.model_id = model_id;
   d.op = op;
-  d.kind = s->model_kind[model_id];
+  d.kind = kind;
   d.slot = slot;
   int64_t cur = off;
   for (int k = 0; k < 4; ++k) d.in_off[k] = 0;
@@ -531,35 +592,34 @@ frax_status frax_server_submit(frax_server_t s, int model_id, int op, int64_t B,
   r.in_bytes = cur - off;
   r.out_begin = cur;
   r.out_bytes = off + total - cur;
-  // inputs, then the descriptor, then the published-tile count, in stream
-  // order on one copy stream: the kernel can only see the count after both
-  cudaError_t e0 = fault_hit(kFaultSubmitInputCopy)
-                       ? cudaErrorUnknown
-                       : cudaMemcpyAsync(s->slab + off, s->slab_h + off, r.in_bytes, cudaMemcpyHostToDevice,
-                                         s->cstream);
-  if (e0 != cudaSuccess) {
-    slab_free(s, off, total);
-    return cuda_fail("frax_server_submit: input copy", e0);
-  }
   for (int k = 0; k < nout; ++k) {
     d.out_off[k] = cur;
     r.out_off[k] = cur;
     r.out_rows[k] = out_rows[k];
     cur += out_bytes[k];
   }
-  s->pub_stage[slot].tiles_published = static_cast<unsigned long long>(s->tiles_total + ntiles);
-  // the oldest request not yet collected (this one if none): a lower bound
-  // on the owner of any tile the kernel can still claim
-  s->pub_stage[slot].oldest = s->inflight.empty() ? seq : std::min(seq, s->inflight.begin()->first);
-  cudaError_t e = fault_hit(kFaultSubmitPublish)
+  // inputs, then the descriptor, then the published-tile count, in stream
+  // order on one copy stream: the kernel can only see the count after both
+  cudaError_t e = fault_hit(kFaultSubmitInputCopy)
                       ? cudaErrorUnknown
-                      : cudaMemcpyAsync(s->ring + slot, &d, sizeof(ReqDesc), cudaMemcpyHostToDevice, s->cstream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&s->ctl->tiles_published, &s->pub_stage[slot], sizeof(PubStage), cudaMemcpyHostToDevice,
-                        s->cstream);
+                      : cudaMemcpyAsync(s->slab + off, s->slab_h + off, r.in_bytes, cudaMemcpyHostToDevice,
+                                        s->cstream);
+  const char* what = "frax_server_submit: input copy";
+  if (e == cudaSuccess) {
+    what = "frax_server_submit: publish";
+    s->pub_stage[slot].tiles_published = static_cast<unsigned long long>(tile0 + ntiles);
+    s->pub_stage[slot].oldest = oldest;
+    e = fault_hit(kFaultSubmitPublish)
+            ? cudaErrorUnknown
+            : cudaMemcpyAsync(s->ring + slot, &d, sizeof(ReqDesc), cudaMemcpyHostToDevice, s->cstream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&s->ctl->tiles_published, &s->pub_stage[slot], sizeof(PubStage), cudaMemcpyHostToDevice,
+                          s->cstream);
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
   if (e != cudaSuccess) {
     slab_free(s, off, total);
-    return cuda_fail("frax_server_submit: publish", e);
+    return cuda_fail(what, e);
   }
   r.seq = seq;
   r.slot = slot;
@@ -574,6 +634,7 @@ frax_status frax_server_submit(frax_server_t s, int model_id, int op, int64_t B,
   r.t0 = t_arrive;
   s->inflight[seq] = r;
   s->slot_owner[slot] = seq;
+  s->slot_done[slot] = false;
   s->tiles_total += ntiles;
   s->next_seq++;
   s->submitted++;
@@ -588,7 +649,7 @@ frax_status frax_server_poll(frax_server_t s, int64_t request, int* done) {
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->inflight.find(request);
   if (it == s->inflight.end()) return set_error(FRAX_EINVAL, "frax_server_poll: unknown request");
-  scan_flags(s, nullptr);
+  scan_flags(s);
   if (*s->status_h) return set_error(FRAX_EINTERNAL, "frax_server_poll: device error " + std::to_string(*s->status_h));
   *done = it->second.done ? 1 : 0;
   if (!*done) {
@@ -604,22 +665,20 @@ frax_status frax_server_wait_any(frax_server_t s, double timeout_ms, int64_t* re
   while (true) {
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      // a request already seen complete but not collected
-      for (auto& kv : s->inflight)
-        if (kv.second.done) {
-          *request = kv.first;
-          return clear_error();
-        }
+      if (first_uncollected(s, request)) return clear_error();  // seen complete earlier
       if (s->inflight.empty()) return set_error(FRAX_EINVAL, "frax_server_wait_any: nothing in flight");
-      int64_t first = -1;
-      if (scan_flags(s, &first) > 0) {
-        *request = first;
-        return clear_error();
-      }
+      if (scan_flags(s) > 0 && first_uncollected(s, request)) return clear_error();
       if (*s->status_h)
         return set_error(FRAX_EINTERNAL, "frax_server_wait_any: device error " + std::to_string(*s->status_h));
-      frax_status st = ensure_running(s);
-      if (st != FRAX_OK) return st;
+      // The kernel leaves only after idle_exit_ms without a claim and every
+      // submit checks it, so while waiting its state is queried at most once
+      // every 20 us (each query takes the driver's lock).
+      const auto now = std::chrono::steady_clock::now();
+      if (now - s->last_query > std::chrono::microseconds(20)) {
+        s->last_query = now;
+        frax_status st = ensure_running(s);
+        if (st != FRAX_OK) return st;
+      }
     }
     if (std::chrono::steady_clock::now() > t_end)
       return set_error(FRAX_ETIMEOUT, "frax_server_wait_any: no request completed within the timeout");
@@ -634,7 +693,7 @@ frax_status frax_server_collect(frax_server_t s, int64_t request, float* const* 
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->inflight.find(request);
     if (it == s->inflight.end()) return set_error(FRAX_EINVAL, "frax_server_collect: unknown request");
-    scan_flags(s, nullptr);
+    scan_flags(s);
     if (!it->second.done) return set_error(FRAX_EBUSY, "frax_server_collect: request not complete");
     if (it->second.collecting) return set_error(FRAX_EBUSY, "frax_server_collect: already being collected");
     it->second.collecting = true;
@@ -662,7 +721,7 @@ frax_status frax_server_collect(frax_server_t s, int64_t request, float* const* 
 frax_status frax_server_info(frax_server_t s, frax_server_info_t* info) {
   if (!s || !info) return set_error(FRAX_EINVAL, "frax_server_info: NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
-  scan_flags(s, nullptr);
+  scan_flags(s);
   info->budget_bytes = s->budget;
   info->bytes_in_use = s->in_use;
   info->submitted = s->submitted;
@@ -677,8 +736,9 @@ frax_status frax_server_info(frax_server_t s, frax_server_info_t* info) {
 frax_status frax_server_destroy(frax_server_t s, int force, double timeout_ms) {
   if (!s) return clear_error();
   {
+    std::lock_guard<std::mutex> sub(s->submit_mu);  // a submit under way finishes first
     std::lock_guard<std::mutex> lk(s->mu);
-    scan_flags(s, nullptr);
+    scan_flags(s);
     bool pending = false;
     for (auto& kv : s->inflight) pending = pending || !kv.second.done;
     if (pending && !force) return set_error(FRAX_EBUSY, "frax_server_destroy: requests still in flight");
@@ -710,11 +770,16 @@ frax_status frax_server_replay(frax_server_t s, int n, const int* model_id, cons
   std::atomic<int> collected{0};
   std::atomic<int> failure{0};
   std::string fail_msg;
+  auto fail = [&](int st, const char* msg) {  // the first failure wins
+    std::lock_guard<std::mutex> lk(mu);
+    int expect = 0;
+    if (failure.compare_exchange_strong(expect, st)) fail_msg = msg ? msg : "";
+  };
   auto at = [&](int k) { return t0 + std::chrono::nanoseconds(int64_t(arrival_us[k] * 1e3)); };
   std::thread collector([&]() {
     while (collected.load() < n && failure.load() == 0) {
       if (clk::now() > t_end) {
-        failure = FRAX_ETIMEOUT;
+        fail(FRAX_ETIMEOUT, nullptr);
         break;
       }
       int64_t r;
@@ -724,8 +789,7 @@ frax_status frax_server_replay(frax_server_t s, int n, const int* model_id, cons
         continue;
       }
       if (st != FRAX_OK) {
-        failure = st;
-        fail_msg = frax_last_error();
+        fail(st, frax_last_error());
         break;
       }
       const auto seen = clk::now();
@@ -735,12 +799,14 @@ frax_status frax_server_replay(frax_server_t s, int n, const int* model_id, cons
         auto it = index.find(r);
         if (it != index.end()) k = it->second;
       }
-      if (k < 0) continue;  // published but not yet recorded by the submitter
+      if (k < 0) {  // submitted, not yet recorded by the submitting thread
+        std::this_thread::yield();
+        continue;
+      }
       latency_us[k] = std::chrono::duration<double, std::micro>(seen - at(k)).count();
       st = frax_server_collect(s, r, outputs ? outputs + 3 * size_t(k) : nullptr, nullptr);
       if (st != FRAX_OK) {
-        failure = st;
-        fail_msg = frax_last_error();
+        fail(st, frax_last_error());
         break;
       }
       collected++;
@@ -750,20 +816,18 @@ frax_status frax_server_replay(frax_server_t s, int n, const int* model_id, cons
     while (clk::now() < at(k)) std::this_thread::yield();
     while (true) {
       int64_t r;
-      std::unique_lock<std::mutex> lk(mu);
       frax_status st = frax_server_submit(s, model_id[k], op[k], B[k], inputs + 4 * size_t(k), &r);
       if (st == FRAX_OK) {
+        std::lock_guard<std::mutex> lk(mu);
         index[r] = k;
         break;
       }
-      lk.unlock();
       if (st != FRAX_EBUSY) {
-        failure = st;
-        fail_msg = frax_last_error();
+        fail(st, frax_last_error());
         break;
       }
       if (clk::now() > t_end) {
-        failure = FRAX_ETIMEOUT;
+        fail(FRAX_ETIMEOUT, nullptr);
         break;
       }
       std::this_thread::yield();
