@@ -276,3 +276,87 @@ def test_long_mixed_replay_with_relaunches():
         for o, ref in zip(outs[j], _oracle(ROBOTS[k], op, s_, g_)):
             assert normwise(gen.from_soa(o, Bj), ref) < _tol(ROBOTS[k], op)
     srv.close()
+
+
+def test_concurrent_submitters_and_collector(server):
+    """Four threads submit at once (submit copies the inputs and publishes
+    outside the server lock, one submitter at a time) while a fifth collects
+    with wait_any: every request completes, its outputs are bit-identical to
+    the same request served alone, and nothing stays in flight or reserved."""
+    import threading
+
+    srv, ids = server
+    rng = np.random.default_rng(11)
+    pool = []
+    for j in range(12):
+        k = j % len(ROBOTS)
+        op = ["rnea", "crba", "aba", "rnea_grad"][j % 4]
+        Bj = int(rng.integers(1, 300)) if ROBOTS[k].n_bodies < 64 else int(rng.integers(1, 64))
+        _, _, inp = _inputs(ROBOTS[k], op, Bj, 2000 + j)
+        alone, _ = _run(srv, ids[k], op, inp, Bj)
+        pool.append((ids[k], op, Bj, inp, alone))
+    n_threads, per_thread = 4, 120
+    total = n_threads * per_thread
+    owner = {}  # request -> pool index
+    lock = threading.Lock()
+    errors = []
+    done = []
+
+    def submitter(t):
+        try:
+            r = np.random.default_rng(100 + t)
+            for _ in range(per_thread):
+                p = int(r.integers(len(pool)))
+                mid, op, Bj, inp, _ = pool[p]
+                deadline = time.time() + 30.0
+                while True:
+                    req = srv.submit(mid, op, inp, Bj)
+                    if req is not None:
+                        break
+                    assert time.time() < deadline, "server stayed busy"
+                    time.sleep(1e-4)
+                with lock:
+                    owner[req] = p
+        except Exception as e:  # reported by the main thread
+            errors.append(e)
+
+    def collector():
+        try:
+            deadline = time.time() + 60.0
+            while len(done) < total:
+                assert time.time() < deadline, "requests did not complete"
+                try:
+                    r = srv.wait_any(5.0)
+                except fx.FraxError as e:
+                    if e.status != 1:  # FRAX_EINVAL: nothing in flight yet
+                        raise
+                    time.sleep(1e-4)
+                    continue
+                if r is None:
+                    continue
+                with lock:
+                    p = owner.get(r)
+                if p is None:  # submitted, not yet recorded by its thread
+                    time.sleep(1e-5)
+                    continue
+                mid, op, Bj, _, alone = pool[p]
+                outs, _ = srv.collect(r, mid, op, Bj)
+                done.append((p, outs))
+        except Exception as e:
+            errors.append(e)
+
+    threads = [threading.Thread(target=submitter, args=(t,)) for t in range(n_threads)]
+    col = threading.Thread(target=collector)
+    col.start()
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    col.join()
+    assert not errors, errors
+    assert len(done) == total
+    for p, outs in done:
+        for a, b in zip(outs, pool[p][4]):
+            assert np.array_equal(a, b)
+    info = srv.info()
+    assert info["in_flight"] == 0 and info["bytes_in_use"] == 0 and info["device_status"] == 0
