@@ -540,7 +540,9 @@ def serve_stream(fx, seconds, check_batched=True, repeats=3):
     traces are replayed natively (frax_server_replay): first a burst that
     gives the saturation rate, then Poisson arrivals at 25, 50, 75 and 90 % of it,
     each point repeated (p50/p99 per repeat and their medians); latency =
-    completion seen by the host - arrival. The server's device error word
+    completion seen by the host - arrival. Every pool request is also timed
+    alone, so each point reports how long requests waited beyond their solo
+    latency, and a one-instance chain request alone gives the latency floor. The server's device error word
     and kernel launch count are reported with the results, and 64 small
     served requests are compared with the batched entry points."""
     import numpy as np
@@ -569,6 +571,17 @@ def serve_stream(fx, seconds, check_batched=True, repeats=3):
         ks = trace_rng.integers(len(pool), size=n)
         return ks, [(ids[pool[k][0]], pool[k][1], pool[k][3]) for k in ks]
 
+    # latency of every pool request alone (3 ms apart, nothing queues; the
+    # smaller of two passes), and the floor: a one-instance chain RNEA
+    solo_tr = [(ids[p[0]], p[1], p[3]) for p in pool]
+    lat_a, _ = srv.replay(solo_tr + solo_tr, np.arange(2 * len(pool)) * 3000.0)
+    solo = np.minimum(lat_a[:len(pool)], lat_a[len(pool):])
+    st1 = gen.draw_states(robots[0], 1, 49999).as_f32()
+    one = [gen.to_soa(a) for a in (st1.q, st1.qd, st1.qdd)]
+    lat_f, _ = srv.replay([(ids[0], "rnea", one)] * 200, np.arange(200) * 200.0)
+    floor = {"request": "chain7 rnea, 1 instance, alone (200 requests 200 us apart)",
+             "p50_us": float(np.percentile(lat_f, 50)), "p99_us": float(np.percentile(lat_f, 99))}
+
     # saturation: everything arrives at once
     ks, tr = trace(3000)
     t0 = time.perf_counter()
@@ -587,13 +600,18 @@ def serve_stream(fx, seconds, check_batched=True, repeats=3):
             t0 = time.perf_counter()
             lat, _ = srv.replay(tr, arrival)
             el = time.perf_counter() - t0
+            wait = lat - solo[ks]  # beyond the same request's solo latency
             reps.append({"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                         "wait_beyond_solo_p50_us": float(np.percentile(wait, 50)),
+                         "wait_beyond_solo_p99_us": float(np.percentile(wait, 99)),
                          "mean_us": float(lat.mean()), "max_us": float(lat.max()),
                          "evals_per_s": sum(pool[k][2] for k in ks) / el,
                          "device_status": srv.info()["device_status"]})
         points.append({"load": frac, "offered_rate_hz": rate, "requests_per_repeat": n, "repeats": reps,
                        "p50_us": statistics.median(r["p50_us"] for r in reps),
                        "p99_us": statistics.median(r["p99_us"] for r in reps),
+                       "wait_beyond_solo_p50_us": statistics.median(r["wait_beyond_solo_p50_us"] for r in reps),
+                       "wait_beyond_solo_p99_us": statistics.median(r["wait_beyond_solo_p99_us"] for r in reps),
                        "evals_per_s": statistics.median(r["evals_per_s"] for r in reps)})
     # served results against the library's batched entry points on the same
     # inputs (those are pinned to the FP64 oracle by the parity tests)
@@ -621,6 +639,11 @@ def serve_stream(fx, seconds, check_batched=True, repeats=3):
                         "rnea-gradient uniform, 1-4096 instances log-uniform; replayed natively; latency = "
                         "host-seen completion - arrival",
             "saturation_req_per_s": sat_req, "saturation_evals_per_s": sat_inst, "points": points,
+            "latency_floor": floor,
+            "solo": {"what": "each of the 256 pool requests alone", "p50_us": float(np.percentile(solo, 50)),
+                     "p99_us": float(np.percentile(solo, 99)),
+                     "p50_by_op_us": {op: float(np.median([solo[k] for k in range(len(pool)) if pool[k][1] == op]))
+                                      for op in SERVE_OPS}},
             "max_rel_diff_vs_batched": diff, "checked_requests": checked,
             "kernel_launches": info["kernel_launches"], "resident_ctas": info["resident_ctas"],
             "device_status": info["device_status"], "completed": info["completed"],
