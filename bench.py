@@ -45,7 +45,9 @@ FP32_LANES_PER_SM = 128
 # state by stepping back through the joints; the tree ABA recomputes
 # velocities; the tree factor comes from articulated inertias) the table
 # keeps the count of the direct formulation that stores instead, so the
-# roofline is against the algorithm's work, not the kernel's extra work. The
+# roofline is against the algorithm's work, not the kernel's extra work.
+# Articulated inertias are counted with the zeros of their projection
+# (I^A - U U^T / D annihilates e_z) skipped, as every kernel skips them. The
 # chain ABA adjoint = its M^-1 solve through the mass-matrix factor (1677)
 # plus the stored-state RNEA adjoint (4272); the chain's forward dynamics
 # go through the same factor, RNEA bias (1683) + solve (1677) = 3360
@@ -56,11 +58,11 @@ FP32_LANES_PER_SM = 128
 # plain kernel's count plus the force sweep's (554 chain, 2585 humanoid).
 FLOPS = {
     "chain7": {"fk_jac": 748, "fk": 664, "rnea": 1683, "bias": 1683, "crba_ltdl": 1586, "crba": 1453,
-               "aba": 3360, "aba_sweep": 4073, "rnea_vjp": 4272, "aba_vjp": 5949, "osc": 8219, "rnea_ext": 2237,
+               "aba": 3360, "aba_sweep": 3431, "rnea_vjp": 4272, "aba_vjp": 5949, "osc": 7730, "rnea_ext": 2237,
                "aba_ext": 3914, "fk_jvp": 593, "rnea_jvp": 4175, "aba_jvp": 5859},
     "humanoid": {"fk_jac": 4685, "fk": 3173, "rnea": 7761, "bias": 7755, "crba_ltdl": 13474, "crba": 9704,
-                 "aba": 20322, "aba_sweep": 20322, "rnea_vjp": 19471, "aba_vjp": 36261, "osc": 24675, "rnea_ext": 10346,
-                 "aba_ext": 22907, "fk_jvp": 2584, "rnea_jvp": 17866, "aba_jvp": 34310},
+                 "aba": 17399, "aba_sweep": 17399, "rnea_vjp": 19471, "aba_vjp": 32178, "osc": 22680, "rnea_ext": 10346,
+                 "aba_ext": 19984, "fk_jvp": 2584, "rnea_jvp": 17866, "aba_jvp": 30662},
 }
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # chain step's kernels, from one `ncu --set full` capture of this bench's

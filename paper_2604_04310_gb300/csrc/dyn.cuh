@@ -508,9 +508,10 @@ FD void aba_core(const Img& M, const float* __restrict__ q, const float* __restr
     const int k = T::parent(M, i);
     if (k >= 0) {
       AI Ia = IA[i];
-      ai_rank1_sub(Ia, Ui, di);
-      const SV pa = pA[i] + ai_mul(Ia, cb[i]) + (ui * di) * Ui;
-      ai_out(M.body[i], cq[i], sq[i], Ia, dh_of<T>(M, i));
+      ai_rank1_sub_z(Ia, Ui, di);
+      SV pa = axpy(ui * di, Ui, pA[i]);
+      if (VEL) pa = ai_mul_z_add(pa, Ia, cb[i]);
+      ai_out_z(M.body[i], cq[i], sq[i], Ia, dh_of<T>(M, i));
       ai_add(IA[k], Ia);
       pA[k] = pA[k] + frc_out(M.body[i], cq[i], sq[i], pa, dh_of<T>(M, i));
     }

@@ -239,11 +239,11 @@ struct AbaLg {
     S[P0() + 6 * i + 4] = Ud.v.z;
     S[P0() + 6 * i + 5] = ud;
     Ia = IA;
-    ai_rank1_sub_d(Ia, Ud, U);
-    if (VEL) pa = pA + ai_mul(Ia, ez_velprod(vi, col.in(qd, iv_of<T>(i)))) + ud * U;
-    else pa = pA + ud * U;  // children's bias contributions, no velocity products
+    ai_rank1_sub_d_z(Ia, Ud, U);
+    pa = axpy(ud, U, pA);
+    if (VEL) pa = ai_mul_z_add(pa, Ia, ez_velprod(vi, col.in(qd, iv_of<T>(i))));
     with_dh(bi.dh, [&](auto dh) {
-      ai_out(bi, cs, sn, Ia, dh);
+      ai_out_z(bi, cs, sn, Ia, dh);
       pa = frc_out(bi, cs, sn, pa, dh);
     });
     if (fl & kLgStoreIn) {
@@ -502,11 +502,11 @@ struct CrbaLg {
     const float dinv = rcp(U.w.z);
     if (LD) putL(di, di, U.w.z);
     crba_emit_row<T, ModelImage<32>, C, false, 3>(M, i, FM, dinv * U, Mout, LD, SinCos{S, CS(), SN()}, col);
-    ai_rank1_sub(IAi, U, dinv);
+    ai_rank1_sub_z(IAi, U, dinv);
     const float cs = S[CS() + i], sn = S[SN() + i];
     with_dh(b.dh, [&](auto dh) {
       Cc = rbi_out(b, cs, sn, Ci, dh);
-      ai_out(b, cs, sn, IAi, dh);
+      ai_out_z(b, cs, sn, IAi, dh);
     });
     Ia = IAi;
     if (fl & kLgStoreIn) {

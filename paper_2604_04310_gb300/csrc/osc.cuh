@@ -144,8 +144,8 @@ FD AI osc_inertias(const Img& M, const float* __restrict__ q, uint64_t path, PL&
         P.at(i, 3) = U.v.x; P.at(i, 4) = U.v.y; P.at(i, 5) = U.v.z;
         P.at(i, 6) = dinv;
       }
-      ai_rank1_sub(IA, U, dinv);
-      with_dh(b.dh, [&](auto dh) { ai_out(b, cs, sn, IA, dh); });
+      ai_rank1_sub_z(IA, U, dinv);
+      with_dh(b.dh, [&](auto dh) { ai_out_z(b, cs, sn, IA, dh); });
       if (k > 0) {
         AI Ip = ai_of(rbi_of(M.body[M.order[st + k - 1]]));
         ai_add(Ip, IA);
@@ -318,8 +318,8 @@ FD void osc_chain(const Img& M, int task, const float* __restrict__ q, const flo
     IA = Ik;
     U[k] = ai_col_z(IA);
     dinv[k] = rcp(U[k].w.z);
-    ai_rank1_sub(IA, U[k], dinv[k]);
-    ai_out(b, cs[k], sn[k], IA, k > 0);
+    ai_rank1_sub_z(IA, U[k], dinv[k]);
+    ai_out_z(b, cs[k], sn[k], IA, k > 0);
   }
   // sweep 2: outward along bodies 0 .. task
   OscPath o;

@@ -353,9 +353,10 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         P.put(i, 4, Ud.v.z);
         P.put(i, 5, ud);
         Ia = IA;
-        ai_rank1_sub_d(Ia, Ud, U);
-        pa = pAt + ai_mul(Ia, cb) + ud * U;
-        ai_out(b, ck, sk, Ia, dh);
+        ai_rank1_sub_d_z(Ia, Ud, U);
+        pa = axpy(ud, U, pAt);
+        if (VEL) pa = ai_mul_z_add(pa, Ia, cb);
+        ai_out_z(b, ck, sk, Ia, dh);
         pa = frc_out(b, ck, sk, pa, dh);
         if (VEL && k > 0) {
           SV vp = vk;
@@ -624,8 +625,8 @@ FD void crba_seg(const Img& M, const float* __restrict__ q, float* __restrict__ 
           putL(di, di, U.w.z);
           FL = dinv * U;
           Ia = IA;
-          ai_rank1_sub(Ia, U, dinv);
-          ai_out(b, sc[i], ss[i], Ia);
+          ai_rank1_sub_z(Ia, U, dinv);
+          ai_out_z(b, sc[i], ss[i], Ia);
         }
         crba_emit_row<T, Img, C, ZEROS, OUT>(M, i, FM, FL, Mout, LD, SinCosArrays{sc, ss}, col);
         const RBI Ip = rbi_of(M.body[M.order[st + (k > 0 ? k - 1 : 0)]]);

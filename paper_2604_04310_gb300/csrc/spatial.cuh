@@ -73,6 +73,11 @@ FD SV operator-(const SV& a, const SV& b) { return SV{a.w - b.w, a.v - b.v}; }
 FD SV operator*(float s, const SV& a) { return SV{s * a.w, s * a.v}; }
 FD float dot(const SV& a, const SV& b) { return dot(a.w, b.w) + dot(a.v, b.v); }
 FD SV szero() { return SV{mk(0, 0, 0), mk(0, 0, 0)}; }
+// s x + y with every component one FMA (no contraction left to the compiler)
+FD SV axpy(float s, const SV& x, const SV& y) {
+  return SV{mk(fmaf(s, x.w.x, y.w.x), fmaf(s, x.w.y, y.w.y), fmaf(s, x.w.z, y.w.z)),
+            mk(fmaf(s, x.v.x, y.v.x), fmaf(s, x.v.y, y.v.y), fmaf(s, x.v.z, y.v.z))};
+}
 
 // motion x motion (Table III's x); sums of cross products as FMA chains
 FD SV crm(const SV& a, const SV& b) { return SV{cross(a.w, b.w), cross_add(cross(a.w, b.v), a.v, b.w)}; }
@@ -418,36 +423,6 @@ FD void ai_add(AI& a, const AI& b) {
 }
 // column z of the angular part: I e_z = [A[:,2]; B[2,:]^T]
 FD SV ai_col_z(const AI& I) { return SV{mk(I.A[4], I.A[5], I.A[2]), mk(I.B[6], I.B[7], I.B[8])}; }
-// I -= u u^T * k
-// I -= d u^T for d = k u given (the ABA's U / D): no scaling left to do
-FD void ai_rank1_sub_d(AI& I, const SV& d, const SV& u) {
-  const float a[6] = {u.w.x, u.w.y, u.w.z, u.v.x, u.v.y, u.v.z};
-  const float e[6] = {d.w.x, d.w.y, d.w.z, d.v.x, d.v.y, d.v.z};
-  const int si[6] = {0, 1, 2, 0, 0, 1}, sj[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    I.A[t] = fmaf(-e[si[t]], a[sj[t]], I.A[t]);
-    I.C[t] = fmaf(-e[3 + si[t]], a[3 + sj[t]], I.C[t]);
-  }
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) I.B[3 * r + c] = fmaf(-e[r], a[3 + c], I.B[3 * r + c]);
-}
-
-FD void ai_rank1_sub(AI& I, const SV& u, float k) {
-  float a[6] = {u.w.x, u.w.y, u.w.z, u.v.x, u.v.y, u.v.z};
-  const int si[6] = {0, 1, 2, 0, 0, 1}, sj[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-  for (int t = 0; t < 6; ++t) {
-    I.A[t] = fmaf(-k * a[si[t]], a[sj[t]], I.A[t]);
-    I.C[t] = fmaf(-k * a[3 + si[t]], a[3 + sj[t]], I.C[t]);
-  }
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) I.B[3 * r + c] = fmaf(-k * a[r], a[3 + c], I.B[3 * r + c]);
-}
 // Shift of a symmetric force-space tensor to a frame whose origin sits at
 // -p: C' = C, B' = B + P C, A' = A - (Y P + (Y P)^T), P = [p]x, Y = B + P C / 2.
 FD void ai_shift(const V3& p, AI& I) {
@@ -485,6 +460,91 @@ FD void ai_in(const BodyImage& b, float c, float s, AI& I, bool dh = false) {
   sym_rotT_b(b, I.A, dh); sym_rotz(c, -s, I.A);
   sym_rotT_b(b, I.C, dh); sym_rotz(c, -s, I.C);
   gen_rotT_b(b, I.B, dh); gen_rotz(c, -s, I.B);
+}
+
+// --- the projected articulated inertia Ia = I^A - U U^T / D ------------------
+// With U = I^A e_z and D = U_z, Ia e_z = U - U = 0: the z row and column of A
+// and the z row of B vanish, leaving 15 free entries. The _z forms below set
+// those entries to zero and skip their arithmetic in the projection, in the
+// product with a velocity product v x e_z qd (whose z components vanish too)
+// and in the congruence to the parent's coordinates.
+
+// I -= d u^T with d = U / D (so d_z = 1), leaving the zeros exact
+FD void ai_rank1_sub_d_z(AI& I, const SV& d, const SV& u) {
+  const float a[6] = {u.w.x, u.w.y, u.w.z, u.v.x, u.v.y, u.v.z};
+  const float e[6] = {d.w.x, d.w.y, d.w.z, d.v.x, d.v.y, d.v.z};
+  I.A[0] = fmaf(-e[0], a[0], I.A[0]);
+  I.A[1] = fmaf(-e[1], a[1], I.A[1]);
+  I.A[3] = fmaf(-e[0], a[1], I.A[3]);
+  I.A[2] = 0.f; I.A[4] = 0.f; I.A[5] = 0.f;
+  const int si[6] = {0, 1, 2, 0, 0, 1}, sj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int t = 0; t < 6; ++t) I.C[t] = fmaf(-e[3 + si[t]], a[3 + sj[t]], I.C[t]);
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) I.B[3 * r + c] = fmaf(-e[r], a[3 + c], I.B[3 * r + c]);
+  I.B[6] = 0.f; I.B[7] = 0.f; I.B[8] = 0.f;
+}
+// I -= k u u^T with k = 1 / u_z, leaving the zeros exact
+FD void ai_rank1_sub_z(AI& I, const SV& u, float k) {
+  SV d = k * u;
+  d.w.z = 1.f;
+  ai_rank1_sub_d_z(I, d, u);
+}
+// acc + Ia m for m with m.w.z = m.v.z = 0 (a velocity product v x e_z qd)
+FD SV ai_mul_z_add(const SV& acc, const AI& I, const SV& m) {
+  const float wx = m.w.x, wy = m.w.y, vx = m.v.x, vy = m.v.y;
+  const V3 n = mk(fmaf(I.A[0], wx, fmaf(I.A[3], wy, fmaf(I.B[0], vx, fmaf(I.B[1], vy, acc.w.x)))),
+                  fmaf(I.A[3], wx, fmaf(I.A[1], wy, fmaf(I.B[3], vx, fmaf(I.B[4], vy, acc.w.y)))), acc.w.z);
+  const V3 f = mk(fmaf(I.B[0], wx, fmaf(I.B[3], wy, fmaf(I.C[0], vx, fmaf(I.C[3], vy, acc.v.x)))),
+                  fmaf(I.B[1], wx, fmaf(I.B[4], wy, fmaf(I.C[3], vx, fmaf(I.C[1], vy, acc.v.y)))),
+                  fmaf(I.B[2], wx, fmaf(I.B[5], wy, fmaf(I.C[4], vx, fmaf(I.C[5], vy, acc.v.z)))));
+  return SV{n, f};
+}
+// ai_out (below) for Ia: the rotation by Rot_z(q) keeps the zeros, a Rot_x
+// rotation (dh) fills them from the non-zero entries alone
+FD void ai_out_z(const BodyImage& b, float c, float s, AI& I, bool dh = false) {
+  {  // A: only xx, yy, xy are non-zero
+    const float xx = I.A[0], yy = I.A[1], xy = I.A[3];
+    const float cc = c * c, ss = s * s, cs = c * s;
+    I.A[0] = fmaf(cc, xx, fmaf(-2.f * cs, xy, ss * yy));
+    I.A[1] = fmaf(ss, xx, fmaf(2.f * cs, xy, cc * yy));
+    I.A[3] = fmaf(cs, xx - yy, (cc - ss) * xy);
+  }
+  sym_rotz(c, s, I.C);
+  {  // B: row z is zero
+    const float a0 = fmaf(c, I.B[0], -s * I.B[3]), a1 = fmaf(c, I.B[1], -s * I.B[4]);
+    const float a2 = fmaf(c, I.B[2], -s * I.B[5]);
+    const float b0 = fmaf(s, I.B[0], c * I.B[3]), b1 = fmaf(s, I.B[1], c * I.B[4]);
+    const float b2 = fmaf(s, I.B[2], c * I.B[5]);
+    I.B[0] = fmaf(c, a0, -s * a1); I.B[1] = fmaf(s, a0, c * a1); I.B[2] = a2;
+    I.B[3] = fmaf(c, b0, -s * b1); I.B[4] = fmaf(s, b0, c * b1); I.B[5] = b2;
+  }
+  if (dh) {
+    const float ca = b.ca, sa = b.sa;
+    {  // A: Rot_x with zz = xz = yz = 0
+      const float yy = I.A[1], xy = I.A[3];
+      I.A[1] = (ca * ca) * yy;
+      I.A[2] = (sa * sa) * yy;
+      I.A[5] = (ca * sa) * yy;
+      I.A[3] = ca * xy;
+      I.A[4] = sa * xy;
+    }
+    sym_rotx(ca, sa, I.C);
+    {  // B: Rot_x B Rot_x^T with row z zero
+      const float m0 = I.B[0], m1 = I.B[1], m2 = I.B[2], m3 = I.B[3], m4 = I.B[4], m5 = I.B[5];
+      const float t1 = fmaf(ca, m4, -sa * m5), t2 = fmaf(sa, m4, ca * m5);
+      I.B[0] = m0; I.B[1] = fmaf(ca, m1, -sa * m2); I.B[2] = fmaf(sa, m1, ca * m2);
+      I.B[3] = ca * m3; I.B[4] = ca * t1; I.B[5] = ca * t2;
+      I.B[6] = sa * m3; I.B[7] = sa * t1; I.B[8] = sa * t2;
+    }
+  } else {
+    sym_rot(b.R, I.A);
+    sym_rot(b.R, I.C);
+    gen_rot(b.R, I.B);
+  }
+  ai_shift(mk(b.p[0], b.p[1], b.p[2]), I);
 }
 
 }  // namespace frax
