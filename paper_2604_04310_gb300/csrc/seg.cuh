@@ -219,12 +219,10 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
   };
   const SV ag = VEL ? gravity_acc(M.g) : szero();
   V3 gam = mk(0, 0, 0);  // root: E^T (-g)
-  AI azero;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) { azero.A[k] = 0.f; azero.C[k] = 0.f; }
-#pragma unroll
-  for (int k = 0; k < 9; ++k) azero.B[k] = 0.f;
   uint64_t opened = 0;  // segments with child segments: their tips' accelerations are kept
+  // bodies whose IAa / pAa hold a child segment's contribution: the first
+  // contribution is stored, later ones added (no zero fill, no read of zeros)
+  uint64_t acc = 0;
 #pragma unroll 1
   for (int t = 0; t < M.n_act; ++t) {
     const int act = M.act[t];
@@ -237,8 +235,6 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         const RootPose RP = root_pose(M, q, col);
         gam = rotT(RP.E, ag.v);
         bv[0] = VEL ? load6(qd, 0, col) : szero();
-        IAa[0] = azero;
-        pAa[0] = szero();
         if constexpr (EXTW) {
 #pragma unroll
           for (int u = 0; u < 9; ++u) bR[0][u] = RP.E[u];
@@ -247,13 +243,17 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         if (kind == kActOpen) continue;
       }
       AI IA0 = ai_of(I0);
-      ai_add(IA0, IAa[0]);
+      SV pAc = szero();
+      if (acc & 1ull) {
+        ai_add(IA0, IAa[0]);
+        pAc = pAa[0];
+      }
       SV pA0 = VEL ? crf(bv[0], rbi_mul(I0, bv[0])) : szero();
       if constexpr (EXTW) {
         const RootPose RP = root_pose(M, q, col);
         pA0 = pA0 - ext_in(RP.E, RP.r, 0);
       }
-      const SV a0 = spd6_solve(IA0, rhs_at.root() - (pA0 + pAa[0]));
+      const SV a0 = spd6_solve(IA0, rhs_at.root() - (pA0 + pAc));
       out_at.root(a0 - SV{mk(0, 0, 0), gam});
       bA[0] = a0;
       continue;
@@ -294,8 +294,6 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
       vtip = vv;
       if (kind == kActOpen) {
         bv[last] = vv;
-        pAa[last] = szero();
-        IAa[last] = azero;
         if constexpr (EXTW) {
 #pragma unroll
           for (int u = 0; u < 9; ++u) bR[last][u] = Rt[u];
@@ -333,7 +331,7 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
         }
         if constexpr (EXTW) pAt = pAt - ext_in(Rt, ot, i);
         if (k == len - 1) {
-          if (closing) {
+          if (closing && ((acc >> last) & 1ull)) {
             ai_add(IA, IAa[last]);
             pAt = pAt + pAa[last];
           }
@@ -380,8 +378,14 @@ FD void aba_seg_core(const Img& M, const float* __restrict__ q, const float* __r
     });
     const int p = M.seg_parent[s];
     if (p >= 0) {
-      ai_add(IAa[p], Ia);
-      pAa[p] = pAa[p] + pa;
+      if ((acc >> p) & 1ull) {
+        ai_add(IAa[p], Ia);
+        pAa[p] = pAa[p] + pa;
+      } else {
+        IAa[p] = Ia;
+        pAa[p] = pa;
+        acc |= 1ull << p;
+      }
     }
   }
   // outward sweep: accelerations, segment by segment in the reverse of the
