@@ -986,10 +986,19 @@ def frax_arm(args, rank, world, local_rank):
         hsteps = max(20, args.steps // 4)
         hms, hper, hl, _, _ = time_step(hstep, hsteps, max(3, args.warmup), flush, world, dist)
         launches += hl
+        # the same six calls captured once as a CUDA graph, the two memory-bound
+        # ones on a second stream beside the ALU-bound ones (as the chain's step)
+        gms, gl, _, _, gwhy = time_graph(hstep, hsteps, max(3, args.warmup), flush, world, dist, None, HBM_OPS)
+        launches += gl or 0
         humanoid = {"workload": "floating-base humanoid (root + 29 revolute, seed 0), 2^18 instances; FK + 4 "
                                 "end-frame Jacobians, bias forces, CRBA + LTDL, ABA, RNEA-VJP, ABA-VJP",
                     "batch": hB, "steps": hsteps, "ms_per_step": hms, "statistic": "median over steps",
+                    "launch": "eager: one public call per op, CUDA events between them",
                     "evals_per_s": world * len(hops) * hB / (hms / 1e3),
+                    "graph": ({"ms_per_step": gms, "evals_per_s": world * len(hops) * hB / (gms / 1e3),
+                               "launch": "the six calls captured once as a CUDA graph and replayed; FK+J and "
+                                         "CRBA+LTDL on a second stream"} if gms is not None
+                              else {"unavailable": gwhy}),
                     "per_op": roofline_of(hper, FLOPS["humanoid"], hB, peak, hbm, hrobot)}
         del hstep, hdev
 
