@@ -810,6 +810,9 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
   float sc[NB], ss[NB];
   const SV ag = gravity_acc(M.g);
   V3 gam = mk(0, 0, 0);
+  // bodies whose aF / aab / avb hold a child segment's contribution (the
+  // first one is stored, later ones added)
+  uint64_t acc = 0;
 #pragma unroll 1
   for (int t = 0; t < M.n_act; ++t) {
     const int act = M.act[t];
@@ -823,12 +826,12 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
         bv[0] = load6(qd, 0, col);
         ba[0] = SV{mk(0, 0, 0), gam} + load6(qdd, 0, col);
         bF[0] = gb_at.root();
-        aF[0] = aab[0] = avb[0] = szero();
         if (kind == kActOpen) continue;
       }
       const SV v0 = bv[0], Fb0 = bF[0];
-      const SV ab = rbi_mul_add(aab[0], I, Fb0);
-      const SV vb = rbi_mul_sub(crf_sub(avb[0], Fb0, rbi_mul(I, v0)), I, crm(v0, Fb0));
+      const bool has = acc & 1ull;
+      const SV ab = rbi_mul_add(has ? aab[0] : szero(), I, Fb0);
+      const SV vb = rbi_mul_sub(crf_sub(has ? avb[0] : szero(), Fb0, rbi_mul(I, v0)), I, crm(v0, Fb0));
       sink.root(cross(ab.v, gam), vb, ab);
       continue;
     }
@@ -861,7 +864,6 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
         bv[last] = v;
         ba[last] = a;
         bF[last] = Fb;
-        aF[last] = aab[last] = avb[last] = szero();
         continue;
       }
     } else {
@@ -869,7 +871,7 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
       a = ba[last];
       Fb = bF[last];
     }
-    const bool closing = kind == kActClose;
+    const bool closing = kind == kActClose && ((acc >> last) & 1ull);
     SV Fc = closing ? aF[last] : szero();
     SV abc = closing ? aab[last] : szero();
     SV vbc = closing ? avb[last] : szero();
@@ -911,9 +913,16 @@ FD void rnea_vjp_seg(const Img& M, const float* __restrict__ q, const float* __r
     });
     const int p = M.seg_parent[s];
     if (p >= 0) {
-      aF[p] = aF[p] + Fc;
-      aab[p] = aab[p] + abc;
-      avb[p] = avb[p] + vbc;
+      if ((acc >> p) & 1ull) {
+        aF[p] = aF[p] + Fc;
+        aab[p] = aab[p] + abc;
+        avb[p] = avb[p] + vbc;
+      } else {
+        aF[p] = Fc;
+        aab[p] = abc;
+        avb[p] = vbc;
+        acc |= 1ull << p;
+      }
     }
   }
 }
