@@ -19,8 +19,9 @@
  *    and 6 velocity entries, the body-frame twist [w_b; v_b]; qdd is its time
  *    derivative. Revolute joints have one entry each.
  *  - Batched arrays are FP32, structure-of-arrays, entry-major: element
- *    (entry k, instance b) lives at ptr[k * ld + b], ld >= B. All batched
- *    pointers are DEVICE pointers, caller-owned, 4-byte aligned.
+ *    (entry k, instance b) lives at ptr[k * ld + b], B <= ld < 2^30 (a
+ *    larger ld is an argument error). All batched pointers are DEVICE
+ *    pointers, caller-owned, 4-byte aligned.
  *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*,
  *    NULL = legacy default stream) and never synchronise. Argument errors are
  *    reported before anything is launched. B == 0 is a no-op returning

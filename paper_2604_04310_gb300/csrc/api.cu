@@ -55,6 +55,8 @@ frax_status check_batch(frax_model_t model, int64_t B, int64_t ld, const char* f
   if (!model) return fail(FRAX_EINVAL, std::string(fn) + ": model is NULL");
   if (B < 0) return fail(FRAX_EINVAL, std::string(fn) + ": B must be >= 0");
   if (B > 0 && ld < B) return fail(FRAX_EINVAL, std::string(fn) + ": ld must be >= B");
+  // the kernels address entry k as k * ld * 4 bytes in 32 x 32-bit products
+  if (ld >= (int64_t(1) << 30)) return fail(FRAX_EINVAL, std::string(fn) + ": ld must be below 2^30");
   if (B > (int64_t(1) << 40)) return fail(FRAX_EINVAL, std::string(fn) + ": B too large");
   return FRAX_OK;
 }

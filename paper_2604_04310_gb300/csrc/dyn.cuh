@@ -12,6 +12,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "spatial.cuh"
 
 namespace frax {
@@ -68,28 +70,51 @@ FD void st_cs(float* p, float v) {
 #endif
 }
 
-template <bool kNC>
+// Byte offset of entry k of a batched array, k * ld floats: the boundary
+// keeps ld below 2^30, so the row stride in bytes fits 32 bits and the
+// offset is one 32 x 32 -> 64-bit multiply (not a 64-bit multiply and add per
+// access).
+FD uint64_t row_off(int k, int64_t ld) { return uint64_t(uint32_t(k)) * uint64_t(uint32_t(ld) * 4u); }
+template <class F>
+FD F* at_row(F* base, int k, int64_t ld) {
+  using Byte = typename std::conditional<std::is_const<F>::value, const char, char>::type;
+  return reinterpret_cast<F*>(reinterpret_cast<Byte*>(base) + row_off(k, ld));
+}
+
+// kRow32 = false addresses entry k as p + k * ld + b in 64-bit arithmetic:
+// the two uncapped chain kernels that solve through the register factor after
+// an extra sweep (forces, JVP) are scheduled better by the compiler that way
+// (128 registers, 104 and 146 us at 2^20, against 96 registers and 117 and
+// 163 us with the 32-bit offsets).
+template <bool kNC, bool kRow32 = true>
 struct ColT {
   int64_t ld, b;
+  // this instance's entry k of p
+  template <class F>
+  FD F* at(F* p, int k) const {
+    if constexpr (kRow32) return at_row(p + b, k, ld);
+    else return p + k * ld + b;
+  }
   FD float in(const float* __restrict__ p, int k) const {
 #ifdef __CUDA_ARCH__
-    return kNC ? __ldg(p + k * ld + b) : __ldcg(p + k * ld + b);
+    return kNC ? __ldg(at(p, k)) : __ldcg(at(p, k));
 #else
-    return p[k * ld + b];
+    return *at(p, k);
 #endif
   }
   // outputs are written once and not read again by the kernel that writes
   // them (except through ColT<false>): streaming stores (evict-first in L2)
-  FD void out(float* __restrict__ p, int k, float v) const { st_cs(p + k * ld + b, v); }
+  FD void out(float* __restrict__ p, int k, float v) const { st_cs(at(p, k), v); }
 };
 using Col = ColT<true>;
+using Col64 = ColT<true, false>;
 
 // Asks L2 for this instance's n entries of p (one line per warp and entry)
 // ahead of a sweep that reads them one body at a time.
 template <class C>
 FD void prefetch_entries(const float* p, int n, const C& col) {
 #ifdef __CUDA_ARCH__
-  for (int k = 0; k < n; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + k * col.ld + col.b));
+  for (int k = 0; k < n; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(col.at(p, k)));
 #endif
 }
 

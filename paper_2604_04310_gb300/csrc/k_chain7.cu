@@ -19,7 +19,9 @@ __global__ void __launch_bounds__(kBlock) k_aba_jvp_chain7(const __grid_constant
                                                             int64_t ld, const float* q, const float* qd,
                                                             const float* qdd, const float* dq, const float* dqd,
                                                             const float* dtau, float* dqdd) {
-  FRAX_TID();
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const Col64 col{ld, b};
   aba_jvp_chain_one<7>(M, q, qd, qdd, dq, dqd, dtau, dqdd, col);
 }
 
@@ -51,20 +53,22 @@ struct TauExtMinusBias {
   const float* tau;
   const float* bias;
   const LocalVec<ChainTopo<7>>* ext;
-  Col col;
-  ColT<false> own;
+  Col64 col;
+  ColT<false, false> own;
   FD float operator()(int k) const { return (col.in(tau, k) + (*ext)(k)) - own.in(bias, k); }
 };
 __global__ void __launch_bounds__(kBlock) k_aba_ext_chain7(const __grid_constant__ ModelImage<8> M, int64_t B,
                                                              int64_t ld, const float* q, const float* qd,
                                                              const float* tau, const float* fext, float* qdd) {
-  FRAX_TID();
+  const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const Col64 col{ld, b};
   using T = ChainTopo<7>;
   LocalVec<T> w;
   ext_tau_chain<7>(M, q, fext, col, OutToLocal<T>{&w});
   rnea_one<T>(M, q, qd, nullptr, qdd, col);
   float x[7];
-  chain_minv<7>(M, q, TauExtMinusBias{tau, qdd, &w, col, ColT<false>{ld, b}}, x, col);
+  chain_minv<7>(M, q, TauExtMinusBias{tau, qdd, &w, col, ColT<false, false>{ld, b}}, x, col);
 #pragma unroll
   for (int k = 0; k < 7; ++k) col.out(qdd, k, x[k]);
 }

@@ -36,7 +36,10 @@ struct LgCol {
   int64_t ld, b;  // global output column
   int inst;       // staged input column
   FD float in(const float* __restrict__ p, int k) const { return p[k * kLgInst + inst]; }
-  FD void out(float* __restrict__ p, int k, float v) const { st_cs(p + k * ld + b, v); }
+  // this instance's entry k of a global output
+  template <class F>
+  FD F* at(F* p, int k) const { return at_row(p + b, k, ld); }
+  FD void out(float* __restrict__ p, int k, float v) const { st_cs(at(p, k), v); }
 };
 
 // One instance's scratch, field f at base[f * stride] (instance-major in

@@ -160,8 +160,8 @@ extern "C" frax_status frax_serve_batch_noalloc(const frax_batch_request_t* reqs
   for (int i = 0; i < n_reqs; ++i) {
     const frax_batch_request_t& q = reqs[i];
     if (!q.model) return set_error(FRAX_EINVAL, "frax_serve_batch_noalloc: a request has no model");
-    if (q.B < 0 || q.B > (int64_t(1) << 30))
-      return set_error(FRAX_EINVAL, "frax_serve_batch_noalloc: B must be in [0, 2^30]");
+    if (q.B < 0 || q.B >= (int64_t(1) << 30))
+      return set_error(FRAX_EINVAL, "frax_serve_batch_noalloc: B must be in [0, 2^30)");
     int nin, nout;
     switch (q.op) {
       case FRAX_OP_RNEA: nin = 3; nout = 1; break;

@@ -461,16 +461,15 @@ FD void crba_emit_row(const Img& M, int i, SV FM, SV FL, float* __restrict__ Mou
   const bool wM = (OUT & 1) && Mout != nullptr, wL = (OUT & 2) && LD != nullptr;
   // this instance's row di of M, column di of M and row di of the factor:
   // entry c of each one multiply and one add away
-  float* const rowM = wM ? Mout + int64_t(di) * nv * col.ld + col.b : nullptr;
-  float* const colM = wM ? Mout + int64_t(di) * col.ld + col.b : nullptr;
-  float* const rowL = wL ? LD + int64_t(MSink::tri(di, 0)) * col.ld + col.b : nullptr;
-  const int64_t ldM = int64_t(nv) * col.ld;
+  float* const rowM = wM ? col.at(Mout, di * nv) : nullptr;
+  float* const colM = wM ? col.at(Mout, di) : nullptr;
+  float* const rowL = wL ? col.at(LD, MSink::tri(di, 0)) : nullptr;
   auto put = [&](int c, float m, float l) {  // c < di
     if (wM) {
-      st_cs(rowM + c * col.ld, m);
-      st_cs(colM + c * ldM, m);
+      st_cs(at_row(rowM, c, col.ld), m);
+      st_cs(at_row(colM, c * nv, col.ld), m);
     }
-    if (wL) st_cs(rowL + c * col.ld, l);
+    if (wL) st_cs(at_row(rowL, c, col.ld), l);
   };
   int j = i;
   while (true) {

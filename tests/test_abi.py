@@ -92,6 +92,8 @@ def test_batch_argument_checks_before_any_launch():
     assert L.frax_rnea(m.handle, -1, 0, null, null, null, null, null) == 1
     assert L.frax_rnea(m.handle, 16, 8, null, null, null, null, null) == 1
     assert b"ld" in L.frax_last_error()
+    assert L.frax_rnea(m.handle, 16, 1 << 30, null, null, null, null, null) == 1
+    assert b"below 2^30" in L.frax_last_error()
     assert L.frax_rnea(m.handle, 16, 16, null, null, null, null, null) == 1
     assert b"q is NULL" in L.frax_last_error()
     assert L.frax_crba(m.handle, 16, 16, ctypes.c_void_p(16), null, null, null) == 1
