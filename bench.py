@@ -69,8 +69,8 @@ FLOPS = {
 # workload; an entry is removed when its kernel changes. aba_vjp = the factor
 # solve plus the adjoint sweep.
 NCU_TRAFFIC = {
-    "fk_jac": 29.40e6 + 491.16e6, "rnea": 88.12e6 + 7.86e6, "crba_ltdl": 25.20e6 + 263.56e6,
-    "aba": 88.13e6 + 9.34e6, "rnea_vjp": 117.51e6 + 43.44e6, "aba_vjp": 54.55e6 + 2.02e6 + 117.52e6 + 25.56e6,
+    "fk_jac": 29.39e6 + 490.03e6, "rnea": 88.11e6 + 3.83e6, "crba_ltdl": 25.22e6 + 260.06e6,
+    "aba": 88.13e6 + 6.27e6, "rnea_vjp": 117.51e6 + 40.27e6, "aba_vjp": 54.56e6 + 0.35e6 + 117.51e6 + 22.37e6,
 }
 # operational-space control task bodies (the last end frame of each model)
 OSC_TASK = {"chain7": 6, "humanoid": 29}
