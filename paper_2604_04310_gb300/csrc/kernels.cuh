@@ -49,10 +49,10 @@ __global__ void __launch_bounds__(kBlock, 4) k_aba(const __grid_constant__ Model
   aba_one<T>(M, q, qd, tau, qdd, col);
 }
 
-// RNEA adjoint and JVP: 8 blocks/SM (64 registers), measured best for the
-// chain and the trees.
+// RNEA adjoint and JVP: 8 blocks/SM (64 registers) for chains, 7 for trees
+// (measured best).
 template <class T>
-__global__ void __launch_bounds__(kBlock, 8) k_rnea_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, T::kSeg ? 7 : 8) k_rnea_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                       int64_t ld, const float* q, const float* qd,
                                                       const float* qdd, const float* gbar, float* qbar,
                                                       float* qdbar, float* qddbar) {
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_rnea_vjp(const __grid_constant__ 
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock, 8) k_aba_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, T::kSeg ? 7 : 8) k_aba_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                      int64_t ld, const float* q, const float* qd,
                                                      const float* tau, const float* qdd, const float* gbar,
                                                      float* qbar, float* qdbar, float* taubar) {
@@ -87,10 +87,11 @@ __global__ void __launch_bounds__(kBlock) k_ltdl_inverse(const __grid_constant__
 
 // Trees (segment-unrolled). FK+J and CRBA leave the structural zeros of J, M
 // and the factor to the row fill of zeros.cu. Register caps (128-thread blocks per SM) chosen
-// by measurement on the humanoid: 8 for FK, RNEA and ABA (which keeps 8
-// floats per body in thread-local memory between its sweeps), 4 for CRBA;
-// more resident warps hide those memory latencies better than the registers
-// they cost.
+// by measurement on the humanoid at 2^18 instances: 8 for FK, 7 for RNEA, ABA
+// (which keeps 6 floats per body in thread-local memory between its sweeps)
+// and both adjoints, 5 for CRBA with both outputs; more resident warps hide
+// those memory latencies better than the registers they cost, down to about
+// 7 blocks.
 template <class T>
 __global__ void __launch_bounds__(kBlock, 8) k_fk_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                        int64_t ld, const float* q, float* pose,
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_fk_seg(const __grid_constant__ Mo
   fk_seg<T, ModelImage<T::NBMAX>, Col, false>(M, q, pose, fr, J, col);
 }
 template <class T>
-__global__ void __launch_bounds__(kBlock, 8) k_rnea_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
+__global__ void __launch_bounds__(kBlock, 7) k_rnea_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
                                                          int64_t B, int64_t ld, const float* q, const float* qd,
                                                          const float* qdd, float* tau) {
   FRAX_TID();
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : (OUT == 3 ? 5 : 6)) k_c
   for (int r = Z.n0; r < Z.n; ++r) col.out(LD, Z.row[r], 0.f);
 }
 template <class T>
-__global__ void __launch_bounds__(kBlock, 8) k_aba_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
+__global__ void __launch_bounds__(kBlock, 7) k_aba_seg(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                         int64_t ld, const float* q, const float* qd,
                                                         const float* tau, float* qdd) {
   FRAX_TID();
