@@ -970,8 +970,15 @@ def frax_arm(args, rank, world, local_rank):
     # copies of one step overlap the kernels of the next
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_pipeline(fx, model, robot, host, dev, step, device, args.steps, world, dist)
-        launches += e2e.pop("launches")
+        # three repeats of the pipelined run, the median reported (single runs
+        # have come out at 5.8 or, on some boxes, about 10 ms per step)
+        reps = [e2e_pipeline(fx, model, robot, host, dev, step, device, args.steps, world, dist) for _ in range(3)]
+        launches += sum(r.pop("launches") for r in reps)
+        e2e = sorted(reps, key=lambda r: r["ms_per_step"])[1]
+        e2e["repeats_ms_per_step"] = [r["ms_per_step"] for r in reps]
+        e2e["statistic"] = "median of 3 repeats of the pipelined run"
+        e2e["frac_of_copy_ceiling"] = (e2e["d2h_bytes_per_step"] / (e2e["copy_ceiling"]["d2h_gbs"] * 1e9)) / (
+            e2e["ms_per_step"] / 1e3)
     del step, dev, host
 
     # second workload: the floating-base humanoid (30 bodies, nv = 35), 2^18
