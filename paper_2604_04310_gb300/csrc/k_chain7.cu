@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(kBlock) k_aba_jvp_chain7(const __grid_constant
 // 7-body chains: forward dynamics through the mass-matrix factor,
 // qdd = M^-1 (tau - c - g) (the Cholesky-style solve of the Sec. VI
 // footnote): c + g by RNEA into qdd, then the register factor solve reading
-// it back. 3353 flops against the articulated-body algorithm's 4073, and 64
+// it back. 3353 flops against the articulated-body algorithm's 3431, and 64
 // registers instead of 128.
 struct TauMinusBias {
   const float* tau;
