@@ -111,7 +111,10 @@ __global__ void __launch_bounds__(kBlock, 7) k_rnea_seg(const __grid_constant__ 
 // registers); for both, one kernel (two would repeat the sweeps: slower).
 // The structural zeros (the same entries for every instance) are written by
 // the same threads after their sweeps, from the row list Z: the stores fill
-// the memory system while other warps compute.
+// the memory system while other warps compute. A warp whose 32 instances are
+// all in the batch writes them as 16-byte stores, each lane four instances
+// of every fourth row (when ld and both outputs allow 16-byte alignment); a
+// partial warp writes one float per thread and row.
 template <class T, int OUT>
 __global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : (OUT == 3 ? 5 : 6)) k_crba_seg(const __grid_constant__ ModelImage<T::NBMAX> M,
                                                                        const __grid_constant__ ZeroRows Z, int64_t B,
@@ -120,6 +123,19 @@ __global__ void __launch_bounds__(kBlock, OUT == 1 ? 8 : (OUT == 3 ? 5 : 6)) k_c
   FRAX_TID();
   prefetch_entries(q, M.nq, col);  // measured: helps here, not in the kernels that also read qd, tau
   crba_seg<T, ModelImage<T::NBMAX>, Col, false, OUT>(M, q, Mout, LD, col);
+  const int64_t b0 = b & ~int64_t(31);  // the warp's first instance (blocks are whole warps)
+  const bool vec = b0 + 32 <= B &&
+                   ((uint64_t(ld) | reinterpret_cast<uintptr_t>(Mout) | reinterpret_cast<uintptr_t>(LD)) & 3) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(Mout) | reinterpret_cast<uintptr_t>(LD)) & 15) == 0;
+  if (vec) {
+    const int lane = int(threadIdx.x & 31);
+    const int sub = lane >> 3;  // row offset within a group of four rows
+    const int64_t off = b0 + (lane & 7) * 4;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = sub; r < Z.n0; r += 4) __stcs(reinterpret_cast<float4*>(at_row(Mout + off, Z.row[r], ld)), z4);
+    for (int r = Z.n0 + sub; r < Z.n; r += 4) __stcs(reinterpret_cast<float4*>(at_row(LD + off, Z.row[r], ld)), z4);
+    return;
+  }
 #pragma unroll 4
   for (int r = 0; r < Z.n0; ++r) col.out(Mout, Z.row[r], 0.f);
 #pragma unroll 4
