@@ -389,7 +389,7 @@ enum { FRAX_NOALLOC_MAX_REQUESTS = 256, FRAX_NOALLOC_MAX_MODELS = 16 };
 typedef struct {
   frax_model_t model;
   int op;             /* FRAX_OP_RNEA, _CRBA, _ABA or _RNEA_GRAD */
-  int64_t B;          /* instances; 0 allowed                    */
+  int64_t B;          /* instances, 0 <= B < 2^30 (0 allowed)    */
   const float* in[4]; /* device inputs, unused entries NULL      */
   float* out[3];      /* device outputs, unused entries NULL     */
 } frax_batch_request_t;
