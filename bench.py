@@ -267,6 +267,22 @@ class Step:
                 events[name][1].record()
         return self.kernels
 
+    def run_groups(self, streams, groups):
+        """The same calls, group g issued in order on streams[g] (forked from and
+        joined back into the current stream): the groups overlap on the GPU."""
+        import torch
+        cur = torch.cuda.current_stream()
+        fns = dict(self.launches)
+        for st in streams:
+            st.wait_stream(cur)
+        for st, g in zip(streams, groups):
+            with torch.cuda.stream(st):
+                for name in g:
+                    fns[name]()
+        for st in streams:
+            cur.wait_stream(st)
+        return self.kernels
+
     def run_split(self, side, side_ops):
         """The same calls, those in side_ops issued on the stream `side`
         (forked from and joined back into the current stream), the rest on
@@ -321,7 +337,7 @@ def time_step(step, steps, warmup, flush, world, dist, clocks=None):
     return step_ms, per_op_ms, launches, wall, clk
 
 
-def time_graph(step, steps, warmup, flush, world, dist, clocks=None, side_ops=()):
+def time_graph(step, steps, warmup, flush, world, dist, clocks=None, side_ops=(), groups=None):
     """The same step captured once as a CUDA graph (the same calls, the same
     kernels; replaying it trims the host's launch gaps between them) and
     replayed `steps` times, L2 flushed between replays outside the events.
@@ -339,9 +355,12 @@ def time_graph(step, steps, warmup, flush, world, dist, clocks=None, side_ops=()
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     fork = torch.cuda.Stream()
+    gstreams = [torch.cuda.Stream() for _ in (groups or ())]
     try:
         with torch.cuda.graph(g):
-            if side_ops:
+            if groups:
+                step.run_groups(gstreams, groups)
+            elif side_ops:
                 step.run_split(fork, set(side_ops))
             else:
                 step.run()
@@ -652,6 +671,16 @@ def serve_stream(fx, seconds, check_batched=True, repeats=3):
             "idle_exit_ms": 20.0}
 
 
+def concurrent_groups(ops):
+    """One stream per op of the step, the ABA and its adjoint (which reads
+    the ABA's output) on one."""
+    groups, rest = [], list(ops)
+    if "aba" in rest and "aba_vjp" in rest:
+        groups.append(["aba", "aba_vjp"])
+        rest = [o for o in rest if o not in ("aba", "aba_vjp")]
+    return groups + [[o] for o in rest]
+
+
 SWEEP_B = [1, 4, 16, 64, 256, 1024, 4096, 16384, 1 << 16, 1 << 18, 1 << 20]
 
 
@@ -659,7 +688,9 @@ def batch_sweep(fx, device, flush):
     """Throughput against batch size (the shape of the paper's Fig. 2) for the
     chain's and the humanoid's six-op steps: kernel time (the step's public
     calls captured once as a CUDA graph and replayed, CUDA events, L2 flushed
-    between replays), the calls issued one by one (CUDA events between them),
+    between replays), the same graph with each independent op on its own
+    stream (small batches leave most SMs idle, so the ops then run side by
+    side), end to end with that graph replayed between the copies, the calls issued one by one (CUDA events between them),
     the host time to issue one public call (Python binding + C ABI + launch,
     no synchronisation), and end to end through the public API (the inputs,
     one pinned [rows][B] block, copied in with one copy; the six calls; the
@@ -690,8 +721,11 @@ def batch_sweep(fx, device, flush):
             step = Step(fx, model, robot, dev, device, ops, flat=True)
             reps = 200 if B <= 4096 else (40 if B <= (1 << 16) else 12)
             g_ms, g_l, _, _, why = time_graph(step, reps, 3, flush, 1, None)
+            # the same calls with every independent op on its own stream (the
+            # ABA adjoint reads the ABA's output, so the two share one)
+            c_ms, c_l, _, _, _ = time_graph(step, reps, 3, flush, 1, None, groups=concurrent_groups(ops))
             e_ms, _, e_l, _, _ = time_step(step, reps, 3, flush, 1, None)
-            res["launches"] += (g_l or 0) + e_l
+            res["launches"] += (g_l or 0) + (c_l or 0) + e_l
             torch.cuda.synchronize()
             host_us = []
             for _ in range(reps):
@@ -717,17 +751,49 @@ def batch_sweep(fx, device, flush):
                 torch.cuda.synchronize()
                 e2e_us.append((time.perf_counter() - t0) * 1e6)
             res["launches"] += reps * step.kernels
+            # end to end again, the six calls replayed as the concurrent graph
+            # between the two copies (the public calls captured once, as a
+            # caller issuing the same batch shape every cycle would)
+            ge2e_us = []
+            gstreams = [torch.cuda.Stream() for _ in concurrent_groups(ops)]
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                step.run_groups(gstreams, concurrent_groups(ops))
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            ge = torch.cuda.CUDAGraph()
+            try:
+                with torch.cuda.graph(ge):
+                    step.run_groups(gstreams, concurrent_groups(ops))
+            except Exception:  # noqa: BLE001 - the row then has no graph figure
+                ge = None
+                torch.cuda.synchronize()
+            if ge is not None:
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    din.copy_(hin, non_blocking=True)
+                    ge.replay()
+                    hout.copy_(dspan, non_blocking=True)
+                    torch.cuda.synchronize()
+                    ge2e_us.append((time.perf_counter() - t0) * 1e6)
+                res["launches"] += (reps + 1) * step.kernels
             ev = len(ops) * B
             e2e = statistics.median(e2e_us)
+            ge2e = statistics.median(ge2e_us) if ge2e_us else None
             rows.append({"B": B, "reps": reps,
                          "kernel_us": g_ms * 1e3 if g_ms is not None else None,
                          "kernel_evals_per_s": ev / (g_ms / 1e3) if g_ms is not None else None,
                          "graph": why or "replayed",
+                         "concurrent_us": c_ms * 1e3 if c_ms is not None else None,
+                         "concurrent_evals_per_s": ev / (c_ms / 1e3) if c_ms is not None else None,
                          "eager_us": e_ms * 1e3, "eager_evals_per_s": ev / (e_ms / 1e3),
                          "host_us_per_call": statistics.median(host_us),
                          "e2e_us": e2e, "e2e_evals_per_s": ev / (e2e / 1e6),
+                         "e2e_graph_us": ge2e, "e2e_graph_evals_per_s": ev / (ge2e / 1e6) if ge2e else None,
                          "h2d_bytes": hin.numel() * 4, "d2h_bytes": hout.numel() * 4})
-            del step, dev, host, hin, din, hout, dspan
+            del step, dev, host, hin, din, hout, dspan, ge, gstreams
         res[name] = rows
     return res
 
