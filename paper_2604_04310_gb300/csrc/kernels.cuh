@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_aba(const __grid_constant__ Model
   aba_one<T>(M, q, qd, tau, qdd, col);
 }
 
-// RNEA adjoint and JVP: 8 blocks/SM (64 registers) for chains, 7 for trees
-// (measured best).
+// RNEA adjoint: 8 blocks/SM (64 registers) for chains, 7 for trees (measured
+// best; the tree JVP below keeps 8).
 template <class T>
 __global__ void __launch_bounds__(kBlock, T::kSeg ? 7 : 8) k_rnea_vjp(const __grid_constant__ ModelImage<T::NBMAX> M, int64_t B,
                                                       int64_t ld, const float* q, const float* qd,
