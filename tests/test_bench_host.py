@@ -72,3 +72,15 @@ def test_kernels_per_call_matches_the_dispatch():
     assert bench.kernels_per_call(chain_tree, "fk_jac") == 1
     assert bench.kernels_per_call(t, "crba_ltdl") == 1
 
+
+
+def test_concurrent_groups_keep_the_adjoint_after_the_aba():
+    """Every op of a step lies in exactly one stream group, and the ABA adjoint
+    (which reads the ABA's output) shares the ABA's group, after it."""
+    for ops in (bench.OPS, bench.HUMANOID_OPS):
+        groups = bench.concurrent_groups(ops)
+        flat = [o for g in groups for o in g]
+        assert sorted(flat) == sorted(ops)
+        g = next(g for g in groups if "aba_vjp" in g)
+        assert g.index("aba") < g.index("aba_vjp")
+        assert all(len(g) == 1 for g in groups if "aba" not in g)
