@@ -168,3 +168,15 @@ def test_tree_path_setting_is_validated():
     assert L.frax_model_set_tree_path(h.handle, 3) == 1 and "unknown path" in L.frax_last_error().decode()
     assert L.frax_model_set_tree_path(None, 0) == 1
     h.set_tree_path("auto")
+
+
+def test_fp32_probe_argument_checks():
+    """The probe rejects empty launches and a missing sink before any launch."""
+    L = _lib.load()
+    null = ctypes.c_void_p(0)
+    flops = ctypes.c_double(-1.0)
+    assert L.frax_fp32_probe(0, 0, 10, ctypes.c_void_p(16), ctypes.byref(flops), null) == 1
+    assert b"blocks" in L.frax_last_error()
+    assert L.frax_fp32_probe(1, 4, 0, ctypes.c_void_p(16), ctypes.byref(flops), null) == 1
+    assert L.frax_fp32_probe(0, 4, 10, null, ctypes.byref(flops), null) == 1
+    assert flops.value == -1.0
