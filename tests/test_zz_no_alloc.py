@@ -95,6 +95,7 @@ def test_noalloc_batch_limits():
     fx.frax_serve_batch_noalloc([])
 
 
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
 def test_noalloc_batch_refused_while_capturing():
     """Under stream capture the call returns FRAX_EINVAL and enqueues nothing,
     so the capture stays valid and ends as an empty graph."""
