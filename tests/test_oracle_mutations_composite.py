@@ -10,9 +10,10 @@ reversal or with D unsquared; the packed factor read across the diagonal;
 Eq. 2 with the wrong bias; Jacobian columns left in the joint frame or not
 shifted to the frame origin; the free-flyer cotangent map without its factor
 2; J-dot q-dot dropped; Lambda left uninverted; the ancestor mask used
-transposed in the mask form. The unmutated copies of CRBA and the Jacobian
-written here agree with the oracle's own to rounding, so each case differs
-from the oracle by its one planted mistake."""
+transposed in the mask form; a free-flyer retraction that moves the root in
+world instead of body coordinates. The unmutated copies of CRBA, the
+Jacobian and the retraction written here agree with the oracle's own to
+rounding, so each case differs from the oracle by its one planted mistake."""
 
 import numpy as np
 import pytest
@@ -20,7 +21,8 @@ import pytest
 import gen
 from oracle import derivatives as dv
 from oracle import mask_form, rbd, task_space
-from oracle.spatial import motion_transform_inverse, skew
+from oracle.spatial import matvec, motion_transform_inverse, quat_exp, quat_multiply, quat_to_rotation, skew
+from tests import pins as pin_helpers
 from tests import test_oracle_derivatives as pins_der
 from tests import test_oracle_invariants as pins_inv
 from tests import test_oracle_task_space as pins_ts
@@ -103,7 +105,10 @@ def _jacobian_copy(to_world=True, shift_to_frame=True):
                 shift[:, 3:, :3] = -skew(p[:, k])
             for j in lay.ancestors(k):
                 S = rbd.motion_subspace(model, j)
-                S0 = motion_transform_inverse(R[:, j], p[:, j]) @ S if to_world else np.broadcast_to(S, (B, 6, S.shape[1]))
+                if to_world:
+                    S0 = motion_transform_inverse(R[:, j], p[:, j]) @ S
+                else:
+                    S0 = np.broadcast_to(S, (B, 6, S.shape[1]))
                 out[:, f, :, lay.vslice(j)] = shift @ S0
         return out
     return jacobian
@@ -230,4 +235,49 @@ def test_planted_mistake_is_caught(monkeypatch, models, case):
     module, attr, fn, pins = MUTATIONS[case]
     monkeypatch.setattr(module, attr, fn)
     caught = [(pin.__name__, name) for pin, name in pins if _fails(pin, models, name)]
+    assert caught, f"{case} passed every pin meant to guard it"
+
+
+def _retract_copy(body_frame_translation=True, body_frame_rotation=True):
+    """derivatives.retract restated: q (+) d moves a free root by
+    T * Exp([dw; dv]); either half switchable to world coordinates."""
+    def retract(model, q, d):
+        lay = rbd.Layout(model)
+        out = q.astype(np.result_type(q, d)).copy()
+        for i in range(lay.n):
+            qs, vs = lay.qslice(i), lay.vslice(i)
+            if lay.jtype[i] == rbd.FREE:
+                qi, di = q[:, qs], d[:, vs]
+                dv_world = matvec(quat_to_rotation(qi[:, 3:7]), di[:, 3:6]) if body_frame_translation else di[:, 3:6]
+                out[:, qs.start:qs.start + 3] = qi[:, 0:3] + dv_world
+                turn = quat_exp(di[:, 0:3])
+                out[:, qs.start + 3:qs.start + 7] = (quat_multiply(qi[:, 3:7], turn) if body_frame_rotation
+                                                     else quat_multiply(turn, qi[:, 3:7]))
+            else:
+                out[:, qs] = q[:, qs] + d[:, vs]
+        return out
+    return retract
+
+
+RETRACT_PINS = [(pins_inv.test_kinetic_energy, "humanoid"), (pins_inv.test_forward_dynamics, "humanoid"),
+                (pins_der.test_vjp_ambient_mapping, None)]
+
+
+def test_unmutated_retract_copy_equals_the_oracle(models):
+    m = models["humanoid"]
+    s = gen.draw_states(m, 4, 23)
+    d = np.random.default_rng(24).standard_normal((4, m.nv))
+    assert normwise(_retract_copy()(m, s.q, d), dv.retract(m, s.q, d)) < 1e-15
+
+
+@pytest.mark.parametrize("case", ["translation_in_world", "rotation_in_world"])
+def test_planted_retraction_mistake_is_caught(monkeypatch, models, case):
+    """The retraction is the free-flyer convention that the pins' own curves
+    (FK twists, energy along q (+) h qd) and the oracle's derivatives share,
+    so the mistake is planted in all of them at once."""
+    fn = _retract_copy(body_frame_translation=case != "translation_in_world",
+                       body_frame_rotation=case != "rotation_in_world")
+    for module in (dv, pin_helpers, task_space):
+        monkeypatch.setattr(module, "retract", fn)
+    caught = [(pin.__name__, name) for pin, name in RETRACT_PINS if _fails(pin, models, name)]
     assert caught, f"{case} passed every pin meant to guard it"
