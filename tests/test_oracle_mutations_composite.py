@@ -11,7 +11,8 @@ Eq. 2 with the wrong bias; Jacobian columns left in the joint frame or not
 shifted to the frame origin; the free-flyer cotangent map without its factor
 2; J-dot q-dot dropped; Lambda left uninverted; the ancestor mask used
 transposed in the mask form; a free-flyer retraction that moves the root in
-world instead of body coordinates. The unmutated copies of CRBA, the
+world instead of body coordinates; JVPs that drop one direction or take the
+frame's angular rate from the transposed product. The unmutated copies of CRBA, the
 Jacobian and the retraction written here agree with the oracle's own to
 rounding, so each case differs from the oracle by its one planted mistake."""
 
@@ -25,6 +26,7 @@ from oracle.spatial import matvec, motion_transform_inverse, quat_exp, quat_mult
 from tests import pins as pin_helpers
 from tests import test_oracle_derivatives as pins_der
 from tests import test_oracle_invariants as pins_inv
+from tests import test_oracle_jvp as pins_jvp
 from tests import test_oracle_task_space as pins_ts
 from tests.pins import normwise
 
@@ -280,4 +282,51 @@ def test_planted_retraction_mistake_is_caught(monkeypatch, models, case):
     for module in (dv, pin_helpers, task_space):
         monkeypatch.setattr(module, "retract", fn)
     caught = [(pin.__name__, name) for pin, name in RETRACT_PINS if _fails(pin, models, name)]
+    assert caught, f"{case} passed every pin meant to guard it"
+
+
+_rnea_jvp, _aba_jvp, _fk_jvp = dv.rnea_jvp, dv.aba_jvp, dv.fk_jvp
+
+
+def _rnea_jvp_without_dqd(model, q, qd, qdd, dq, dqd, dqdd):
+    return _rnea_jvp(model, q, qd, qdd, dq, np.zeros_like(dqd), dqdd)
+
+
+def _aba_jvp_without_dq(model, q, qd, tau, dq, dqd, dtau):
+    return _aba_jvp(model, q, qd, tau, np.zeros_like(dq), dqd, dtau)
+
+
+def _fk_jvp_transposed_rate(model, q, dq, frames):
+    """omega from vee(R^T dR) (the body-frame rate) instead of vee(dR R^T)."""
+    h = dv.H_STEP
+    Rc, pc = rbd.fk(model, dv.retract(model, q, 1j * h * dq.astype(np.complex128)))
+    R, _ = rbd.fk(model, q)
+    f = list(frames)
+    W = np.swapaxes(R[:, f], -1, -2) @ (np.imag(Rc[:, f]) / h)
+    w = np.stack([W[..., 2, 1], W[..., 0, 2], W[..., 1, 0]], -1)
+    return np.concatenate([w, np.imag(pc[:, f]) / h], -1)
+
+
+JVP_MUTATIONS = {
+    "rnea_jvp_without_dqd": ("rnea_jvp", _rnea_jvp_without_dqd,
+                             [(pins_jvp.test_rnea_aba_jvp_vs_central_differences, "chain7")]),
+    "aba_jvp_without_dq": ("aba_jvp", _aba_jvp_without_dq,
+                           [(pins_jvp.test_rnea_aba_jvp_vs_central_differences, "humanoid")]),
+    "fk_jvp_body_frame_rate": ("fk_jvp", _fk_jvp_transposed_rate,
+                               [(pins_jvp.test_fk_jvp_is_jacobian_times_direction, "chain7"),
+                                (pins_jvp.test_fk_jvp_is_jacobian_times_direction, "humanoid")]),
+}
+
+
+def test_jvp_pins_hold_unmutated(models):
+    for _, _, pins in JVP_MUTATIONS.values():
+        for pin, name in pins:
+            assert not _fails(pin, models, name), (pin.__name__, name)
+
+
+@pytest.mark.parametrize("case", list(JVP_MUTATIONS))
+def test_planted_jvp_mistake_is_caught(monkeypatch, models, case):
+    attr, fn, pins = JVP_MUTATIONS[case]
+    monkeypatch.setattr(dv, attr, fn)
+    caught = [(pin.__name__, name) for pin, name in pins if _fails(pin, models, name)]
     assert caught, f"{case} passed every pin meant to guard it"
