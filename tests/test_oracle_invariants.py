@@ -139,3 +139,38 @@ def test_ancestor_mask_lower_triangular(models):
         assert np.all(np.triu(U, 1) == 0) and np.all(np.diag(U) == 1)
     U = rbd.ancestor_mask(models["humanoid"])
     assert U[22, 15] == 1 and U[22, 0] == 1 and U[22, 6] == 0 and U[29, 22] == 0
+
+
+@pytest.mark.parametrize("name", ["chain7", "humanoid", "tree_a", "tree_b"])
+def test_fk_rotations_are_proper(models, name):
+    """Every body's world rotation is orthonormal with determinant +1."""
+    m = models[name]
+    R, _ = rbd.fk(m, _states(m).q)
+    eye = np.broadcast_to(np.eye(3), R.shape)
+    assert np.max(np.abs(np.swapaxes(R, -1, -2) @ R - eye)) < 1e-13
+    assert np.max(np.abs(np.linalg.det(R) - 1.0)) < 1e-13
+
+
+@pytest.mark.parametrize("name", ["chain7", "humanoid", "tree_a"])
+def test_jacobian_central_differences(models, name):
+    """Column j of J is the frame's motion along tangent direction e_j, by
+    FP64 central differences of FK alone: the origin's displacement, and the
+    rotation vector log(R(q (+) h e_j) R(q (-) h e_j)^T) / 2h."""
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    from oracle.derivatives import retract
+    m = models[name]
+    s = gen.draw_states(m, 3, 9)
+    frames = list(m.end_frames)
+    J = rbd.jacobian(m, s.q, frames)
+    h = 1e-6
+    for j in range(m.nv):
+        e = np.zeros((3, m.nv))
+        e[:, j] = h
+        Rp, pp = rbd.fk(m, retract(m, s.q, e))
+        Rm, pm = rbd.fk(m, retract(m, s.q, -e))
+        for f, k in enumerate(frames):
+            dR = Rp[:, k] @ np.swapaxes(Rm[:, k], -1, -2)
+            w = Rot.from_matrix(dR).as_rotvec() / (2 * h)
+            v = (pp[:, k] - pm[:, k]) / (2 * h)
+            fd = np.concatenate([w, v], -1)
+            assert np.max(np.abs(fd - J[:, f, :, j])) < 1e-7 * max(1.0, np.max(np.abs(J[:, f])))
